@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 multitaper NuFFT path.
+
+One step = one exec of the whole per-signal path (spread, four-step FFT,
+deconvolve, J, eigenspectra, P-hat; the leakage estimates are plan
+constants) over a batch of B synthetic signals that share one sampling
+pattern, per GPU.  Default workload: N = 16384 jittered samples
+(t_n = n + U(-0.4, 0.4)), AR(4) signals, K = 8 tapers, f_w = 5/N,
+I = 2^18 band centres on [-1/2, 1/2), FP32 path with FP64-split coordinates.
+
+Metric: tapered samples x bands per second, sum over signals of K * N * I,
+whole job.  Multi-GPU (torchrun): each rank runs its own batch (independent
+signals, no data-path collective), weak scaling; the timed region is
+bracketed by a barrier and synchronisation and the max over ranks is taken.
+
+--impl reference times the CPU oracle (direct FP64 sum) on a bounded sample
+of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tapered samples x bands per second (sum of K*N*I over signals)"
+UNIT = "samples*bands/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="jitter16k", choices=["jitter16k", "periodic16k", "grid1024"])
+    ap.add_argument("--batch", type=int, default=32, help="signals per step per GPU")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int) -> float:
+    """Compulsory bytes one launch of each exec kernel must move (per chunk of nb signals).
+
+    spread : read x (N reals) + point records (cell int32, offset, source int32) + tapers (K x P),
+             write the spread grid (K x rows*n2 complex)
+    cols   : read the spread grid, write the column-FFT workspace (K x nf complex)
+    rows   : write J (K x I complex), eigenspectra (K x I real), P-hat (I real) and read the
+             deconvolution factors (I complex); its input is the L2-resident workspace
+    """
+    N, K, I = info["N"], info["K"], info["I"]
+    grid = K * info["rows"] * info["n2"] * csz
+    if kernel == "spread":
+        per = N * rsz + grid
+        shared = N * (8 + rsz) + K * N * (rsz if info["real_taper"] else csz)
+        return nb * per + shared
+    if kernel == "cols":
+        return nb * (grid + K * info["nf"] * csz)
+    if kernel == "rows":
+        return nb * (K * I * csz + K * I * rsz + I * rsz) + I * csz
+    raise KeyError(kernel)
+
+
+def cpu_oracle_rate(wl, target_s: float, seed: int = 0):
+    """Time the oracle's direct FP64 sum on a band subset of one signal."""
+    from oracle import _native
+    from oracle import estimator as oest
+    from synth import taper_like  # taper-shaped rows; the direct sum costs the same for any taper
+    w = taper_like(wl.K, wl.N, seed)
+    rng = np.random.default_rng(seed)
+    probe = np.sort(rng.choice(wl.I, size=256, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, probe)
+    dt = time.perf_counter() - t0
+    nb = int(min(wl.I, max(256, 256 * target_s / max(dt, 1e-6))))
+    idx = np.sort(rng.choice(wl.I, size=nb, replace=False)).astype(np.int64)
+    t0 = time.perf_counter()
+    oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, idx)
+    dt = time.perf_counter() - t0
+    units = wl.K * wl.N * nb
+    return units / dt, nb, dt, _native.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    wl = synth.workload(args.workload, batch=1, seed=0)
+    from oracle import _native
+    from oracle import estimator as oest
+    from synth import taper_like
+    w = taper_like(wl.K, wl.N, 0)
+    # bounded sample per step so that warmup + steps stay within a few minutes
+    rate, nb, dt, cores = cpu_oracle_rate(wl, min(args.cpu_seconds, 4.0))
+    per_step_s = max(0.5, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    nb_step = int(min(wl.I, max(64, rate * per_step_s / (wl.K * wl.N))))
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(wl.I, size=nb_step, replace=False)).astype(np.int64)
+    for _ in range(args.warmup):
+        oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, idx[: max(64, nb_step // 8)])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, idx)
+    total = time.perf_counter() - t0
+    units = args.steps * wl.K * wl.N * nb_step
+    value = units / total
+    sample = (f"{args.workload}: one signal, {nb_step} of {wl.I} band centres per step "
+              f"(direct FP64 sum, {cores} threads)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "bands_per_step": nb_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2407_01943_gb300 as pkg
+    import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+
+    B = args.batch
+    wl = synth.workload(args.workload, batch=B, seed=1000 * rank)
+    rdt = torch.float32 if args.precision == 32 else torch.float64
+    cdt = torch.complex64 if args.precision == 32 else torch.complex128
+    csz, rsz = (8, 4) if args.precision == 32 else (16, 8)
+
+    t_plan = time.perf_counter()
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local)
+    t_plan = time.perf_counter() - t_plan
+    info = plan.info
+
+    x = torch.from_numpy(wl.x.astype(np.float32 if args.precision == 32 else np.float64)).to(dev)
+    J = torch.empty((B, wl.K, wl.I), dtype=cdt, device=dev)
+    E = torch.empty((B, wl.K, wl.I), dtype=rdt, device=dev)
+    P = torch.empty((B, wl.I), dtype=rdt, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.exec(x, J, E, P, stream=stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K device-timed steps, L2 flushed between them ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.get_timing()
+    plan.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        evs[s][0].record(stream)
+        plan.exec(x, J, E, P, stream=stream)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    plan.set_timing(False)
+    kms, klaunch = plan.get_timing()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units_per_signal = wl.K * wl.N * wl.I
+    value = world * args.steps * B * units_per_signal / (total_ms * 1e-3)
+    chunks = -(-B // info["chunk"])
+    launches = args.steps * chunks * 3
+
+    # ---- per-kernel roofline from the live event timing ----
+    names = ["spread", "cols", "rows"]
+    hbm_peak, peak_kind = measured_peaks()
+    kern = {}
+    for i, n in enumerate(names):
+        if klaunch[i] == 0:
+            continue
+        avg_ms = kms[i] / klaunch[i]
+        nb = min(B, info["chunk"])
+        byts = algorithmic_bytes(info, n, nb, csz, rsz)
+        kern[n] = {"launches": int(klaunch[i]), "total_ms": float(kms[i]), "avg_us": 1e3 * avg_ms,
+                   "alg_bytes_per_launch": byts, "gbs": byts / (avg_ms * 1e-3) / 1e9,
+                   "share": float(kms[i] / max(sum(kms), 1e-12))}
+    dom = max(kern, key=lambda n: kern[n]["total_ms"]) if kern else None
+    roofline = None
+    if dom:
+        achieved = kern[dom]["gbs"]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                    "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"], "traffic": None}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.x.astype(np.float32 if args.precision == 32 else np.float64)).pin_memory()
+        ph = torch.empty((B, wl.I), dtype=rdt).pin_memory()
+        xd = torch.empty_like(x)
+        for _ in range(2):
+            xd.copy_(xh, non_blocking=True)
+            plan.exec(xd, J, E, P, stream=stream)
+            ph.copy_(P, non_blocking=True)
+        torch.cuda.synchronize()
+        ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.zero_()
+            ev_e[s][0].record(stream)
+            xd.copy_(xh, non_blocking=True)
+            plan.exec(xd, J, E, P, stream=stream)
+            ph.copy_(P, non_blocking=True)
+            ev_e[s][1].record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = float(sum(a.elapsed_time(b) for a, b in ev_e))
+        if world > 1:
+            tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        e2e = {"value": world * args.steps * B * units_per_signal / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(ph.numel() * ph.element_size()),
+               "ms_per_step": e2e_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nb, dt, cores = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.workload}: one signal, {nb} of {wl.I} band centres, direct FP64 sum, "
+                         f"{dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: N={wl.N} samples ({'jittered' if 'jitter' in args.workload else 'grid'}), "
+                                   f"K={wl.K}, f_w={wl.f_w:.3g}, I={wl.I}, B={B} signals per GPU per step",
+                       "signals_per_gpu_per_step": B, "N": wl.N, "K": wl.K, "I": wl.I, "nf": info["nf"],
+                       "kernel_width": info["width"], "chunk": info["chunk"],
+                       "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "kernels": kern,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "plan_seconds": t_plan,
+            "gep_seconds": info["gep_seconds"],
+            "wall_seconds_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * m2nufft.h -- C ABI of the GB300 multitaper NuFFT power-spectrum path.
+ *
+ * Method: Cui, Brinkmann & Worrell, "Multiband-Multitaper Nonuniform FFT"
+ * (arXiv 2407.01943).  Given samples x(t_n) at arbitrary times t_n
+ * (n = 1..N), a signal band B = {|f| <= f_max} with f_max = fs/2, analysis
+ * bands of half-width f_w and K tapers (Sec. 2; Table 1 steps 1-2), the
+ * library
+ *
+ *   plan  : solves the nominal-band GEP R(A0) w = lambda R(B) w for the K
+ *           largest eigenpairs in FP64 on the GPU (Sec. 3.2, Eq. gep_at_A0;
+ *           Table 1 step 3), scales each taper to w^T R(B) w = 2 f_w
+ *           (Sec. 2.2, Eq. bg_norm_requirement), and caches everything the
+ *           per-signal path needs on the device;
+ *   exec  : for every signal computes, for all I band centres
+ *           f_i = f_lo + i*df (i = 0..I-1), the eigencoefficients
+ *               J_k(A_i) = sum_n w_k(t_n) x(t_n) exp(-i 2 pi f_i t_n)
+ *           (Sec. 3.2, Eq. eigencoefficients; Table 1 step 4), the
+ *           eigenspectra |J_k(A_i)|^2 and the estimate
+ *               P(A_i) = (1/K) sum_k |J_k(A_i)|^2
+ *           (Eq. power_spectrum_estimator; Table 1 step 5), and hands out
+ *           the suboptimality estimates L_k^i = |lambda_k - lambda_hat_k^i|
+ *           and E_i = (1/K) sum_k L_k^i (Sec. 3.5; App. B, Eq. lambda_hat_ki).
+ *
+ * The nominal band is centred at f_c0 = 0, so the frequency shift of
+ * Eq. (freq_shift_op) is the band centre itself and the tapers are real.
+ * The sum over n is evaluated by a nonuniform FFT to a relative accuracy set
+ * by m2_opts.tol; the sum itself is exact by definition.
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "host" are read or written synchronously.
+ *     Pointers documented as "device" must be CUDA device (or managed)
+ *     memory of the plan's device.
+ *   - The caller owns every buffer it passes.  A plan copies what it needs
+ *     from t and owns all its device caches until m2nufft_destroy.
+ *   - Real arrays have the plan's precision: float for precision 32, double
+ *     for precision 64.  Complex arrays are interleaved (re, im) pairs of
+ *     that type.  L-hat and E-hat are always double.
+ *   - Every call returns an m2_status; on failure m2nufft_last_error()
+ *     returns a message for the calling thread.  No call aborts the process
+ *     and no C++ exception crosses this interface.
+ */
+#ifndef M2NUFFT_H
+#define M2NUFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m2nufft_plan_s* m2nufft_plan_t;
+
+typedef enum {
+    M2_OK = 0,
+    M2_ERR_ARG = 1,        /* invalid argument (sizes, NaN/inf times, f_w outside (0, fs/2), ...) */
+    M2_ERR_NOMEM = 2,      /* device or host allocation failed */
+    M2_ERR_BUDGET = 3,     /* the plan would exceed m2_opts.mem_budget */
+    M2_ERR_GEP = 4,        /* GEP failed (e.g. R(B) not positive definite in FP64: repeated times) */
+    M2_ERR_CUDA = 5,       /* a CUDA runtime / library call failed */
+    M2_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    M2_ERR_CANCELLED = 7   /* work was cancelled by the caller */
+} m2_status;
+
+/* Band centres f_i = f_lo + i*df, i = 0..I-1 (Sec. 3.1: identical analysis
+ * bands that differ only by a frequency shift).  Requires df > 0, I >= 1. */
+typedef struct {
+    double f_lo;
+    double df;
+    int64_t I;
+} m2_fgrid;
+
+/* Output selection bits (informational; exec writes whatever pointers are non-NULL). */
+enum {
+    M2_OUT_J = 1,
+    M2_OUT_E = 2,
+    M2_OUT_P = 4,
+    M2_OUT_LHAT = 8,
+    M2_OUT_EHAT = 16
+};
+
+typedef struct {
+    int precision;      /* 32 (FP32 spread/FFT, FP64-split coordinates) or 64 */
+    double tol;         /* target relative accuracy of the NuFFT; <= 0 selects
+                           1e-6 for precision 32 and 1e-12 for precision 64 */
+    size_t mem_budget;  /* maximum bytes of device memory the plan may hold
+                           (including GEP scratch); 0 = unlimited */
+    int device;         /* CUDA device ordinal; < 0 = the caller's current device */
+    int max_batch;      /* signals processed per internal chunk; <= 0 = automatic */
+} m2_opts;
+
+/* Geometry of a plan, for callers that size buffers or compute rooflines. */
+typedef struct {
+    int64_t N;           /* number of samples */
+    int K;               /* tapers */
+    int64_t I;           /* band centres */
+    int precision;       /* 32 or 64 */
+    int width;           /* spreading kernel width in fine-grid cells */
+    double beta;         /* exponential-of-semicircle kernel shape */
+    int64_t nf;          /* fine-grid (FFT) length, a power of two >= 2 I */
+    int64_t n1, n2;      /* nf = n1 * n2: column-FFT and row-FFT lengths */
+    int64_t rows;        /* nonzero input rows of the column FFTs (support / n2) */
+    int wrap;            /* 1 when the sampling span covers a whole 1/df period */
+    int real_taper;      /* 1 when the modulated tapers are real (f_lo + (I/2) df == 0) */
+    int integer_grid;    /* 1 when fs * t_n are all integers, so R(B) = I */
+    int chunk;           /* signals per internal chunk */
+    size_t device_bytes; /* device memory held by the plan */
+    double gep_seconds;  /* wall time of the GEP during planning (0 if tapers were given) */
+} m2_info;
+
+/*
+ * Create a plan for sampling times t and band-centre grid fc.
+ *   t      host, length N, any order (no sorting required); FP64
+ *   N      number of samples, >= 1
+ *   fs     nominal sampling rate; the signal band is |f| <= fs/2 (Sec. 2;
+ *          f_max = 1/2 for unit-rate data, Sec. 4)
+ *   f_w    half-bandwidth of every analysis band, 0 < f_w < fs/2
+ *   K      number of tapers, 1 <= K <= min(N, 16)
+ *   fc     host, band-centre grid
+ *   opts   host, may be NULL for defaults (precision 32)
+ *   out    host, receives the plan handle
+ * Solves the GEP with cuSOLVER in FP64 (dense, O(N^3)); synchronous.
+ * Errors: M2_ERR_ARG, M2_ERR_GEP, M2_ERR_NOMEM, M2_ERR_BUDGET, M2_ERR_CUDA.
+ */
+m2_status m2nufft_plan(const double* t, int64_t N, double fs, double f_w, int K,
+                       const m2_fgrid* fc, const m2_opts* opts, m2nufft_plan_t* out);
+
+/*
+ * Same as m2nufft_plan but with caller-supplied tapers instead of the GEP
+ * (for tapers designed elsewhere, e.g. interpolated DPSS, Table 1 step 3a-c).
+ *   w       host [K][N] FP64, in the order of t
+ *   lambda  host [K] FP64 eigenvalues used by L-hat/E-hat, or NULL (then
+ *           exec rejects requests for L-hat and E-hat)
+ * Repeated times are allowed here.
+ */
+m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double f_w, int K,
+                                   const m2_fgrid* fc, const double* w, const double* lambda,
+                                   const m2_opts* opts, m2nufft_plan_t* out);
+
+/*
+ * Run the per-signal path for B signals that share the plan's sampling times.
+ *   x      device [B][N] real (plan precision), each row in the order of t
+ *   B      number of signals, >= 0 (0 is a no-op)
+ *   J      device [B][K][I] complex, or NULL
+ *   E      device [B][K][I] real eigenspectra |J|^2, or NULL
+ *   P      device [B][I] real multitaper estimate, or NULL
+ *   Lhat   device [K][I] double leakage estimates L_k^i, or NULL
+ *   Ehat   device [I] double taper-averaged leakage E_i, or NULL
+ *   stream cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Asynchronous: returns once the work is enqueued.  Launch errors are
+ * reported here; device faults surface at the caller's next synchronisation.
+ * Calls on one plan must not overlap on the device (they share the plan's
+ * workspace); order them on one stream or synchronise between streams.
+ */
+m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P,
+                       double* Lhat, double* Ehat, void* stream);
+
+/*
+ * Uneven batch: nsig signals, each with its own plan (plans may repeat).
+ *   plans  host [nsig] plan handles
+ *   xs     host [nsig] device pointers, xs[s] -> [N_s] real
+ *   Js, Es, Ps  host [nsig] device pointers ([K_s][I_s] complex, [K_s][I_s]
+ *          real, [I_s] real); an entry or a whole array may be NULL
+ *   stream as for m2nufft_exec
+ * All plans must share one precision and one device.  Work is enqueued
+ * in order on the stream; the same ordering rule as m2nufft_exec applies.
+ */
+m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
+                             void* const* Js, void* const* Es, void* const* Ps, void* stream);
+
+/* Copy the plan's tapers (host [K][N] FP64, order of t) and eigenvalues
+ * (host [K], descending; NaN when the plan was made from caller tapers
+ * without eigenvalues).  Either pointer may be NULL. */
+m2_status m2nufft_get_tapers(m2nufft_plan_t p, double* w, double* lambda);
+
+/* Copy L-hat (host [K][I]) and E-hat (host [I]); either may be NULL. */
+m2_status m2nufft_get_leakage(m2nufft_plan_t p, double* Lhat, double* Ehat);
+
+/* Fill *info with the plan's geometry. */
+m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info);
+
+/*
+ * Instrumentation (no counterpart in the paper): per-kernel device timing.
+ * While enabled, exec records a CUDA event pair around every kernel launch on
+ * the launching stream.  m2nufft_get_timing waits for those events, returns
+ * the summed milliseconds and launch counts of the three exec kernels
+ * (index 0 = spread, 1 = column FFT, 2 = row FFT + epilogue) accumulated since
+ * the previous call, and resets the accumulators.
+ *   ms        host [3] or NULL
+ *   launches  host [3] or NULL
+ */
+m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable);
+m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);
+
+/* Release every resource of the plan (synchronises its device first).  NULL is a no-op. */
+m2_status m2nufft_destroy(m2nufft_plan_t p);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* m2nufft_last_error(void);
+
+/* Library version string. */
+const char* m2nufft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* M2NUFFT_H */

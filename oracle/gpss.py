@@ -87,3 +87,17 @@ def all_generalized_eigenvalues(t: np.ndarray, fs: float, f_w: float) -> np.ndar
     RB = gpss_matrix_b(t, fs / 2.0)
     RA = gpss_matrix_a(t, f_w)
     return np.sort(scipy.linalg.eigh(RA, RB, eigvals_only=True))[::-1]
+
+
+def gpss_rows(t: np.ndarray, rows, f_max: float) -> np.ndarray:
+    """Selected rows of R for the band |f| <= f_max (same formula as
+    gpss_matrix_b, evaluated only for the requested rows) -- lets tests
+    check GEP residuals at sizes where the full N x N matrix is too large."""
+    t = np.asarray(t, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    d = t[rows][:, None] - t[None, :]
+    R = np.empty_like(d)
+    off = d != 0.0
+    R[off] = np.sin(2.0 * np.pi * f_max * d[off]) / (np.pi * d[off])
+    R[~off] = 2.0 * f_max
+    return R

@@ -1,0 +1,266 @@
+"""Thin Python binding of libm2nufft (include/m2nufft.h) via ctypes.
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams; numpy supplies
+host arrays.  If the shared library is missing or fails to load, every
+entry point raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build_lib
+
+M2_OK = 0
+STATUS_NAMES = {0: "M2_OK", 1: "M2_ERR_ARG", 2: "M2_ERR_NOMEM", 3: "M2_ERR_BUDGET", 4: "M2_ERR_GEP",
+                5: "M2_ERR_CUDA", 6: "M2_ERR_TIMEOUT", 7: "M2_ERR_CANCELLED"}
+
+
+class M2Error(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+class m2_fgrid(ctypes.Structure):
+    _fields_ = [("f_lo", ctypes.c_double), ("df", ctypes.c_double), ("I", ctypes.c_int64)]
+
+
+class m2_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
+                ("device", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class m2_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("K", ctypes.c_int), ("I", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("width", ctypes.c_int), ("beta", ctypes.c_double), ("nf", ctypes.c_int64),
+                ("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("rows", ctypes.c_int64), ("wrap", ctypes.c_int),
+                ("real_taper", ctypes.c_int), ("integer_grid", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("gep_seconds", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every exported entry point of include/m2nufft.h
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+EXPORTS = [
+    ("m2nufft_plan", ctypes.c_int, [_DP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(m2_fgrid), ctypes.POINTER(m2_opts), ctypes.POINTER(_VP)]),
+    ("m2nufft_plan_with_tapers", ctypes.c_int,
+     [_DP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(m2_fgrid), _DP, _DP,
+      ctypes.POINTER(m2_opts), ctypes.POINTER(_VP)]),
+    ("m2nufft_exec", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
+                                          ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("m2nufft_get_tapers", ctypes.c_int, [_VP, _DP, _DP]),
+    ("m2nufft_get_leakage", ctypes.c_int, [_VP, _DP, _DP]),
+    ("m2nufft_get_info", ctypes.c_int, [_VP, ctypes.POINTER(m2_info)]),
+    ("m2nufft_set_timing", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("m2nufft_get_timing", ctypes.c_int, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    ("m2nufft_destroy", ctypes.c_int, [_VP]),
+    ("m2nufft_last_error", ctypes.c_char_p, []),
+    ("m2nufft_version", ctypes.c_char_p, []),
+]
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib_path() -> str:
+    return _build_lib.LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libm2nufft.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and _build_lib.is_stale():
+                _build_lib.build()
+            if not os.path.exists(_build_lib.LIB_PATH):
+                raise RuntimeError("libm2nufft.so is not built; run paper_2407_01943_gb300.build()")
+            L = ctypes.CDLL(_build_lib.LIB_PATH)
+            for name, res, args in EXPORTS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != M2_OK:
+        raise M2Error(status, where, load().m2nufft_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _tptr(x) -> Optional[int]:
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A cached M2NuFFT plan for one sampling pattern and one band grid."""
+
+    def __init__(self, t, fs: float, f_w: float, K: int, f_lo: float, df: float, I: int,
+                 precision: int = 32, tol: float = 0.0, mem_budget: int = 0, device: int = -1,
+                 max_batch: int = 0, tapers=None, lam=None):
+        L = load()
+        self._t = np.ascontiguousarray(t, dtype=np.float64)
+        self.N = int(self._t.shape[0])
+        self.K = int(K)
+        self.I = int(I)
+        self.precision = int(precision)
+        self.fs, self.f_w, self.f_lo, self.df = float(fs), float(f_w), float(f_lo), float(df)
+        fg = m2_fgrid(self.f_lo, self.df, self.I)
+        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch))
+        h = _VP()
+        if tapers is None:
+            st = L.m2nufft_plan(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(fg),
+                                ctypes.byref(op), ctypes.byref(h))
+            _check(st, "m2nufft_plan")
+        else:
+            w = np.ascontiguousarray(tapers, dtype=np.float64)
+            if w.shape != (self.K, self.N):
+                raise ValueError(f"tapers must have shape ({self.K}, {self.N})")
+            lp = None
+            if lam is not None:
+                self._lam_in = np.ascontiguousarray(lam, dtype=np.float64)
+                lp = _dptr(self._lam_in)
+            st = L.m2nufft_plan_with_tapers(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(fg),
+                                            _dptr(w), lp, ctypes.byref(op), ctypes.byref(h))
+            _check(st, "m2nufft_plan_with_tapers")
+        self._h = h
+        inf = m2_info()
+        _check(L.m2nufft_get_info(self._h, ctypes.byref(inf)), "m2nufft_get_info")
+        self.info = {f: getattr(inf, f) for f, _ in m2_info._fields_}
+
+    # -- properties -----------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def real_dtype(self):
+        import torch
+        return torch.float32 if self.precision == 32 else torch.float64
+
+    @property
+    def complex_dtype(self):
+        import torch
+        return torch.complex64 if self.precision == 32 else torch.complex128
+
+    def tapers(self):
+        w = np.empty((self.K, self.N))
+        lam = np.empty(self.K)
+        _check(load().m2nufft_get_tapers(self._h, _dptr(w), _dptr(lam)), "m2nufft_get_tapers")
+        return w, lam
+
+    def leakage(self):
+        Lh = np.empty((self.K, self.I))
+        Eh = np.empty(self.I)
+        _check(load().m2nufft_get_leakage(self._h, _dptr(Lh), _dptr(Eh)), "m2nufft_get_leakage")
+        return Lh, Eh
+
+    # -- execution ------------------------------------------------------
+    def exec(self, x, J=None, E=None, P=None, Lhat=None, Ehat=None, stream=None):
+        """Enqueue the path for x [B, N] (torch CUDA tensor of the plan's real dtype)."""
+        if x.dim() != 2 or x.shape[1] != self.N:
+            raise ValueError(f"x must have shape [B, {self.N}]")
+        if x.dtype != self.real_dtype:
+            raise ValueError(f"x must be {self.real_dtype}")
+        B = int(x.shape[0])
+        for name, a, shape, dt in (("J", J, (B, self.K, self.I), self.complex_dtype),
+                                   ("E", E, (B, self.K, self.I), self.real_dtype),
+                                   ("P", P, (B, self.I), self.real_dtype)):
+            if a is not None and (tuple(a.shape) != shape or a.dtype != dt):
+                raise ValueError(f"{name} must be {dt} with shape {shape}")
+        st = load().m2nufft_exec(self._h, _tptr(x), B, _tptr(J), _tptr(E), _tptr(P), _tptr(Lhat),
+                                 _tptr(Ehat), _stream_handle(stream))
+        _check(st, "m2nufft_exec")
+
+    def run(self, x, want=("J", "E", "P"), stream=None):
+        """Allocate the requested outputs with torch and run; returns a dict."""
+        import torch
+        B = int(x.shape[0])
+        dev = x.device
+        out = {}
+        if "J" in want:
+            out["J"] = torch.empty((B, self.K, self.I), dtype=self.complex_dtype, device=dev)
+        if "E" in want:
+            out["E"] = torch.empty((B, self.K, self.I), dtype=self.real_dtype, device=dev)
+        if "P" in want:
+            out["P"] = torch.empty((B, self.I), dtype=self.real_dtype, device=dev)
+        if "Lhat" in want:
+            out["Lhat"] = torch.empty((self.K, self.I), dtype=torch.float64, device=dev)
+        if "Ehat" in want:
+            out["Ehat"] = torch.empty((self.I,), dtype=torch.float64, device=dev)
+        self.exec(x, out.get("J"), out.get("E"), out.get("P"), out.get("Lhat"), out.get("Ehat"), stream)
+        return out
+
+    def set_timing(self, enable: bool = True):
+        _check(load().m2nufft_set_timing(self._h, 1 if enable else 0), "m2nufft_set_timing")
+
+    def get_timing(self):
+        """(ms[3], launches[3]) of spread / column FFT / row FFT+epilogue since the last call."""
+        ms = np.zeros(3)
+        n = np.zeros(3, dtype=np.int64)
+        _check(load().m2nufft_get_timing(self._h, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "m2nufft_get_timing")
+        return ms, n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().m2nufft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def exec_batch(plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, stream=None):
+    """Uneven batch: one signal per entry, each with its own plan."""
+    n = len(plans)
+    arr = lambda vals: (_VP * n)(*vals)
+    hp = arr([p.handle.value for p in plans])
+    hx = arr([_tptr(x) for x in xs])
+    hJ = arr([_tptr(j) for j in Js]) if Js is not None else None
+    hE = arr([_tptr(e) for e in Es]) if Es is not None else None
+    hP = arr([_tptr(q) for q in Ps]) if Ps is not None else None
+    st = load().m2nufft_exec_batch(hp, hx, n, hJ, hE, hP, _stream_handle(stream))
+    _check(st, "m2nufft_exec_batch")
+
+
+def version() -> str:
+    return load().m2nufft_version().decode()

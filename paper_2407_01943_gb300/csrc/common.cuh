@@ -1,0 +1,115 @@
+// Shared definitions of the GB300 M2NuFFT library (plan + exec).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "m2nufft.h"
+
+namespace m2 {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define M2_CUDA_TRY(expr)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::m2::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),        \
+                            __FILE__, __LINE__);                                           \
+            return e_ == cudaErrorMemoryAllocation ? M2_ERR_NOMEM : M2_ERR_CUDA;           \
+        }                                                                                  \
+    } while (0)
+
+#define M2_TRY(expr)                      \
+    do {                                  \
+        m2_status s_ = (expr);            \
+        if (s_ != M2_OK) return s_;       \
+    } while (0)
+
+template <typename R> struct CT;
+template <> struct CT<float> { using C = float2; };
+template <> struct CT<double> { using C = double2; };
+
+// Spreading tile: fine-grid cells per CTA of the spread kernel.
+constexpr int kSpreadTile = 256;
+// Points staged in shared memory per chunk of the spread kernel.
+constexpr int kSpreadChunk = 256;
+// Largest K the exec kernels are instantiated for.
+constexpr int kMaxK = 16;
+
+// Fine-grid / FFT geometry of one plan.
+struct Geometry {
+    int64_t N = 0;        // samples
+    int K = 0;            // tapers
+    int64_t I = 0;        // band centres
+    double f_lo = 0, df = 0;
+    int64_t i_c = 0;      // I / 2: band index of the mid frequency
+    double fmid_hi = 0, fmid_lo = 0;  // f_lo + i_c df as a double-double
+    int width = 0;        // spreading kernel width (cells)
+    double beta = 0;      // ES kernel shape
+    int64_t nf = 0;       // FFT length
+    int log_nf = 0;
+    int64_t n1 = 0, n2 = 0;  // nf = n1 * n2
+    int log_n1 = 0, log_n2 = 0;
+    int64_t rows = 0;     // nonzero rows of the column FFT input
+    int64_t Lg = 0;       // spread-grid cells written per (signal, taper) = rows * n2
+    int wrap = 0;         // support covers the whole period
+    double h = 0;         // cell width in time units = 1 / (nf df)
+    double t_ref = 0;     // time of fine-grid cell 0
+    int real_taper = 1;   // modulated taper is real
+    int64_t P = 0;        // number of (extended) spread points
+    int64_t ntiles = 0;   // spread tiles
+    int cw = 0;           // columns per CTA in the column pass
+    int rw = 0;           // rows per CTA in the row pass
+    int chunk = 1;        // signals per chunk
+    int twb_bits = 0;     // low-bit width of the two-level nf twiddle table
+};
+
+}  // namespace m2
+
+struct m2nufft_plan_s {
+    m2::Geometry g;
+    int device = 0;
+    int precision = 32;
+    double fs = 1.0, f_w = 0.0;
+    double tol = 0.0;
+    int integer_grid = 0;
+    int have_lambda = 0;
+    int have_leakage = 0;
+    double gep_seconds = 0.0;
+    size_t device_bytes = 0;
+    std::vector<double> t;       // caller order
+    std::vector<double> w;       // [K][N] caller order
+    std::vector<double> lambda;  // [K] descending
+
+    // device caches (precision-typed buffers are void*)
+    int32_t* d_pt_src = nullptr;   // [P] index into x (caller order)
+    int32_t* d_pt_cell = nullptr;  // [P] first fine-grid cell of the point's window
+    void* d_pt_off = nullptr;      // [P] R: (first cell) - u_n, in cells
+    void* d_taper = nullptr;       // [K][P] R (real taper) or C (modulated taper)
+    int32_t* d_tile_pb = nullptr;  // [ntiles] first point of each spread tile
+    int32_t* d_tile_pe = nullptr;  // [ntiles] one past the last point
+    void* d_deconv = nullptr;      // [I] C: exp(-i 2 pi m df t_ref) / phihat(m)
+    void* d_tw1 = nullptr;         // [n1/2] C: exp(-i 2 pi q / n1)
+    void* d_tw2 = nullptr;         // [n2/2] C: exp(-i 2 pi q / n2)
+    void* d_twa = nullptr;         // [nf >> twb_bits] C: exp(-i 2 pi (q << twb_bits) / nf)
+    void* d_twb = nullptr;         // [1 << twb_bits]  C: exp(-i 2 pi q / nf)
+    double* d_Lhat = nullptr;      // [K][I]
+    double* d_Ehat = nullptr;      // [I]
+    void* d_g = nullptr;           // workspace [chunk][K][Lg] C
+    void* d_Z = nullptr;           // workspace [chunk][K][nf] C
+    std::vector<void*> allocations;
+
+    // per-kernel timing (instrumentation): event pairs recorded by exec
+    int timing = 0;
+    std::vector<cudaEvent_t> ev_pool;       // free events
+    std::vector<cudaEvent_t> ev_rec[3][2];  // [kernel][begin/end] in launch order
+    double timing_ms[3] = {0, 0, 0};
+    int64_t timing_launches[3] = {0, 0, 0};
+};

@@ -1,0 +1,535 @@
+// Per-signal hot path of the multitaper NuFFT (Sec. 3.2, Eq. eigencoefficients
+// and Eq. power_spectrum_estimator; Table 1 steps 4-5).
+//
+// For each chunk of signals three kernels run on the caller's stream:
+//   spread  : taper-weight the samples (c_k[n] = u_k[n] x[n], kept in shared
+//             memory) and gather them onto the fine grid with the
+//             exponential-of-semicircle window.  Every CTA owns a tile of
+//             cells and sums the contributions of the points whose window
+//             covers its cells; no atomics, fixed summation order.
+//   cols    : first half of a four-step FFT of length nf = n1*n2 (column
+//             DFTs of length n1 over the nonzero support rows, then the
+//             nf-point twiddle), written to the L2-resident workspace Z.
+//   rows    : row DFTs of length n2, then the fused epilogue: deconvolve
+//             and re-phase (J = X * s[i]), write J and |J|^2, and average
+//             |J|^2 over the K tapers of the signal inside the CTA to form
+//             P-hat without atomics.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace m2 {
+namespace {
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) {
+    C r;
+    r.x = a.x + b.x;
+    r.y = a.y + b.y;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C csub(C a, C b) {
+    C r;
+    r.x = a.x - b.x;
+    r.y = a.y - b.y;
+    return r;
+}
+// a * (-i)
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) {
+    C r;
+    r.x = a.y;
+    r.y = -a.x;
+    return r;
+}
+
+__device__ __forceinline__ float es_kernel(float z, float two_over_w, float beta) {
+    float a = z * two_over_w;
+    float s = fmaxf(0.0f, 1.0f - a * a);
+    return expf(beta * (sqrtf(s) - 1.0f));
+}
+__device__ __forceinline__ double es_kernel(double z, double two_over_w, double beta) {
+    double a = z * two_over_w;
+    double s = fmax(0.0, 1.0 - a * a);
+    return exp(beta * (sqrt(s) - 1.0));
+}
+
+__device__ __forceinline__ int bitrev(int v, int bits) {
+    return (int)(__brev((unsigned)v) >> (32 - bits));
+}
+
+// In-place radix-2/4 decimation-in-time FFTs of `nrows` rows of length M
+// (row stride `rs` elements) in shared memory.  Input must be in
+// bit-reversed order; output is in natural order.  `tw[q]` = exp(-i 2 pi q/M)
+// for q < M/2.  Caller synchronises before (data ready) and after.
+template <typename C>
+__device__ void fft_rows_dit(C* buf, int nrows, int M, int logM, int rs, const C* tw) {
+    const int nt = blockDim.x;
+    int s = 0;
+    if (logM & 1) {
+        const int half = M >> 1;
+        for (int idx = threadIdx.x; idx < nrows * half; idx += nt) {
+            int r = idx / half, j = idx - r * half;
+            C* b = buf + r * rs + 2 * j;
+            C a = b[0], c = b[1];
+            b[0] = cadd(a, c);
+            b[1] = csub(a, c);
+        }
+        s = 1;
+        __syncthreads();
+    }
+    for (; s < logM; s += 2) {
+        const int h = 1 << s;
+        const int quarter = M >> 2;
+        const int sh1 = logM - s - 1, sh2 = logM - s - 2;
+        for (int idx = threadIdx.x; idx < nrows * quarter; idx += nt) {
+            int r = idx / quarter, q = idx - r * quarter;
+            int blk = q >> s, rr = q & (h - 1);
+            C* b = buf + r * rs + blk * 4 * h + rr;
+            C x0 = b[0], x1 = b[h], x2 = b[2 * h], x3 = b[3 * h];
+            C w1 = tw[rr << sh1];
+            C t1 = cmul(x1, w1), t3 = cmul(x3, w1);
+            C a0 = cadd(x0, t1), a1 = csub(x0, t1), a2 = cadd(x2, t3), a3 = csub(x2, t3);
+            C w2 = tw[rr << sh2];
+            C u2 = cmul(a2, w2), u3 = cmul_mi(cmul(a3, w2));
+            b[0] = cadd(a0, u2);
+            b[2 * h] = csub(a0, u2);
+            b[h] = cadd(a1, u3);
+            b[3 * h] = csub(a1, u3);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spread: g[b][k][c] = sum_n u_k[n] x_b[n] phi(c - u_n)
+// ---------------------------------------------------------------------------
+template <typename R, bool CPLX, int KM>
+__global__ void __launch_bounds__(kSpreadTile)
+spread_kernel(const R* __restrict__ x, int64_t N, const int32_t* __restrict__ pt_src,
+              const int32_t* __restrict__ pt_cell, const R* __restrict__ pt_off,
+              const void* __restrict__ taper_v, int64_t P, const int32_t* __restrict__ tile_pb,
+              const int32_t* __restrict__ tile_pe, int K, int w, R two_over_w, R beta, int64_t Lg,
+              typename CT<R>::C* __restrict__ g) {
+    using C = typename CT<R>::C;
+    using V = typename std::conditional<CPLX, C, R>::type;
+    extern __shared__ unsigned char smem_raw[];
+    int32_t* s_cell = reinterpret_cast<int32_t*>(smem_raw);
+    R* s_off = reinterpret_cast<R*>(smem_raw + sizeof(R) * kSpreadChunk);  // aligned: chunk*8 bytes
+    V* s_val = reinterpret_cast<V*>(smem_raw + 2 * sizeof(R) * kSpreadChunk);
+
+    const V* taper = reinterpret_cast<const V*>(taper_v);
+    const int tile = blockIdx.x;
+    const int b = blockIdx.y;
+    const int64_t c = (int64_t)tile * kSpreadTile + threadIdx.x;
+    const int pb = tile_pb[tile], pe = tile_pe[tile];
+    const R* xb = x + (int64_t)b * N;
+
+    C acc[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) acc[k].x = acc[k].y = R(0);
+
+    for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
+        const int n = min(kSpreadChunk, pe - q0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const int p = q0 + j;
+            s_cell[j] = pt_cell[p];
+            s_off[j] = pt_off[p];
+            const R xv = xb[pt_src[p]];
+            for (int k = 0; k < K; ++k) {
+                V tv = taper[(int64_t)k * P + p];
+                if constexpr (CPLX) {
+                    tv.x *= xv;
+                    tv.y *= xv;
+                } else {
+                    tv *= xv;
+                }
+                s_val[k * kSpreadChunk + j] = tv;
+            }
+        }
+        __syncthreads();
+        if (c < Lg) {
+            const int ci = (int)c;
+            // first staged point whose window reaches cell c
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (s_cell[mid] + w <= ci) lo = mid + 1; else hi = mid;
+            }
+            for (int j = lo; j < n && s_cell[j] <= ci; ++j) {
+                const R z = s_off[j] + (R)(ci - s_cell[j]);
+                const R phi = es_kernel(z, two_over_w, beta);
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (k < K) {
+                        V v = s_val[k * kSpreadChunk + j];
+                        if constexpr (CPLX) {
+                            acc[k].x += v.x * phi;
+                            acc[k].y += v.y * phi;
+                        } else {
+                            acc[k].x += v * phi;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (c < Lg) {
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+            if (k < K) g[((int64_t)b * K + k) * Lg + c] = acc[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// column pass: Z[b][k][k1][l2] = W_nf^{l2 k1} sum_{l1 < rows} g[b][k][n2 l1 + l2] W_n1^{l1 k1}
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+cols_kernel(const typename CT<R>::C* __restrict__ g, int64_t Lg, int rows, int n1, int log_n1,
+            int n2, int cw, int K, const typename CT<R>::C* __restrict__ tw1,
+            const typename CT<R>::C* __restrict__ twa, const typename CT<R>::C* __restrict__ twb,
+            int twb_bits, typename CT<R>::C* __restrict__ Z) {
+    using C = typename CT<R>::C;
+    extern __shared__ unsigned char smem_raw[];
+    C* s_tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = s_tw + (n1 >> 1);
+    const int rs = n1 + 1;
+
+    const int c0 = blockIdx.x * cw;
+    const int k = blockIdx.y;
+    const int b = blockIdx.z;
+    const C* gk = g + ((int64_t)b * K + k) * Lg;
+    C* Zk = Z + ((int64_t)b * K + k) * (int64_t)n1 * n2;
+
+    for (int q = threadIdx.x; q < (n1 >> 1); q += blockDim.x) s_tw[q] = tw1[q];
+    const int total = n1 * cw;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int l1 = idx / cw, c = idx - l1 * cw;
+        C v;
+        if (l1 < rows) v = gk[(int64_t)l1 * n2 + c0 + c];
+        else v.x = v.y = R(0);
+        buf[c * rs + bitrev(l1, log_n1)] = v;
+    }
+    __syncthreads();
+    fft_rows_dit(buf, cw, n1, log_n1, rs, s_tw);
+    const int lmask = (1 << twb_bits) - 1;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int k1 = idx / cw, c = idx - k1 * cw;
+        const int l2 = c0 + c;
+        const int64_t q = (int64_t)l2 * k1;  // < nf
+        const C tw = cmul(twa[q >> twb_bits], twb[q & lmask]);
+        Zk[(int64_t)k1 * n2 + l2] = cmul(buf[c * rs + k1], tw);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row pass + epilogue
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+rows_kernel(const typename CT<R>::C* __restrict__ Z, int n1, int n2, int log_n2, int rw, int K,
+            int64_t I, int64_t i_c, int64_t nf, const typename CT<R>::C* __restrict__ tw2,
+            const typename CT<R>::C* __restrict__ deconv, typename CT<R>::C* __restrict__ J,
+            R* __restrict__ E, R* __restrict__ Pout) {
+    using C = typename CT<R>::C;
+    extern __shared__ unsigned char smem_raw[];
+    C* s_tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = s_tw + (n2 >> 1);
+    const int rs = n2 + 1;
+    R* pacc = reinterpret_cast<R*>(buf + rw * rs);
+
+    const int r0 = blockIdx.x * rw;
+    const int b = blockIdx.y;
+    const int total = rw * n2;
+    const int64_t half = nf >> 1;
+
+    for (int q = threadIdx.x; q < (n2 >> 1); q += blockDim.x) s_tw[q] = tw2[q];
+    for (int e = threadIdx.x; e < total; e += blockDim.x) pacc[e] = R(0);
+
+    for (int k = 0; k < K; ++k) {
+        const C* Zk = Z + ((int64_t)b * K + k) * (int64_t)n1 * n2;
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = idx / n2, l2 = idx - r * n2;
+            buf[r * rs + bitrev(l2, log_n2)] = Zk[(int64_t)(r0 + r) * n2 + l2];
+        }
+        __syncthreads();
+        fft_rows_dit(buf, rw, n2, log_n2, rs, s_tw);
+        C* Jk = J ? J + ((int64_t)b * K + k) * I : nullptr;
+        R* Ek = E ? E + ((int64_t)b * K + k) * I : nullptr;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int r = e % rw, k2 = e / rw;
+            const int64_t kk = (int64_t)(r0 + r) + (int64_t)n1 * k2;
+            const int64_t m = kk < half ? kk : kk - nf;
+            const int64_t i = m + i_c;
+            if (i >= 0 && i < I) {
+                const C jv = cmul(buf[r * rs + k2], deconv[i]);
+                const R p = jv.x * jv.x + jv.y * jv.y;
+                if (Jk) Jk[i] = jv;
+                if (Ek) Ek[i] = p;
+                pacc[e] += p;
+            }
+        }
+    }
+    if (Pout) {
+        __syncthreads();
+        const R invK = R(1) / (R)K;
+        R* Pb = Pout + (int64_t)b * I;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            const int r = e % rw, k2 = e / rw;
+            const int64_t kk = (int64_t)(r0 + r) + (int64_t)n1 * k2;
+            const int64_t m = kk < half ? kk : kk - nf;
+            const int64_t i = m + i_c;
+            if (i >= 0 && i < I) Pb[i] = pacc[e] * invK;
+        }
+    }
+}
+
+template <typename R>
+size_t spread_smem(int K, bool cplx) {
+    return 2 * sizeof(R) * kSpreadChunk +
+           (size_t)K * kSpreadChunk * (cplx ? 2 * sizeof(R) : sizeof(R));
+}
+template <typename R>
+size_t cols_smem(const Geometry& g) {
+    using C = typename CT<R>::C;
+    return sizeof(C) * ((size_t)(g.n1 >> 1) + (size_t)g.cw * (g.n1 + 1));
+}
+template <typename R>
+size_t rows_smem(const Geometry& g) {
+    using C = typename CT<R>::C;
+    return sizeof(C) * ((size_t)(g.n2 >> 1) + (size_t)g.rw * (g.n2 + 1)) +
+           sizeof(R) * (size_t)g.rw * g.n2;
+}
+
+template <typename R, bool CPLX, int KM>
+m2_status launch_spread(const m2nufft_plan_s* p, const R* x, int nb, cudaStream_t st) {
+    using C = typename CT<R>::C;
+    const Geometry& g = p->g;
+    const size_t smem = spread_smem<R>(g.K, CPLX);
+    auto kern = spread_kernel<R, CPLX, KM>;
+    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)g.ntiles, (unsigned)nb);
+    kern<<<grid, kSpreadTile, smem, st>>>(
+        x, g.N, p->d_pt_src, p->d_pt_cell, reinterpret_cast<const R*>(p->d_pt_off), p->d_taper, g.P,
+        p->d_tile_pb, p->d_tile_pe, g.K, g.width, (R)(2.0 / g.width), (R)g.beta, g.Lg,
+        reinterpret_cast<C*>(p->d_g));
+    M2_CUDA_TRY(cudaGetLastError());
+    return M2_OK;
+}
+
+template <typename R, bool CPLX>
+m2_status launch_spread_k(const m2nufft_plan_s* p, const R* x, int nb, cudaStream_t st) {
+    const int K = p->g.K;
+    if (K <= 4) return launch_spread<R, CPLX, 4>(p, x, nb, st);
+    if (K <= 8) return launch_spread<R, CPLX, 8>(p, x, nb, st);
+    return launch_spread<R, CPLX, 16>(p, x, nb, st);
+}
+
+// Instrumentation: record an event on the launching stream before / after a kernel.
+cudaEvent_t take_event(m2nufft_plan_s* p) {
+    cudaEvent_t e = nullptr;
+    if (!p->ev_pool.empty()) {
+        e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+inline void mark(m2nufft_plan_s* p, int kernel, int which, cudaStream_t st) {
+    if (!p->timing) return;
+    cudaEvent_t e = take_event(p);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    p->ev_rec[kernel][which].push_back(e);
+}
+
+template <typename R>
+m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J, R* E, R* P,
+                     cudaStream_t st) {
+    using C = typename CT<R>::C;
+    const Geometry& g = p->g;
+    mark(p, 0, 0, st);
+    if (g.real_taper) M2_TRY((launch_spread_k<R, false>(p, x, nb, st)));
+    else M2_TRY((launch_spread_k<R, true>(p, x, nb, st)));
+    mark(p, 0, 1, st);
+
+    {
+        const size_t smem = cols_smem<R>(g);
+        auto kern = cols_kernel<R>;
+        M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)(g.n2 / g.cw), (unsigned)g.K, (unsigned)nb);
+        mark(p, 1, 0, st);
+        kern<<<grid, 256, smem, st>>>(reinterpret_cast<const C*>(p->d_g), g.Lg, (int)g.rows, (int)g.n1,
+                                      g.log_n1, (int)g.n2, g.cw, g.K,
+                                      reinterpret_cast<const C*>(p->d_tw1),
+                                      reinterpret_cast<const C*>(p->d_twa),
+                                      reinterpret_cast<const C*>(p->d_twb), g.twb_bits,
+                                      reinterpret_cast<C*>(p->d_Z));
+        M2_CUDA_TRY(cudaGetLastError());
+        mark(p, 1, 1, st);
+    }
+    {
+        const size_t smem = rows_smem<R>(g);
+        auto kern = rows_kernel<R>;
+        M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)(g.n1 / g.rw), (unsigned)nb);
+        mark(p, 2, 0, st);
+        kern<<<grid, 256, smem, st>>>(reinterpret_cast<const C*>(p->d_Z), (int)g.n1, (int)g.n2, g.log_n2,
+                                      g.rw, g.K, g.I, g.i_c, g.nf,
+                                      reinterpret_cast<const C*>(p->d_tw2),
+                                      reinterpret_cast<const C*>(p->d_deconv), J, E, P);
+        M2_CUDA_TRY(cudaGetLastError());
+        mark(p, 2, 1, st);
+    }
+    return M2_OK;
+}
+
+template <typename R>
+m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, void* Ev, void* Pv,
+                     cudaStream_t st) {
+    using C = typename CT<R>::C;
+    const Geometry& g = p->g;
+    const R* x = reinterpret_cast<const R*>(xv);
+    C* J = reinterpret_cast<C*>(Jv);
+    R* E = reinterpret_cast<R*>(Ev);
+    R* P = reinterpret_cast<R*>(Pv);
+    for (int64_t b0 = 0; b0 < B; b0 += g.chunk) {
+        const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
+        M2_TRY(exec_chunk<R>(p, x + b0 * g.N, nb, J ? J + b0 * g.K * g.I : nullptr,
+                             E ? E + b0 * g.K * g.I : nullptr, P ? P + b0 * g.I : nullptr, st));
+    }
+    return M2_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E, void* P,
+                   double* Lhat, double* Ehat, cudaStream_t st) {
+    if (B < 0) {
+        set_error("m2nufft_exec: B must be >= 0");
+        return M2_ERR_ARG;
+    }
+    if ((Lhat || Ehat) && !p->have_leakage) {
+        set_error("m2nufft_exec: L-hat/E-hat are not available for this plan "
+                  "(no eigenvalues were supplied, or the sampling pattern needs the general leakage path)");
+        return M2_ERR_ARG;
+    }
+    if (B > 0 && !x) {
+        set_error("m2nufft_exec: x is NULL");
+        return M2_ERR_ARG;
+    }
+    if (B > 0) {
+        if (p->precision == 32) M2_TRY(exec_typed<float>(p, x, B, J, E, P, st));
+        else M2_TRY(exec_typed<double>(p, x, B, J, E, P, st));
+    }
+    const Geometry& g = p->g;
+    if (Lhat)
+        M2_CUDA_TRY(cudaMemcpyAsync(Lhat, p->d_Lhat, sizeof(double) * g.K * g.I, cudaMemcpyDeviceToDevice, st));
+    if (Ehat)
+        M2_CUDA_TRY(cudaMemcpyAsync(Ehat, p->d_Ehat, sizeof(double) * g.I, cudaMemcpyDeviceToDevice, st));
+    return M2_OK;
+}
+
+}  // namespace
+}  // namespace m2
+
+extern "C" m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P,
+                                  double* Lhat, double* Ehat, void* stream) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("m2nufft_exec: plan is NULL");
+        return M2_ERR_ARG;
+    }
+    m2::DeviceGuard guard(p->device);
+    return m2::exec_one(p, x, B, J, E, P, Lhat, Ehat, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
+                                        void* const* Js, void* const* Es, void* const* Ps, void* stream) {
+    m2::clear_error();
+    if (nsig < 0 || (nsig > 0 && (!plans || !xs))) {
+        m2::set_error("m2nufft_exec_batch: invalid arguments");
+        return M2_ERR_ARG;
+    }
+    if (nsig == 0) return M2_OK;
+    for (int64_t s = 0; s < nsig; ++s) {
+        if (!plans[s]) {
+            m2::set_error("m2nufft_exec_batch: plan %lld is NULL", (long long)s);
+            return M2_ERR_ARG;
+        }
+        if (plans[s]->precision != plans[0]->precision || plans[s]->device != plans[0]->device) {
+            m2::set_error("m2nufft_exec_batch: plans differ in precision or device");
+            return M2_ERR_ARG;
+        }
+    }
+    m2::DeviceGuard guard(plans[0]->device);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int64_t s = 0; s < nsig; ++s) {
+        m2_status r = m2::exec_one(plans[s], xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr,
+                                   Ps ? Ps[s] : nullptr, nullptr, nullptr, st);
+        if (r != M2_OK) return r;
+    }
+    return M2_OK;
+}
+
+extern "C" m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    p->timing = enable ? 1 : 0;
+    return M2_OK;
+}
+
+extern "C" m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    m2::DeviceGuard guard(p->device);
+    for (int k = 0; k < 3; ++k) {
+        auto& b = p->ev_rec[k][0];
+        auto& e = p->ev_rec[k][1];
+        const size_t n = std::min(b.size(), e.size());
+        for (size_t i = 0; i < n; ++i) {
+            float t = 0.f;
+            if (cudaEventSynchronize(e[i]) == cudaSuccess && cudaEventElapsedTime(&t, b[i], e[i]) == cudaSuccess) {
+                p->timing_ms[k] += t;
+                p->timing_launches[k] += 1;
+            }
+        }
+        for (cudaEvent_t ev : b) p->ev_pool.push_back(ev);
+        for (cudaEvent_t ev : e) p->ev_pool.push_back(ev);
+        b.clear();
+        e.clear();
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (ms) ms[k] = p->timing_ms[k];
+        if (launches) launches[k] = p->timing_launches[k];
+        p->timing_ms[k] = 0;
+        p->timing_launches[k] = 0;
+    }
+    return M2_OK;
+}

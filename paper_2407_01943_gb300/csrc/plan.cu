@@ -1,0 +1,888 @@
+// Plan construction (Table 1 steps 1-3) and the plan-level C ABI.
+//
+//   * sort the sampling times, check them, detect integer grids (R(B) = I);
+//   * nominal-band GEP R(A0) w = lambda R(B) w (Sec. 3.2, Eq. gep_at_A0) in
+//     FP64 with cuSOLVER on matrices built by a kernel from Eq. (gpss_matrix_b)
+//     and Eq. (gpss_matrix_a) with f_c0 = 0; keep the K largest eigenpairs and
+//     scale to w^T R(B) w = 2 f_w (Sec. 2.2, Eq. bg_norm_requirement);
+//   * NuFFT geometry: fine-grid length, support rows, split coordinates
+//     (int32 cell + small offset, formed from FP64 two-products), spreading
+//     tiles, twiddle tables, and the per-band deconvolution / re-phasing
+//     factors (FP64 Gauss-Legendre quadrature of the kernel transform);
+//   * the leakage estimate of App. B (Eq. lambda_hat_ki).
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace m2 {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+void clear_error() { g_last_error.clear(); }
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+// exact products and sums (error-free transformations)
+inline void two_prod(double a, double b, double& p, double& e) {
+    p = a * b;
+    e = std::fma(a, b, -p);
+}
+inline void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// fractional cycles of (ah + al) * t, in [-0.5, 0.5]
+inline double frac_cycles(double ah, double al, double t) {
+    double p, e;
+    two_prod(ah, t, p, e);
+    double r = (p - std::nearbyint(p)) + e + al * t;
+    return r - std::nearbyint(r);
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt) {
+    x.resize(n);
+    wt.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = pk;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plan kernels (FP64)
+// ---------------------------------------------------------------------------
+// Column-major N x N: RB[i + j N] = sin(2 pi fmax d)/(pi d), RA likewise with f_w;
+// d = t_i - t_j; diagonals 2 fmax and 2 f_w (Eqs. gpss_matrix_b, gpss_matrix_a, f_c0 = 0).
+__global__ void gpss_matrices_kernel(const double* __restrict__ t, int N, double fmax, double fw,
+                                     double* __restrict__ RA, double* __restrict__ RB) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= N) return;
+    const size_t o = (size_t)i + (size_t)j * N;
+    if (i == j) {
+        RB[o] = 2.0 * fmax;
+        RA[o] = 2.0 * fw;
+        return;
+    }
+    const double d = t[i] - t[j];
+    const double pd = kPi * d;
+    RB[o] = sinpi(2.0 * fmax * d) / pd;
+    RA[o] = sinpi(2.0 * fw * d) / pd;
+}
+
+// s[i] = exp(-i 2 pi m df t_ref) / phihat(m), m = i - i_c, with
+// phihat(m) = 2 sum_q pw[q] cos(2 pi m z_q / nf)  (pw = GL weight * phi(z_q) on [0, w/2]).
+template <typename C>
+__global__ void deconv_kernel(int64_t I, int64_t i_c, double inv_nf, const double* __restrict__ zq,
+                              const double* __restrict__ pw, int Q, double ah, double al,
+                              C* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    const double m = (double)(i - i_c);
+    double acc = 0.0;
+    for (int q = 0; q < Q; ++q) acc += pw[q] * cospi(2.0 * m * zq[q] * inv_nf);
+    const double ph = 2.0 * acc;
+    // cycles = m * (ah + al), reduced exactly
+    const double p = m * ah;
+    const double e = fma(m, ah, -p);
+    double cyc = (p - rint(p)) + e + m * al;
+    cyc -= rint(cyc);
+    double s, c;
+    sincospi(2.0 * cyc, &s, &c);
+    C r;
+    r.x = (decltype(r.x))(c / ph);
+    r.y = (decltype(r.x))(-s / ph);
+    out[i] = r;
+}
+
+// Integer grids: R(B) = I, so D_k^i = ||w_k||^2 for every band and
+// L_k^i = lambda_k |1 - 2 f_w / ||w_k||^2| (App. B).
+__global__ void leakage_const_kernel(int K, int64_t I, const double* __restrict__ Lk, double* __restrict__ L,
+                                     double* __restrict__ Eh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+        L[(int64_t)k * I + i] = Lk[k];
+        s += Lk[k];
+    }
+    Eh[i] = s / K;
+}
+
+// General sampling, small problems: D_k^i = sum_{n,m} w_n w_m R(B|n,m) cos(2 pi f_i (t_n - t_m))
+// evaluated directly (App. B, Eq. lambda_hat_ki); one thread per band.
+__global__ void leakage_direct_kernel(int N, int K, int64_t I, const double* __restrict__ tc,
+                                      const double* __restrict__ w /*[K][N] sorted*/, double fmax,
+                                      double f_lo, double df, const double* __restrict__ lam, double fw,
+                                      double* __restrict__ L, double* __restrict__ Eh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    const double f = f_lo + (double)i * df;
+    double D[kMaxK];
+    for (int k = 0; k < K; ++k) D[k] = 0.0;
+    for (int n = 0; n < N; ++n) {
+        for (int k = 0; k < K; ++k) D[k] += w[(int64_t)k * N + n] * w[(int64_t)k * N + n] * 2.0 * fmax;
+        for (int m = n + 1; m < N; ++m) {
+            const double d = tc[n] - tc[m];
+            const double r = sinpi(2.0 * fmax * d) / (kPi * d) * 2.0 * cospi(2.0 * f * d);
+            for (int k = 0; k < K; ++k) D[k] += w[(int64_t)k * N + n] * w[(int64_t)k * N + m] * r;
+        }
+    }
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double lh = lam[k] * 2.0 * fw / D[k];
+        const double l = fabs(lam[k] - lh);
+        L[(int64_t)k * I + i] = l;
+        s += l;
+    }
+    Eh[i] = s / K;
+}
+
+// ---------------------------------------------------------------------------
+// device allocation helpers
+// ---------------------------------------------------------------------------
+struct PlanBuilder {
+    m2nufft_plan_s* p;
+    size_t budget;
+    template <typename T>
+    m2_status alloc(T** out, size_t count) {
+        size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        if (budget && p->device_bytes + bytes > budget) {
+            set_error("plan needs more than mem_budget = %zu bytes of device memory", budget);
+            return M2_ERR_BUDGET;
+        }
+        void* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, bytes);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+            return M2_ERR_NOMEM;
+        }
+        p->allocations.push_back(d);
+        p->device_bytes += bytes;
+        *out = reinterpret_cast<T*>(d);
+        return M2_OK;
+    }
+    template <typename T>
+    m2_status upload(T** out, const std::vector<T>& h) {
+        M2_TRY(alloc(out, h.size()));
+        M2_CUDA_TRY(cudaMemcpy(*out, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+        return M2_OK;
+    }
+};
+
+void free_plan(m2nufft_plan_s* p) {
+    if (!p) return;
+    {
+        DeviceGuard guard(p->device);
+        cudaDeviceSynchronize();
+        for (void* d : p->allocations) cudaFree(d);
+        for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+        for (auto& kk : p->ev_rec)
+            for (auto& v : kk)
+                for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+    delete p;
+}
+
+// ---------------------------------------------------------------------------
+// GEP on the GPU (cuSOLVER, FP64)
+// ---------------------------------------------------------------------------
+m2_status solve_gep(const std::vector<double>& ts, double fmax, double fw, int K, size_t budget,
+                    std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds) {
+    const int N = (int)ts.size();
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t mat = (size_t)N * N;
+    double *dA = nullptr, *dB = nullptr, *dt = nullptr, *dW = nullptr, *work = nullptr;
+    int* dinfo = nullptr;
+    cusolverDnHandle_t h = nullptr;
+    m2_status st = M2_OK;
+    int lwork = 0, meig = 0, info = 0;
+    cusolverStatus_t cs;
+
+    auto fail = [&](m2_status s) {
+        st = s;
+    };
+    do {
+        if (budget && 2 * mat * sizeof(double) > budget) {
+            set_error("GEP needs %zu bytes for R(A0) and R(B), above mem_budget", 2 * mat * sizeof(double));
+            fail(M2_ERR_BUDGET);
+            break;
+        }
+        cudaError_t e;
+        if ((e = cudaMalloc(&dA, mat * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&dB, mat * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&dt, N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&dW, N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&dinfo, sizeof(int))) != cudaSuccess) {
+            set_error("GEP allocation failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_NOMEM);
+            break;
+        }
+        if ((e = cudaMemcpy(dt, ts.data(), N * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            set_error("GEP copy failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_CUDA);
+            break;
+        }
+        dim3 grid((N + 255) / 256, N);
+        gpss_matrices_kernel<<<grid, 256>>>(dt, N, fmax, fw, dA, dB);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            set_error("GPSS matrix kernel failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_CUDA);
+            break;
+        }
+        if ((cs = cusolverDnCreate(&h)) != CUSOLVER_STATUS_SUCCESS) {
+            set_error("cusolverDnCreate failed (%d)", (int)cs);
+            fail(M2_ERR_CUDA);
+            break;
+        }
+        cs = cusolverDnDsygvdx_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                          CUBLAS_FILL_MODE_LOWER, N, dA, N, dB, N, 0.0, 0.0, N - K + 1, N,
+                                          &meig, dW, &lwork);
+        if (cs != CUSOLVER_STATUS_SUCCESS) {
+            set_error("cusolverDnDsygvdx_bufferSize failed (%d)", (int)cs);
+            fail(M2_ERR_GEP);
+            break;
+        }
+        if (budget && (2 * mat + (size_t)lwork) * sizeof(double) > budget) {
+            set_error("GEP workspace exceeds mem_budget");
+            fail(M2_ERR_BUDGET);
+            break;
+        }
+        if ((e = cudaMalloc(&work, sizeof(double) * std::max(lwork, 1))) != cudaSuccess) {
+            set_error("GEP workspace allocation failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_NOMEM);
+            break;
+        }
+        cs = cusolverDnDsygvdx(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                               CUBLAS_FILL_MODE_LOWER, N, dA, N, dB, N, 0.0, 0.0, N - K + 1, N, &meig, dW,
+                               work, lwork, dinfo);
+        if (cs != CUSOLVER_STATUS_SUCCESS) {
+            set_error("cusolverDnDsygvdx failed (%d)", (int)cs);
+            fail(M2_ERR_GEP);
+            break;
+        }
+        if ((e = cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            set_error("GEP info copy failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_CUDA);
+            break;
+        }
+        if (info != 0) {
+            if (info > N)
+                set_error("R(B) is not positive definite in FP64 (cuSOLVER info %d): "
+                          "sampling times too close or repeated",
+                          info);
+            else
+                set_error("GEP did not converge (cuSOLVER info %d)", info);
+            fail(M2_ERR_GEP);
+            break;
+        }
+        if (meig != K) {
+            set_error("GEP returned %d eigenpairs, expected %d", meig, K);
+            fail(M2_ERR_GEP);
+            break;
+        }
+        std::vector<double> W(K), V((size_t)K * N);
+        if ((e = cudaMemcpy(W.data(), dW, K * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(V.data(), dA, (size_t)K * N * sizeof(double), cudaMemcpyDeviceToHost)) !=
+                cudaSuccess) {
+            set_error("GEP result copy failed: %s", cudaGetErrorString(e));
+            fail(M2_ERR_CUDA);
+            break;
+        }
+        // ascending -> descending; eigenvectors satisfy v^T R(B) v = 1, so scale by sqrt(2 f_w)
+        const double sc = std::sqrt(2.0 * fw);
+        lam.assign(K, 0.0);
+        w_sorted.assign((size_t)K * N, 0.0);
+        for (int k = 0; k < K; ++k) {
+            const int src = K - 1 - k;
+            lam[k] = W[src];
+            for (int n = 0; n < N; ++n) w_sorted[(size_t)k * N + n] = V[(size_t)src * N + n] * sc;
+        }
+    } while (0);
+    if (h) cusolverDnDestroy(h);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dt);
+    cudaFree(dW);
+    cudaFree(work);
+    cudaFree(dinfo);
+    cudaDeviceSynchronize();
+    seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+int ilog2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+template <typename R>
+m2_status upload_typed(PlanBuilder& pb, void** out, const std::vector<double>& h) {
+    std::vector<R> v(h.begin(), h.end());
+    R* d = nullptr;
+    M2_TRY(pb.upload(&d, v));
+    *out = d;
+    return M2_OK;
+}
+
+// complex table stored as interleaved (re, im) doubles -> precision-typed device copy
+m2_status upload_complex(PlanBuilder& pb, int precision, void** out, const std::vector<double>& h) {
+    return precision == 32 ? upload_typed<float>(pb, out, h) : upload_typed<double>(pb, out, h);
+}
+
+std::vector<double> unit_roots(int64_t count, int64_t n, int64_t step) {
+    // exp(-i 2 pi (q * step) / n), q < count
+    std::vector<double> v(2 * count);
+    for (int64_t q = 0; q < count; ++q) {
+        const int64_t a = (q * step) % n;
+        const double x = 2.0 * (double)a / (double)n;  // angle / pi, exact
+        v[2 * q] = std::cos(kPi * x);
+        v[2 * q + 1] = -std::sin(kPi * x);
+    }
+    return v;
+}
+
+#define M2_TRY_OR(expr)                   \
+    do {                                  \
+        m2_status s_ = (expr);            \
+        if (s_ != M2_OK) return bail(s_); \
+    } while (0)
+#define M2_CUDA_TRY_OR(expr)                                                                 \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return bail(e_ == cudaErrorMemoryAllocation ? M2_ERR_NOMEM : M2_ERR_CUDA);        \
+        }                                                                                    \
+    } while (0)
+
+m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
+                     const double* w_given, const double* lam_given, const m2_opts* opts_in,
+                     m2nufft_plan_t* out) {
+    if (!out) {
+        set_error("out is NULL");
+        return M2_ERR_ARG;
+    }
+    *out = nullptr;
+    m2_opts opts{};
+    opts.precision = 32;
+    if (opts_in) opts = *opts_in;
+    if (opts.precision != 32 && opts.precision != 64) {
+        set_error("precision must be 32 or 64");
+        return M2_ERR_ARG;
+    }
+    if (!t || N < 1 || N > (int64_t(1) << 30)) {
+        set_error("need t != NULL and 1 <= N <= 2^30");
+        return M2_ERR_ARG;
+    }
+    if (!(fs > 0) || !std::isfinite(fs)) {
+        set_error("fs must be positive and finite");
+        return M2_ERR_ARG;
+    }
+    const double fmax = 0.5 * fs;
+    if (!(f_w > 0) || !(f_w < fmax)) {
+        set_error("need 0 < f_w < fs/2");
+        return M2_ERR_ARG;
+    }
+    if (K < 1 || K > kMaxK || K > N) {
+        set_error("need 1 <= K <= min(N, %d)", kMaxK);
+        return M2_ERR_ARG;
+    }
+    if (!fc || fc->I < 1 || fc->I > (int64_t(1) << 23) || !(fc->df > 0) || !std::isfinite(fc->df) ||
+        !std::isfinite(fc->f_lo)) {
+        set_error("band grid needs 1 <= I <= 2^23, df > 0 and finite f_lo");
+        return M2_ERR_ARG;
+    }
+    for (int64_t n = 0; n < N; ++n) {
+        if (!std::isfinite(t[n])) {
+            set_error("sampling time %lld is not finite", (long long)n);
+            return M2_ERR_ARG;
+        }
+    }
+    if (w_given) {
+        for (int64_t q = 0; q < (int64_t)K * N; ++q)
+            if (!std::isfinite(w_given[q])) {
+                set_error("taper value %lld is not finite", (long long)q);
+                return M2_ERR_ARG;
+            }
+    }
+
+    int dev = opts.device;
+    if (dev < 0) M2_CUDA_TRY(cudaGetDevice(&dev));
+    DeviceGuard guard(dev);
+
+    auto* p = new m2nufft_plan_s();
+    p->device = dev;
+    p->precision = opts.precision;
+    p->fs = fs;
+    p->f_w = f_w;
+    p->tol = opts.tol > 0 ? opts.tol : (opts.precision == 32 ? 1e-6 : 1e-12);
+    p->t.assign(t, t + N);
+    PlanBuilder pb{p, opts.mem_budget};
+    auto bail = [&](m2_status s) {
+        free_plan(p);
+        return s;
+    };
+
+    // ---- sort ----
+    std::vector<int64_t> ord(N);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return t[a] < t[b]; });
+    std::vector<double> ts(N);
+    for (int64_t j = 0; j < N; ++j) ts[j] = t[ord[j]];
+    bool integer_grid = true;
+    for (int64_t j = 0; j < N; ++j) {
+        const double v = ts[j] * fs;
+        if (v != std::nearbyint(v) || std::fabs(v) > 9.0e15) {
+            integer_grid = false;
+            break;
+        }
+    }
+    p->integer_grid = integer_grid ? 1 : 0;
+
+    // ---- tapers ----
+    std::vector<double> w_sorted((size_t)K * N);
+    if (w_given) {
+        for (int k = 0; k < K; ++k)
+            for (int64_t j = 0; j < N; ++j) w_sorted[(size_t)k * N + j] = w_given[(size_t)k * N + ord[j]];
+        if (lam_given) {
+            p->lambda.assign(lam_given, lam_given + K);
+            p->have_lambda = 1;
+        }
+    } else {
+        for (int64_t j = 0; j + 1 < N; ++j)
+            if (ts[j] == ts[j + 1]) {
+                set_error("repeated sampling time %.17g: R(B) is singular", ts[j]);
+                return bail(M2_ERR_GEP);
+            }
+        if (N > 46340) {
+            set_error("GEP size N = %lld is above the dense solver limit (46340)", (long long)N);
+            return bail(M2_ERR_ARG);
+        }
+        std::vector<double> lam;
+        m2_status s = solve_gep(ts, fmax, f_w, K, opts.mem_budget, w_sorted, lam, p->gep_seconds);
+        if (s != M2_OK) return bail(s);
+        // sign: sum_n w_k(t_n) (t_n - tbar)^(k mod 2) > 0
+        double tbar = 0;
+        for (double v : ts) tbar += v;
+        tbar /= (double)N;
+        for (int k = 0; k < K; ++k) {
+            double sgn = 0;
+            for (int64_t j = 0; j < N; ++j) sgn += w_sorted[(size_t)k * N + j] * ((k & 1) ? (ts[j] - tbar) : 1.0);
+            if (sgn < 0)
+                for (int64_t j = 0; j < N; ++j) w_sorted[(size_t)k * N + j] = -w_sorted[(size_t)k * N + j];
+        }
+        p->lambda = lam;
+        p->have_lambda = 1;
+    }
+    p->w.assign((size_t)K * N, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int64_t j = 0; j < N; ++j) p->w[(size_t)k * N + ord[j]] = w_sorted[(size_t)k * N + j];
+
+    // ---- geometry ----
+    Geometry& g = p->g;
+    g.N = N;
+    g.K = K;
+    g.I = fc->I;
+    g.f_lo = fc->f_lo;
+    g.df = fc->df;
+    g.i_c = g.I / 2;
+    {
+        double pr, pe, s, se;
+        two_prod((double)g.i_c, g.df, pr, pe);
+        two_sum(g.f_lo, pr, s, se);
+        g.fmid_hi = s;
+        g.fmid_lo = se + pe;
+    }
+    double tmax_abs = 0;
+    for (double v : ts) tmax_abs = std::max(tmax_abs, std::fabs(v));
+    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < 1e-14 ? 1 : 0;
+    g.width = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
+    g.beta = 2.30 * g.width;
+    g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
+    g.log_nf = ilog2(g.nf);
+    g.log_n1 = g.log_nf / 2;
+    g.log_n2 = g.log_nf - g.log_n1;
+    g.n1 = int64_t(1) << g.log_n1;
+    g.n2 = int64_t(1) << g.log_n2;
+    const double s_cells = (double)g.nf * g.df;  // exact: nf is a power of two
+    g.h = 1.0 / s_cells;
+    const double span_cells = (ts.back() - ts.front()) * s_cells;
+    g.wrap = (span_cells + g.width + 2.0 >= (double)g.nf) ? 1 : 0;
+    const double half_w = 0.5 * g.width;
+    g.t_ref = g.wrap ? ts.front() : ts.front() - half_w * g.h;
+
+    struct Pt {
+        int64_t cell;
+        double off;
+        int64_t src;    // caller index
+        int64_t sidx;   // sorted index
+        double uh;
+    };
+    std::vector<Pt> pts(N);
+    const double nf_d = (double)g.nf;
+    for (int64_t j = 0; j < N; ++j) {
+        const double d = ts[j] - g.t_ref;
+        double uh, ul;
+        two_prod(d, s_cells, uh, ul);
+        if (g.wrap) uh -= std::floor(uh / nf_d) * nf_d;  // exact: nf is a power of two
+        const int64_t i0 = (int64_t)std::ceil(uh - half_w);
+        const double off = ((double)i0 - uh) - ul;
+        pts[j] = {i0, off, ord[j], j, uh};
+    }
+    if (g.wrap) {
+        std::stable_sort(pts.begin(), pts.end(), [](const Pt& a, const Pt& b) {
+            return a.cell < b.cell || (a.cell == b.cell && a.uh < b.uh);
+        });
+        std::vector<Pt> ext;
+        for (const Pt& q : pts)
+            if (q.cell + g.width > g.nf) {
+                Pt c = q;
+                c.cell -= g.nf;
+                ext.push_back(c);
+            }
+        for (const Pt& q : pts) ext.push_back(q);
+        for (const Pt& q : pts)
+            if (q.cell < 0) {
+                Pt c = q;
+                c.cell += g.nf;
+                ext.push_back(c);
+            }
+        pts.swap(ext);
+        g.rows = g.n1;
+    } else {
+        const int64_t last = pts.back().cell + g.width;  // one past the last written cell
+        g.rows = std::min<int64_t>(g.n1, (last + g.n2 - 1) / g.n2);
+    }
+    g.Lg = g.rows * g.n2;
+    g.P = (int64_t)pts.size();
+    g.ntiles = (g.Lg + kSpreadTile - 1) / kSpreadTile;
+    // CTA shapes of the FFT passes: at most 8192 (FP32) / 4096 (FP64) complex values in shared memory
+    const int64_t ecta = opts.precision == 32 ? 8192 : 4096;
+    g.cw = (int)std::max<int64_t>(1, std::min<int64_t>(g.n2, ecta / g.n1));
+    g.rw = (int)std::max<int64_t>(1, std::min<int64_t>(g.n1, ecta / g.n2));
+    const size_t csz = opts.precision == 32 ? 8 : 16;
+    {
+        // chunk so that the FFT workspace of a chunk stays well inside L2
+        const size_t z_per_signal = (size_t)K * g.nf * csz;
+        int64_t chunk = std::max<int64_t>(1, (int64_t)((48u << 20) / std::max<size_t>(z_per_signal, 1)));
+        chunk = std::min<int64_t>(chunk, 1024);
+        if (opts.max_batch > 0) chunk = std::min<int64_t>(chunk, opts.max_batch);
+        g.chunk = (int)chunk;
+    }
+    g.twb_bits = (g.log_nf + 1) / 2;
+
+    // ---- point arrays ----
+    {
+        std::vector<int32_t> src(g.P), cell(g.P);
+        std::vector<double> off(g.P);
+        for (int64_t q = 0; q < g.P; ++q) {
+            src[q] = (int32_t)pts[q].src;
+            cell[q] = (int32_t)pts[q].cell;
+            off[q] = pts[q].off;
+        }
+        M2_TRY_OR(pb.upload(&p->d_pt_src, src));
+        M2_TRY_OR(pb.upload(&p->d_pt_cell, cell));
+        if (opts.precision == 32) M2_TRY_OR(upload_typed<float>(pb, &p->d_pt_off, off));
+        else M2_TRY_OR(upload_typed<double>(pb, &p->d_pt_off, off));
+
+        // modulated tapers u_k(t_n) = w_k(t_n) exp(-i 2 pi f_mid t_n)
+        std::vector<double> tap;
+        if (g.real_taper) {
+            tap.resize((size_t)K * g.P);
+            for (int k = 0; k < K; ++k)
+                for (int64_t q = 0; q < g.P; ++q) tap[(size_t)k * g.P + q] = w_sorted[(size_t)k * N + pts[q].sidx];
+        } else {
+            tap.resize((size_t)2 * K * g.P);
+            for (int64_t q = 0; q < g.P; ++q) {
+                const double cyc = frac_cycles(g.fmid_hi, g.fmid_lo, ts[pts[q].sidx]);
+                const double c = std::cos(2.0 * kPi * cyc), s = std::sin(2.0 * kPi * cyc);
+                for (int k = 0; k < K; ++k) {
+                    const double wv = w_sorted[(size_t)k * N + pts[q].sidx];
+                    tap[2 * ((size_t)k * g.P + q)] = wv * c;
+                    tap[2 * ((size_t)k * g.P + q) + 1] = -wv * s;
+                }
+            }
+        }
+        if (opts.precision == 32) M2_TRY_OR(upload_typed<float>(pb, &p->d_taper, tap));
+        else M2_TRY_OR(upload_typed<double>(pb, &p->d_taper, tap));
+
+        // spreading tiles: points whose window [cell, cell + w) meets [c0, c1)
+        std::vector<int32_t> tpb(g.ntiles), tpe(g.ntiles);
+        for (int64_t j = 0; j < g.ntiles; ++j) {
+            const int64_t c0 = j * kSpreadTile, c1 = std::min<int64_t>(c0 + kSpreadTile, g.Lg);
+            auto lo = std::lower_bound(cell.begin(), cell.end(), (int32_t)(c0 - g.width + 1));
+            auto hi = std::lower_bound(cell.begin(), cell.end(), (int32_t)c1);
+            tpb[j] = (int32_t)(lo - cell.begin());
+            tpe[j] = (int32_t)(hi - cell.begin());
+        }
+        M2_TRY_OR(pb.upload(&p->d_tile_pb, tpb));
+        M2_TRY_OR(pb.upload(&p->d_tile_pe, tpe));
+    }
+
+    // ---- twiddles ----
+    M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1, unit_roots(g.n1 / 2, g.n1, 1)));
+    M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw2, unit_roots(g.n2 / 2, g.n2, 1)));
+    M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twa,
+                             unit_roots(g.nf >> g.twb_bits, g.nf, int64_t(1) << g.twb_bits)));
+    M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twb, unit_roots(int64_t(1) << g.twb_bits, g.nf, 1)));
+
+    // ---- deconvolution / re-phasing factors ----
+    {
+        const int Q = 200;
+        std::vector<double> gx, gw;
+        gauss_legendre(Q, gx, gw);
+        std::vector<double> zq(Q), pw(Q);
+        for (int q = 0; q < Q; ++q) {
+            const double z = 0.25 * g.width * (gx[q] + 1.0);  // [0, w/2]
+            const double a = 2.0 * z / g.width;
+            const double phi = std::exp(g.beta * (std::sqrt(std::max(0.0, 1.0 - a * a)) - 1.0));
+            zq[q] = z;
+            pw[q] = 0.25 * g.width * gw[q] * phi;
+        }
+        double *dz = nullptr, *dpw = nullptr;
+        M2_CUDA_TRY_OR(cudaMalloc(&dz, Q * sizeof(double)));
+        M2_CUDA_TRY_OR(cudaMalloc(&dpw, Q * sizeof(double)));
+        cudaMemcpy(dz, zq.data(), Q * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(dpw, pw.data(), Q * sizeof(double), cudaMemcpyHostToDevice);
+        double ah, al;
+        two_prod(g.df, g.t_ref, ah, al);
+        const unsigned blocks = (unsigned)((g.I + 255) / 256);
+        if (p->precision == 32) {
+            float2* d = nullptr;
+            M2_TRY_OR(pb.alloc(&d, g.I));
+            deconv_kernel<float2><<<blocks, 256>>>(g.I, g.i_c, 1.0 / nf_d, dz, dpw, Q, ah, al, d);
+            p->d_deconv = d;
+        } else {
+            double2* d = nullptr;
+            M2_TRY_OR(pb.alloc(&d, g.I));
+            deconv_kernel<double2><<<blocks, 256>>>(g.I, g.i_c, 1.0 / nf_d, dz, dpw, Q, ah, al, d);
+            p->d_deconv = d;
+        }
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(dz);
+        cudaFree(dpw);
+        if (e != cudaSuccess) {
+            set_error("deconvolution kernel failed: %s", cudaGetErrorString(e));
+            return bail(M2_ERR_CUDA);
+        }
+    }
+
+    // ---- leakage estimate (App. B) ----
+    M2_TRY_OR(pb.alloc(&p->d_Lhat, (size_t)K * g.I));
+    M2_TRY_OR(pb.alloc(&p->d_Ehat, (size_t)g.I));
+    if (p->have_lambda) {
+        const unsigned blocks = (unsigned)((g.I + 127) / 128);
+        if (integer_grid) {
+            std::vector<double> Lk(K);
+            for (int k = 0; k < K; ++k) {
+                double nrm = 0;
+                for (int64_t j = 0; j < N; ++j) nrm += w_sorted[(size_t)k * N + j] * w_sorted[(size_t)k * N + j];
+                Lk[k] = std::fabs(p->lambda[k] - p->lambda[k] * 2.0 * f_w / nrm);
+            }
+            double* dLk = nullptr;
+            M2_CUDA_TRY_OR(cudaMalloc(&dLk, K * sizeof(double)));
+            cudaMemcpy(dLk, Lk.data(), K * sizeof(double), cudaMemcpyHostToDevice);
+            leakage_const_kernel<<<blocks, 128>>>(K, g.I, dLk, p->d_Lhat, p->d_Ehat);
+            cudaError_t e = cudaDeviceSynchronize();
+            cudaFree(dLk);
+            if (e != cudaSuccess) {
+                set_error("leakage kernel failed: %s", cudaGetErrorString(e));
+                return bail(M2_ERR_CUDA);
+            }
+            p->have_leakage = 1;
+        } else if ((double)N * (double)N * (double)g.I <= 2.0e10) {
+            double tbar = 0;
+            for (double v : ts) tbar += v;
+            tbar /= (double)N;
+            std::vector<double> tc(N);
+            for (int64_t j = 0; j < N; ++j) tc[j] = ts[j] - tbar;
+            double *dtc = nullptr, *dw = nullptr, *dl = nullptr;
+            M2_CUDA_TRY_OR(cudaMalloc(&dtc, N * sizeof(double)));
+            M2_CUDA_TRY_OR(cudaMalloc(&dw, (size_t)K * N * sizeof(double)));
+            M2_CUDA_TRY_OR(cudaMalloc(&dl, K * sizeof(double)));
+            cudaMemcpy(dtc, tc.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+            cudaMemcpy(dw, w_sorted.data(), (size_t)K * N * sizeof(double), cudaMemcpyHostToDevice);
+            cudaMemcpy(dl, p->lambda.data(), K * sizeof(double), cudaMemcpyHostToDevice);
+            leakage_direct_kernel<<<blocks, 128>>>((int)N, K, g.I, dtc, dw, fmax, g.f_lo, g.df, dl, f_w,
+                                                    p->d_Lhat, p->d_Ehat);
+            cudaError_t e = cudaDeviceSynchronize();
+            cudaFree(dtc);
+            cudaFree(dw);
+            cudaFree(dl);
+            if (e != cudaSuccess) {
+                set_error("leakage kernel failed: %s", cudaGetErrorString(e));
+                return bail(M2_ERR_CUDA);
+            }
+            p->have_leakage = 1;
+        }
+    }
+
+    // ---- workspace ----
+    if (opts.precision == 32) {
+        float2 *dg = nullptr, *dZ = nullptr;
+        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * K * g.Lg));
+        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * K * g.nf));
+        p->d_g = dg;
+        p->d_Z = dZ;
+    } else {
+        double2 *dg = nullptr, *dZ = nullptr;
+        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * K * g.Lg));
+        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * K * g.nf));
+        p->d_g = dg;
+        p->d_Z = dZ;
+    }
+    M2_CUDA_TRY_OR(cudaDeviceSynchronize());
+    *out = p;
+    return M2_OK;
+}
+
+}  // namespace
+}  // namespace m2
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" m2_status m2nufft_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
+                                  const m2_opts* opts, m2nufft_plan_t* out) {
+    m2::clear_error();
+    return m2::build_plan(t, N, fs, f_w, K, fc, nullptr, nullptr, opts, out);
+}
+
+extern "C" m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double f_w, int K,
+                                              const m2_fgrid* fc, const double* w, const double* lambda,
+                                              const m2_opts* opts, m2nufft_plan_t* out) {
+    m2::clear_error();
+    if (!w) {
+        m2::set_error("w is NULL");
+        return M2_ERR_ARG;
+    }
+    return m2::build_plan(t, N, fs, f_w, K, fc, w, lambda, opts, out);
+}
+
+extern "C" m2_status m2nufft_get_tapers(m2nufft_plan_t p, double* w, double* lambda) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    if (w) std::memcpy(w, p->w.data(), sizeof(double) * p->w.size());
+    if (lambda) {
+        if (p->have_lambda) std::memcpy(lambda, p->lambda.data(), sizeof(double) * p->lambda.size());
+        else
+            for (int k = 0; k < p->g.K; ++k) lambda[k] = std::nan("");
+    }
+    return M2_OK;
+}
+
+extern "C" m2_status m2nufft_get_leakage(m2nufft_plan_t p, double* Lhat, double* Ehat) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    if ((Lhat || Ehat) && !p->have_leakage) {
+        m2::set_error("leakage estimate not available for this plan");
+        return M2_ERR_ARG;
+    }
+    m2::DeviceGuard guard(p->device);
+    if (Lhat) M2_CUDA_TRY(cudaMemcpy(Lhat, p->d_Lhat, sizeof(double) * p->g.K * p->g.I, cudaMemcpyDeviceToHost));
+    if (Ehat) M2_CUDA_TRY(cudaMemcpy(Ehat, p->d_Ehat, sizeof(double) * p->g.I, cudaMemcpyDeviceToHost));
+    return M2_OK;
+}
+
+extern "C" m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info) {
+    m2::clear_error();
+    if (!p || !info) {
+        m2::set_error("plan or info is NULL");
+        return M2_ERR_ARG;
+    }
+    const m2::Geometry& g = p->g;
+    info->N = g.N;
+    info->K = g.K;
+    info->I = g.I;
+    info->precision = p->precision;
+    info->width = g.width;
+    info->beta = g.beta;
+    info->nf = g.nf;
+    info->n1 = g.n1;
+    info->n2 = g.n2;
+    info->rows = g.rows;
+    info->wrap = g.wrap;
+    info->real_taper = g.real_taper;
+    info->integer_grid = p->integer_grid;
+    info->chunk = g.chunk;
+    info->device_bytes = p->device_bytes;
+    info->gep_seconds = p->gep_seconds;
+    return M2_OK;
+}
+
+extern "C" m2_status m2nufft_destroy(m2nufft_plan_t p) {
+    m2::clear_error();
+    m2::free_plan(p);
+    return M2_OK;
+}
+
+extern "C" const char* m2nufft_last_error(void) { return m2::g_last_error.c_str(); }
+
+extern "C" const char* m2nufft_version(void) { return "m2nufft-gb300 0.1 (sm_103a)"; }

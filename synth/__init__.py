@@ -40,6 +40,7 @@ __all__ = [
     "batched_uneven",
     "serving_patterns",
     "poisson_arrivals",
+    "taper_like",
 ]
 
 
@@ -246,3 +247,16 @@ def serving_patterns(n_patterns: int = 64, seed: int = 0, n_min: int = 2048,
 def poisson_arrivals(rate_hz: float, n: int, seed: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process."""
     return np.cumsum(_rng(seed).exponential(1.0 / rate_hz, n))
+
+
+def taper_like(K: int, N: int, seed: int) -> np.ndarray:
+    """Arbitrary real taper-shaped rows [K, N] (sine windows times cosines
+    plus 1% noise, scaled like unit-energy tapers).  Used as inputs where
+    the dense GEP would be too slow to run beside the check: the
+    eigencoefficient sum is linear in the taper, so any real sequence is a
+    valid input to it."""
+    rng = _rng(seed)
+    n = np.arange(N)
+    base = np.sin(np.pi * (n + 0.5) / N)
+    return np.stack([base * np.cos(np.pi * k * (n + 0.5) / N) + 0.01 * rng.standard_normal(N)
+                     for k in range(K)]) * np.sqrt(2.0 / N)

@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+J_k(A_i) and P-hat are compared element by element (relative l2 over the
+array, Eq. eigencoefficients / Eq. power_spectrum_estimator): <= 1e-5 for
+the FP32 path and <= 1e-10 for the FP64 path.  Where the oracle's dense GEP
+is cheap, the tapers come from the oracle and are handed to the GPU plan
+(m2nufft_plan_with_tapers), so J is compared with identical tapers; the
+GPU's own GEP is checked separately (eigenvalues, subspace, residuals) and
+through P-hat, which depends only on the span of the tapers.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import estimator as oest
+from oracle import gpss as ogpss
+from oracle import leakage as oleak
+from tests._util import TOL, rel_l2, sample_bands, seeded_tapers
+
+torch = pytest.importorskip("torch")
+pkg = pytest.importorskip("paper_2407_01943_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    d = torch.device("cuda:0")
+    torch.cuda.set_device(d)
+    return d
+
+
+def run_plan(plan, x, dev, want=("J", "E", "P")):
+    xt = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32 if plan.precision == 32 else np.float64)).to(dev)
+    out = plan.run(xt, want=want)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def oracle_all(t, X, w, f_lo, df, I, idx=None):
+    Js, Ps = [], []
+    for b in range(X.shape[0]):
+        J, E, P = oest.m2nufft(t, X[b], w, f_lo, df, I, idx)
+        Js.append(J)
+        Ps.append(P)
+    return np.stack(Js), np.stack(Ps)
+
+
+# ---------------------------------------------------------------------------
+# full-array parity at oracle-friendly sizes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [64, 32])
+def test_grid1024_full_parity(dev, prec):
+    """N=1024 grid with 20% Bernoulli missing, 3 tones + noise, K=6, I=1024."""
+    wl = synth.workload("grid1024", batch=3)
+    w, lam = ogpss.nominal_tapers(wl.t, wl.fs, wl.f_w, wl.K)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=prec, tapers=w, lam=lam)
+    out = run_plan(plan, wl.x, dev)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I)
+    assert rel_l2(out["J"], Jr) <= TOL[prec]
+    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    assert rel_l2(out["E"], np.abs(Jr) ** 2) <= TOL[prec]
+    assert plan.info["wrap"] == 1  # span ~ period: wrap-around spreading
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_jittered_medium_full_parity(dev, prec):
+    """Jittered N=2048 (+-0.4), AR(4)-like tones, K=8, I=2^14: zero-padded
+    grid (support 1/8 of the period) spanning many tiles and FFT rows."""
+    t = synth.jittered(2048, 0.4, 21)
+    X = np.stack([synth.tones(t, (0.1, 0.31), (2.0, 1.0), 1.0, 30 + b) for b in range(2)])
+    K, fw, I = 8, 5.0 / 2048, 1 << 14
+    w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=prec, tapers=w, lam=lam)
+    out = run_plan(plan, X, dev)
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
+    assert plan.info["wrap"] == 0 and plan.info["rows"] < plan.info["n1"]
+    assert rel_l2(out["J"], Jr) <= TOL[prec]
+    assert rel_l2(out["P"], Pr) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_general_band_grid_complex_taper(dev, prec):
+    """Band grid not centred on 0 (f_lo = 0.013, df = 0.37/1000, I = 1000, odd
+    offsets): the modulated taper is complex; large time offset 1e5."""
+    t = 1.0e5 + synth.jittered(700, 0.3, 4)
+    x = synth.tones(t, (0.05, 0.2), (1.0, 1.0), 0.5, 5)[None, :]
+    K, fw = 4, 4.0 / 700
+    w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
+    f_lo, df, I = 0.013, 0.37 / 1000, 1000
+    plan = pkg.Plan(t, 1.0, fw, K, f_lo, df, I, precision=prec, tapers=w, lam=lam)
+    assert plan.info["real_taper"] == 0
+    out = run_plan(plan, x, dev)
+    Jr, Pr = oracle_all(t, x, w, f_lo, df, I)
+    assert rel_l2(out["J"], Jr) <= TOL[prec]
+    assert rel_l2(out["P"], Pr) <= TOL[prec]
+
+
+@pytest.mark.parametrize("I", [1, 2, 7, 63, 65, 1023])
+def test_small_and_odd_band_counts(dev, I):
+    """Degenerate and ragged grids: I = 1, 2, odd, just below/above a power of two."""
+    t = synth.jittered(90, 0.4, 8)
+    x = synth.white(t, 1.0, 9)[None, :]
+    w = seeded_tapers(3, 90, 1)
+    plan = pkg.Plan(t, 1.0, 0.03, 3, -0.45, 0.9 / max(I, 1), I, precision=64, tapers=w)
+    out = run_plan(plan, x, dev)
+    Jr, Pr = oracle_all(t, x, w, -0.45, 0.9 / max(I, 1), I)
+    assert rel_l2(out["J"], Jr) <= TOL[64]
+    assert rel_l2(out["P"], Pr) <= TOL[64]
+
+
+def test_single_sample_single_taper(dev):
+    """N = 1, K = 1: J(f) = w x exp(-i 2 pi f t) exactly."""
+    t = np.array([3.25])
+    plan = pkg.Plan(t, 1.0, 0.1, 1, -0.5, 1.0 / 64, 64, precision=64, tapers=np.array([[0.7]]))
+    out = run_plan(plan, np.array([[2.0]]), dev)
+    f = -0.5 + np.arange(64) / 64
+    np.testing.assert_allclose(out["J"][0, 0], 1.4 * np.exp(-2j * np.pi * f * 3.25), rtol=1e-11, atol=1e-12)
+
+
+def test_many_chunks_and_empty_batch(dev):
+    """B larger than the internal chunk (max_batch=2, B=5) gives the same
+    result per signal; B = 0 is a no-op."""
+    t = synth.jittered(300, 0.4, 3)
+    X = np.stack([synth.white(t, 1.0, 40 + b) for b in range(5)])
+    w = seeded_tapers(4, 300, 2)
+    plan = pkg.Plan(t, 1.0, 0.02, 4, -0.5, 1 / 512, 512, precision=64, tapers=w, max_batch=2)
+    assert plan.info["chunk"] == 2
+    out = run_plan(plan, X, dev)
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1 / 512, 512)
+    assert rel_l2(out["J"], Jr) <= TOL[64]
+    xe = torch.zeros((0, 300), dtype=torch.float64, device=dev)
+    plan.run(xe)
+    torch.cuda.synchronize()
+
+
+def test_batch_equals_alone_bitwise(dev):
+    """Deterministic kernels: a signal gives bit-identical J and P-hat alone
+    and inside a batch (no atomics, fixed summation order)."""
+    t = synth.jittered(1500, 0.4, 13)
+    X = np.stack([synth.white(t, 1.0, 60 + b) for b in range(4)])
+    w = seeded_tapers(6, 1500, 3)
+    plan = pkg.Plan(t, 1.0, 0.004, 6, -0.5, 1 / 8192, 8192, precision=32, tapers=w)
+    allb = run_plan(plan, X, dev)
+    one = run_plan(plan, X[2:3], dev)
+    assert np.array_equal(allb["J"][2], one["J"][0])
+    assert np.array_equal(allb["P"][2], one["P"][0])
+
+
+# ---------------------------------------------------------------------------
+# the GPU GEP (cuSOLVER FP64) against LAPACK
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["grid", "jitter"])
+def test_gep_matches_lapack(dev, kind):
+    if kind == "grid":
+        wl = synth.workload("grid1024")
+        t, fw, K, x = wl.t, wl.f_w, wl.K, wl.x
+    else:
+        t = synth.jittered(1200, 0.4, 17)
+        fw, K = 5.0 / 1200, 8
+        x = synth.tones(t, (0.2,), (1.0,), 1.0, 3)[None, :]
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1 / 2048, 2048, precision=64)
+    wg, lg = plan.tapers()
+    wo, lo = ogpss.nominal_tapers(t, 1.0, fw, K)
+    np.testing.assert_allclose(lg, lo, atol=1e-12)
+    RB = ogpss.gpss_matrix_b(t, 0.5)
+    RA = ogpss.gpss_matrix_a(t, fw)
+    np.testing.assert_allclose(wg @ RB @ wg.T, 2 * fw * np.eye(K), atol=1e-11)
+    res = RA @ wg.T - (RB @ wg.T) * lg[None, :]
+    assert np.linalg.norm(res) / (np.linalg.norm(RA) * np.linalg.norm(wg)) < 1e-12
+    # same K-dimensional subspace (projector), independent of rotations inside it
+    Pg = wg.T @ wg @ RB / (2 * fw)
+    Po = wo.T @ wo @ RB / (2 * fw)
+    assert np.max(np.abs(Pg - Po)) < 1e-8
+    # P-hat depends only on the span: GPU-GEP plan vs oracle tapers
+    out = run_plan(plan, x, dev, want=("P",))
+    _, Pr = oracle_all(t, x, wo, -0.5, 1 / 2048, 2048)
+    assert rel_l2(out["P"], Pr) <= 1e-9
+
+
+def test_gep_errors_are_reported(dev):
+    t = np.array([0.0, 1.0, 1.0, 2.0, 3.0])
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.Plan(t, 1.0, 0.1, 2, -0.5, 0.1, 10, precision=64)
+    assert e.value.status == 4  # M2_ERR_GEP (repeated time => R(B) singular)
+    # repeated times are fine with given tapers
+    pkg.Plan(t, 1.0, 0.1, 2, -0.5, 0.1, 10, precision=64, tapers=np.ones((2, 5)) * 0.1).close()
+    for bad in [dict(K=6), dict(f_w=0.5), dict(f_w=0.0)]:
+        kw = dict(K=2, f_w=0.1)
+        kw.update(bad)
+        with pytest.raises(pkg.M2Error) as e:
+            pkg.Plan(np.arange(5.0), 1.0, kw["f_w"], kw["K"], -0.5, 0.1, 10)
+        assert e.value.status == 1
+    with pytest.raises(pkg.M2Error):
+        pkg.Plan(np.array([0.0, np.nan, 2.0]), 1.0, 0.1, 1, -0.5, 0.1, 10)
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.Plan(np.arange(64.0), 1.0, 0.05, 2, -0.5, 1 / 64, 64, mem_budget=1000)
+    assert e.value.status == 3  # M2_ERR_BUDGET
+
+
+# ---------------------------------------------------------------------------
+# leakage estimate (App. B)
+# ---------------------------------------------------------------------------
+def test_leakage_integer_grid_is_zero(dev):
+    wl = synth.workload("grid1024")
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=64)
+    L, E = plan.leakage()
+    assert np.max(L) < 1e-12 and np.max(E) < 1e-12
+    out = run_plan(plan, wl.x, dev, want=("Lhat", "Ehat"))
+    np.testing.assert_array_equal(out["Lhat"], L)
+
+
+def test_leakage_rate_mismatch_matches_oracle(dev):
+    """t_n = 5n/6 with 10 of 60 dropped (Sec. 4 missing-data scheme):
+    identical tapers, every band."""
+    t = synth.scaled_missing(60, 10, 5.0 / 6.0, 0)
+    fw, K, I = 0.05, 4, 200
+    w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1 / I, I, precision=64, tapers=w, lam=lam)
+    L, E = plan.leakage()
+    Lr, Er = oleak.leakage_at(t, w, lam, 1.0, fw, -0.5 + np.arange(I) / I)
+    np.testing.assert_allclose(L, Lr, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(E, Er, rtol=1e-9, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads (sampled outputs)
+# ---------------------------------------------------------------------------
+def test_jitter16k_full_size_fp32(dev):
+    """N = 16384 jittered, K = 8, I = 2^18 (the benchmark workload): FP32
+    path with FP64-split coordinates against the direct FP64 sum on sampled
+    band centres; seeded tapers (any real taper is a valid input)."""
+    wl = synth.workload("jitter16k", batch=2)
+    w = seeded_tapers(wl.K, wl.N, 7)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w)
+    out = run_plan(plan, wl.x, dev)
+    idx = sample_bands(wl.I, 384, 1)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
+    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+    # P-hat is the taper average of the eigenspectra everywhere
+    np.testing.assert_allclose(out["P"], out["E"].mean(axis=1), rtol=2e-6, atol=1e-30)
+
+
+def test_jitter16k_gep_on_gpu(dev):
+    """The full-size GEP (N = 16384, FP64 cuSOLVER): eigenvalues in (0,1)
+    descending, R(B)-orthonormal tapers and small residuals on sampled rows."""
+    wl = synth.workload("jitter16k")
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32)
+    w, lam = plan.tapers()
+    assert np.all((lam > 0) & (lam < 1)) and np.all(np.diff(lam) <= 0)
+    rows = np.random.default_rng(0).choice(wl.N, 48, replace=False)
+    RBr = ogpss.gpss_rows(wl.t, rows, 0.5)
+    RAr = ogpss.gpss_rows(wl.t, rows, wl.f_w)
+    res = RAr @ w.T - (RBr @ w.T) * lam[None, :]
+    scale = np.abs(RBr @ w.T).max()
+    assert np.max(np.abs(res)) < 1e-9 * scale
+    # R(B)-orthonormality at full size, R(B) w^T formed block by block
+    RBw = np.zeros((wl.N, wl.K))
+    for r0 in range(0, wl.N, 1024):
+        blk = np.arange(r0, min(r0 + 1024, wl.N))
+        RBw[blk] = ogpss.gpss_rows(wl.t, blk, 0.5) @ w.T
+    np.testing.assert_allclose(w @ RBw, 2 * wl.f_w * np.eye(wl.K), atol=1e-10)
+
+
+def test_periodic16k_full_size_fp32(dev):
+    """N = 16384 grid, blocks of 8 drop 2 (12288 kept), K = 10, I = 2^20."""
+    wl = synth.workload("periodic16k")
+    w = seeded_tapers(wl.K, wl.N, 9)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w)
+    out = run_plan(plan, wl.x, dev)
+    idx = sample_bands(wl.I, 256, 2)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
+    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+
+
+def test_jitter16k_fp64_path(dev):
+    wl = synth.workload("jitter16k")
+    w = seeded_tapers(wl.K, wl.N, 5)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=64, tapers=w)
+    out = run_plan(plan, wl.x, dev, want=("J", "P"))
+    idx = sample_bands(wl.I, 128, 3)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[64]
+    assert rel_l2(out["P"][:, idx], Pr) <= TOL[64]
+
+
+def test_exec_batch_uneven_matches_single(dev):
+    """m2nufft_exec_batch over signals with different plans equals
+    per-signal exec bit for bit."""
+    ws = synth.batched_uneven(4, seed=3, n_min=256, n_max=1500)
+    plans, xs, Js, Ps = [], [], [], []
+    for s, wl in enumerate(ws):
+        p = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                     tapers=seeded_tapers(wl.K, wl.N, s))
+        plans.append(p)
+        xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
+        Js.append(torch.empty((wl.K, wl.I), dtype=torch.complex64, device=dev))
+        Ps.append(torch.empty((wl.I,), dtype=torch.float32, device=dev))
+    pkg.exec_batch(plans, xs, Js, None, Ps)
+    torch.cuda.synchronize()
+    for p, x, J, P in zip(plans, xs, Js, Ps):
+        single = p.run(x[None, :], want=("J", "P"))
+        torch.cuda.synchronize()
+        assert torch.equal(single["J"][0], J) and torch.equal(single["P"][0], P)

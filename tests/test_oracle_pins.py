@@ -325,3 +325,10 @@ def test_lambda_hat_is_rayleigh_quotient_of_shifted_taper():
             v = w[k] * np.exp(2j * np.pi * f * t)
             lam_hat = np.real(np.conj(v) @ RAi @ v) / np.real(np.conj(v) @ RB @ v)
             np.testing.assert_allclose(L[k, j], abs(lam[k] - lam_hat), rtol=1e-9, atol=1e-13)
+
+
+def test_gpss_rows_match_full_matrix():
+    t = synth.jittered(70, 0.4, 12)
+    rows = np.array([0, 5, 33, 69])
+    np.testing.assert_array_equal(ogpss.gpss_rows(t, rows, 0.5), ogpss.gpss_matrix_b(t, 0.5)[rows])
+    np.testing.assert_array_equal(ogpss.gpss_rows(t, rows, 0.07), ogpss.gpss_matrix_a(t, 0.07)[rows])
