@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--skip-gep", action="store_true",
+                    help="plan from taper-shaped inputs instead of the FP64 GEP (profiling runs; "
+                         "the exec kernels and their shapes are identical)")
     return ap.parse_args()
 
 
@@ -225,7 +228,11 @@ def run_ours(args):
     csz, rsz = (8, 4) if args.precision == 32 else (16, 8)
 
     t_plan = time.perf_counter()
-    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local)
+    if args.skip_gep:
+        plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local,
+                        tapers=synth.taper_like(wl.K, wl.N, 0))
+    else:
+        plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local)
     t_plan = time.perf_counter() - t_plan
     info = plan.info
 
