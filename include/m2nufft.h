@@ -88,6 +88,9 @@ typedef struct {
                            (including GEP scratch); 0 = unlimited */
     int device;         /* CUDA device ordinal; < 0 = the caller's current device */
     int max_batch;      /* signals processed per internal chunk; <= 0 = automatic */
+    int path;           /* exec kernels: 0 = automatic, 1 = generic (any precision/grid),
+                           2 = packed FP32 path (real tapers, nf >= 2048, support <= 64 rows
+                           of 1024 cells; M2_ERR_ARG if the plan does not qualify) */
 } m2_opts;
 
 /* Geometry of a plan, for callers that size buffers or compute rooflines. */
@@ -105,6 +108,7 @@ typedef struct {
     int real_taper;      /* 1 when the modulated tapers are real (f_lo + (I/2) df == 0) */
     int integer_grid;    /* 1 when fs * t_n are all integers, so R(B) = I */
     int chunk;           /* signals per internal chunk */
+    int path;            /* exec kernels in use: 1 = generic, 2 = packed FP32 */
     size_t device_bytes; /* device memory held by the plan */
     double gep_seconds;  /* wall time of the GEP during planning (0 if tapers were given) */
 } m2_info;

@@ -33,7 +33,7 @@ class m2_fgrid(ctypes.Structure):
 
 class m2_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
-                ("device", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("path", ctypes.c_int)]
 
 
 class m2_info(ctypes.Structure):
@@ -41,6 +41,7 @@ class m2_info(ctypes.Structure):
                 ("width", ctypes.c_int), ("beta", ctypes.c_double), ("nf", ctypes.c_int64),
                 ("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("rows", ctypes.c_int64), ("wrap", ctypes.c_int),
                 ("real_taper", ctypes.c_int), ("integer_grid", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("path", ctypes.c_int),
                 ("device_bytes", ctypes.c_size_t), ("gep_seconds", ctypes.c_double)]
 
 
@@ -126,7 +127,7 @@ class Plan:
 
     def __init__(self, t, fs: float, f_w: float, K: int, f_lo: float, df: float, I: int,
                  precision: int = 32, tol: float = 0.0, mem_budget: int = 0, device: int = -1,
-                 max_batch: int = 0, tapers=None, lam=None):
+                 max_batch: int = 0, tapers=None, lam=None, path: int = 0):
         L = load()
         self._t = np.ascontiguousarray(t, dtype=np.float64)
         self.N = int(self._t.shape[0])
@@ -135,7 +136,7 @@ class Plan:
         self.precision = int(precision)
         self.fs, self.f_w, self.f_lo, self.df = float(fs), float(f_w), float(f_lo), float(df)
         fg = m2_fgrid(self.f_lo, self.df, self.I)
-        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch))
+        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path))
         h = _VP()
         if tapers is None:
             st = L.m2nufft_plan(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(fg),

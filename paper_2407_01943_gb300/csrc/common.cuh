@@ -69,8 +69,21 @@ struct Geometry {
     int rw = 0;           // rows per CTA in the row pass
     int chunk = 1;        // signals per chunk
     int twb_bits = 0;     // low-bit width of the two-level nf twiddle table
+    int path = 1;         // 1 = generic kernels, 2 = packed FP32 kernels
+    int kp = 0;           // FFT signals per signal: K (generic) or ceil(K/2) taper pairs (packed)
 };
 
+}  // namespace m2
+
+struct m2nufft_plan_s;
+
+namespace m2 {
+// Instrumentation: records a CUDA event (begin = 0 / end = 1) around kernel `kernel`
+// on stream `st` while timing is enabled for the plan.
+void mark(m2nufft_plan_s* p, int kernel, int which, cudaStream_t st);
+// Packed FP32 path (fast.cu): one chunk of nb signals.
+m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P,
+                          cudaStream_t st);
 }  // namespace m2
 
 struct m2nufft_plan_s {
@@ -100,6 +113,8 @@ struct m2nufft_plan_s {
     void* d_tw2 = nullptr;         // [n2/2] C: exp(-i 2 pi q / n2)
     void* d_twa = nullptr;         // [nf >> twb_bits] C: exp(-i 2 pi (q << twb_bits) / nf)
     void* d_twb = nullptr;         // [1 << twb_bits]  C: exp(-i 2 pi q / nf)
+    void* d_twn1 = nullptr;        // packed path: [n1] C, exp(-i 2 pi q / n1) full circle
+    void* d_tw1024 = nullptr;      // packed path: [1024] C, exp(-i 2 pi q / 1024) full circle
     double* d_Lhat = nullptr;      // [K][I]
     double* d_Ehat = nullptr;      // [I]
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C

@@ -333,25 +333,6 @@ m2_status launch_spread_k(const m2nufft_plan_s* p, const R* x, int nb, cudaStrea
     return launch_spread<R, CPLX, 16>(p, x, nb, st);
 }
 
-// Instrumentation: record an event on the launching stream before / after a kernel.
-cudaEvent_t take_event(m2nufft_plan_s* p) {
-    cudaEvent_t e = nullptr;
-    if (!p->ev_pool.empty()) {
-        e = p->ev_pool.back();
-        p->ev_pool.pop_back();
-    } else if (cudaEventCreate(&e) != cudaSuccess) {
-        e = nullptr;
-    }
-    return e;
-}
-inline void mark(m2nufft_plan_s* p, int kernel, int which, cudaStream_t st) {
-    if (!p->timing) return;
-    cudaEvent_t e = take_event(p);
-    if (!e) return;
-    cudaEventRecord(e, st);
-    p->ev_rec[kernel][which].push_back(e);
-}
-
 template <typename R>
 m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J, R* E, R* P,
                      cudaStream_t st) {
@@ -404,8 +385,16 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     R* P = reinterpret_cast<R*>(Pv);
     for (int64_t b0 = 0; b0 < B; b0 += g.chunk) {
         const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
-        M2_TRY(exec_chunk<R>(p, x + b0 * g.N, nb, J ? J + b0 * g.K * g.I : nullptr,
-                             E ? E + b0 * g.K * g.I : nullptr, P ? P + b0 * g.I : nullptr, st));
+        C* Jc = J ? J + b0 * g.K * g.I : nullptr;
+        R* Ec = E ? E + b0 * g.K * g.I : nullptr;
+        R* Pc = P ? P + b0 * g.I : nullptr;
+        if constexpr (std::is_same<R, float>::value) {
+            if (g.path == 2) {
+                M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, Jc, Ec, Pc, st));
+                continue;
+            }
+        }
+        M2_TRY(exec_chunk<R>(p, x + b0 * g.N, nb, Jc, Ec, Pc, st));
     }
     return M2_OK;
 }
@@ -451,6 +440,26 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
 }
 
 }  // namespace
+
+cudaEvent_t take_event(m2nufft_plan_s* p) {
+    cudaEvent_t e = nullptr;
+    if (!p->ev_pool.empty()) {
+        e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+void mark(m2nufft_plan_s* p, int kernel, int which, cudaStream_t st) {
+    if (!p->timing) return;
+    cudaEvent_t e = take_event(p);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    p->ev_rec[kernel][which].push_back(e);
+}
+
 }  // namespace m2
 
 extern "C" m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P,

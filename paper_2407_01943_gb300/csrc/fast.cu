@@ -1,0 +1,408 @@
+// Packed FP32 exec path (real tapers, nf = n1 * 1024, support <= 64 rows).
+//
+// Same mathematics as the generic path in exec.cu (Sec. 3.2, Eq.
+// eigencoefficients and Eq. power_spectrum_estimator evaluated by a type-1
+// nonuniform FFT), organised for throughput:
+//
+//   * two real tapers share one complex FFT: the spread grid of taper pair j
+//     is g_{2j} + i g_{2j+1}; since both grids are real, their transforms are
+//     recovered from the packed transform Zp at k and nf - k:
+//         X_{2j}[k]   = (Zp[k] + conj(Zp[nf-k])) / 2
+//         X_{2j+1}[k] = (Zp[k] - conj(Zp[nf-k])) / (2i)
+//     which halves the FFT work and the L2-resident workspace;
+//   * the column DFTs (length n1, only `rows` nonzero inputs) are evaluated per
+//     coset k1 = r + C q (C = n1/F, F = min(n1, 32)): the inputs are folded
+//     modulo F with the twiddle W_n1^{l1 r} and one F-point FFT runs in
+//     registers, one column per lane, so loads and stores are 256-byte rows;
+//   * the 1024-point row DFTs run one per warp as 32 x 32 in registers with a
+//     single padded shared-memory transpose;
+//   * the epilogue pairs each row k1 with its mirror n1 - k1 inside the CTA,
+//     unpacks, deconvolves, writes J and |J|^2 with streaming stores, and sums
+//     P-hat over all taper pairs in registers (no atomics).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace m2 {
+namespace {
+
+constexpr int kRowLen = 1024;     // n2 of the packed path
+constexpr int kRowPad = 33 * 32;  // per-warp transpose / row buffer (padded 32 x 33)
+constexpr int kRowsR = 4;         // low rows per CTA of the row pass (plus as many mirror rows)
+constexpr int kColWarps = 4;      // warps per CTA of the column pass
+
+struct Tw32 {
+    float2 w[16];  // exp(-i 2 pi e / 32), e < 16
+};
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__host__ __device__ constexpr int brev(int v, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+// In-register radix-2 decimation-in-frequency FFT of length N <= 32 (natural
+// input, bit-reversed output): v[q] holds X[brev(q)].
+template <int N>
+__device__ __forceinline__ void fft_reg(float2 (&v)[N], const Tw32& tw) {
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2) {
+#pragma unroll
+        for (int blk = 0; blk < N; blk += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const float2 a = v[blk + j], b = v[blk + j + h];
+                v[blk + j] = make_float2(a.x + b.x, a.y + b.y);
+                const float2 d = make_float2(a.x - b.x, a.y - b.y);
+                const int e = j * (32 / (2 * h));
+                if (e == 0) v[blk + j + h] = d;
+                else if (e == 8) v[blk + j + h] = make_float2(d.y, -d.x);
+                else v[blk + j + h] = cmulf(d, tw.w[e]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spread (packed): gp[b][j][c] = sum_n (u_{2j}[n] + i u_{2j+1}[n]) x_b[n] phi(c - u_n)
+// ---------------------------------------------------------------------------
+template <int KP>
+__global__ void __launch_bounds__(kSpreadTile)
+spread_packed_kernel(const float* __restrict__ x, int64_t N, const int32_t* __restrict__ pt_src,
+                     const int32_t* __restrict__ pt_cell, const float* __restrict__ pt_off,
+                     const float* __restrict__ taper, int64_t P, const int32_t* __restrict__ tile_pb,
+                     const int32_t* __restrict__ tile_pe, int K, int Kp, int w, float two_over_w, float beta,
+                     int64_t Lg, float2* __restrict__ g) {
+    __shared__ int32_t s_cell[kSpreadChunk];
+    __shared__ float s_off[kSpreadChunk];
+    __shared__ float2 s_val[KP][kSpreadChunk];
+    const int tile = blockIdx.x;
+    const int b = blockIdx.y;
+    const int64_t c = (int64_t)tile * kSpreadTile + threadIdx.x;
+    const int pb = tile_pb[tile], pe = tile_pe[tile];
+    const float* xb = x + (int64_t)b * N;
+    float2 acc[KP];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
+        const int n = min(kSpreadChunk, pe - q0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int p = q0 + t;
+            s_cell[t] = pt_cell[p];
+            s_off[t] = pt_off[p];
+            const float xv = xb[pt_src[p]];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                float2 v = make_float2(0.f, 0.f);
+                if (2 * j < K) v.x = taper[(int64_t)(2 * j) * P + p] * xv;
+                if (2 * j + 1 < K) v.y = taper[(int64_t)(2 * j + 1) * P + p] * xv;
+                s_val[j][t] = v;
+            }
+        }
+        __syncthreads();
+        if (c < Lg) {
+            const int ci = (int)c;
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cell[mid] + w <= ci) lo = mid + 1; else hi = mid;
+            }
+            for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
+                const float z = s_off[t] + (float)(ci - s_cell[t]);
+                const float a = z * two_over_w;
+                const float phi = expf(beta * (sqrtf(fmaxf(0.f, 1.f - a * a)) - 1.f));
+#pragma unroll
+                for (int j = 0; j < KP; ++j) {
+                    acc[j].x += s_val[j][t].x * phi;
+                    acc[j].y += s_val[j][t].y * phi;
+                }
+            }
+        }
+    }
+    if (c < Lg) {
+#pragma unroll
+        for (int j = 0; j < KP; ++j)
+            if (j < Kp) g[((int64_t)b * Kp + j) * Lg + c] = acc[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// column pass: Z[b][j][k1][l2] = W_nf^{l2 k1} sum_{l1 < rows} gp[b][j][l1 n2 + l2] W_n1^{l1 k1}
+// CTA = 32 columns x all cosets; lane = column; F-point FFT per coset in registers.
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(32 * kColWarps)
+cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, int Kp,
+                 const float2* __restrict__ tw_n1 /*[n1] full circle*/, const float2* __restrict__ twa,
+                 const float2* __restrict__ twb, int twb_bits, int twa_len, Tw32 tw, float2* __restrict__ Z) {
+    extern __shared__ float2 smem_f2[];
+    float2* s_in = smem_f2;                     // [rows][32]
+    float2* s_tw = s_in + rows * 32;            // [n1]
+    float2* s_twb = s_tw + n1;                  // [1 << twb_bits]
+    float2* s_twa = s_twb + (1 << twb_bits);    // [twa_len]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int l2 = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    const int64_t n2 = kRowLen;
+    const float2* gj = gp + ((int64_t)b * Kp + j) * Lg;
+    float2* Zj = Z + ((int64_t)b * Kp + j) * (int64_t)n1 * n2;
+
+    for (int l1 = warp; l1 < rows; l1 += kColWarps) s_in[l1 * 32 + lane] = gj[(int64_t)l1 * n2 + l2];
+    for (int q = threadIdx.x; q < n1; q += blockDim.x) s_tw[q] = tw_n1[q];
+    for (int q = threadIdx.x; q < (1 << twb_bits); q += blockDim.x) s_twb[q] = twb[q];
+    for (int q = threadIdx.x; q < twa_len; q += blockDim.x) s_twa[q] = twa[q];
+    __syncthreads();
+
+    const int C = n1 / F;
+    const int mask = (1 << twb_bits) - 1;
+    const int nfold = (rows + F - 1) / F;
+    for (int r = warp; r < C; r += kColWarps) {
+        float2 v[F];
+#pragma unroll
+        for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
+        for (int f = 0; f < nfold; ++f) {
+#pragma unroll
+            for (int q = 0; q < F; ++q) {
+                const int l1 = f * F + q;
+                if (l1 < rows) {
+                    const float2 a = s_in[l1 * 32 + lane];
+                    const float2 t = s_tw[(l1 * r) & (n1 - 1)];
+                    v[q].x += a.x * t.x - a.y * t.y;
+                    v[q].y += a.x * t.y + a.y * t.x;
+                }
+            }
+        }
+        fft_reg<F>(v, tw);
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            const int k1 = r + C * q;
+            const int e = l2 * k1;  // < nf <= 2^21
+            const float2 t = cmulf(s_twa[e >> twb_bits], s_twb[e & mask]);
+            Zj[(int64_t)k1 * n2 + l2] = cmulf(v[brev(q, ilog2c(F))], t);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row pass + unpack + epilogue
+// ---------------------------------------------------------------------------
+// Row owned by slot s of CTA t (R = rows per group): slots [0, R) are the low rows
+// k1 = t R + s; slots [R, 2R) their mirrors n1 - k1, except that the mirror slot of
+// k1 = 0 holds the other self-paired row n1/2.
+__device__ __forceinline__ int slot_row(int slot, int t, int R, int n1) {
+    if (slot < R) return t * R + slot;
+    const int k1 = t * R + (slot - R);
+    return k1 == 0 ? (n1 >> 1) : n1 - k1;
+}
+
+__global__ void __launch_bounds__(64 * kRowsR, 2)
+rows_fast_kernel(const float2* __restrict__ Z, int n1, int R, int Kp, int K, int64_t I, int64_t i_c, int64_t nf,
+                 const float2* __restrict__ tw1024 /*[1024] full circle*/, Tw32 tw,
+                 const float2* __restrict__ deconv, float2* __restrict__ J, float* __restrict__ E,
+                 float* __restrict__ Pout) {
+    extern __shared__ float2 smem_f2[];
+    float2* s_tw = smem_f2;                 // [1024]
+    float2* s_row = s_tw + kRowLen;         // [2R][kRowPad]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;      // slot of the row this warp transforms
+    const int t = blockIdx.x;
+    const int b = blockIdx.y;
+    const int nslots = 2 * R;
+    const int64_t half = nf >> 1;
+    const int nthreads = blockDim.x;
+
+    for (int q = threadIdx.x; q < kRowLen; q += nthreads) s_tw[q] = tw1024[q];
+
+    // outputs owned by this thread: e = threadIdx.x + nthreads * it, slot-major within groups:
+    // within a group of R rows, consecutive threads take consecutive rows, then k2.
+    constexpr int kOut = (2 * kRowsR * kRowLen) / (64 * kRowsR);  // 32 when blockDim = 64 R
+    float pacc[kOut];
+#pragma unroll
+    for (int it = 0; it < kOut; ++it) pacc[it] = 0.f;
+
+    const int my_row = warp < nslots ? slot_row(warp, t, R, n1) : 0;
+    float2* S = s_row + warp * kRowPad;
+
+    for (int j = 0; j < Kp; ++j) {
+        __syncthreads();  // previous epilogue done with s_row (and s_tw ready on j = 0)
+        if (warp < nslots) {
+            const float2* Zr = Z + (((int64_t)b * Kp + j) * n1 + my_row) * kRowLen;
+            float2 v[32];
+#pragma unroll
+            for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zr + 32 * a + lane);
+            fft_reg<32>(v, tw);  // over a, column b = lane: v[q] = Y[lane][brev(q)]
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int c = brev(q, 5);
+                S[c * 33 + lane] = cmulf(v[q], s_tw[(lane * c) & 1023]);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
+            __syncwarp();
+            fft_reg<32>(v, tw);  // over b for column c = lane: v[q] = X[lane + 32 brev(q)]
+#pragma unroll
+            for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
+        }
+        __syncthreads();
+
+        // epilogue: every owned output (slot, k2) once
+        const bool has_odd = (2 * j + 1) < K;
+        float2* J0 = J ? J + ((int64_t)b * K + 2 * j) * I : nullptr;
+        float2* J1 = (J && has_odd) ? J + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
+        float* E0 = E ? E + ((int64_t)b * K + 2 * j) * I : nullptr;
+        float* E1 = (E && has_odd) ? E + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
+#pragma unroll
+        for (int it = 0; it < kOut; ++it) {
+            const int e = threadIdx.x + nthreads * it;
+            const int group = e / (R * kRowLen);          // 0 = low rows, 1 = mirror rows
+            const int rem = e - group * R * kRowLen;
+            const int sl = group * R + rem % R;
+            const int k2 = rem / R;
+            if (sl >= nslots) continue;
+            const int row = slot_row(sl, t, R, n1);
+            // partner slot / column holding Zp[nf - k]
+            int psl, pk2;
+            if (row == 0) {
+                psl = sl;
+                pk2 = (kRowLen - k2) & (kRowLen - 1);
+            } else if (row == (n1 >> 1)) {
+                psl = sl;
+                pk2 = kRowLen - 1 - k2;
+            } else {
+                psl = sl < R ? sl + R : sl - R;
+                pk2 = kRowLen - 1 - k2;
+            }
+            const int64_t kk = (int64_t)row + (int64_t)n1 * k2;
+            const int64_t m = kk < half ? kk : kk - nf;
+            const int64_t i = m + i_c;
+            if (i < 0 || i >= I) continue;
+            const float2 A = s_row[sl * kRowPad + k2];
+            const float2 Bc = s_row[psl * kRowPad + pk2];
+            // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
+            const float2 xe = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y));
+            const float2 xo = make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x));
+            const float2 s = __ldg(deconv + i);
+            const float2 j0 = cmulf(xe, s);
+            const float p0 = j0.x * j0.x + j0.y * j0.y;
+            if (J0) __stcs(J0 + i, j0);
+            if (E0) __stcs(E0 + i, p0);
+            float pp = p0;
+            if (has_odd) {
+                const float2 j1 = cmulf(xo, s);
+                const float p1 = j1.x * j1.x + j1.y * j1.y;
+                if (J1) __stcs(J1 + i, j1);
+                if (E1) __stcs(E1 + i, p1);
+                pp += p1;
+            }
+            pacc[it] += pp;
+        }
+    }
+    if (Pout) {
+        const float invK = 1.0f / (float)K;
+        float* Pb = Pout + (int64_t)b * I;
+#pragma unroll
+        for (int it = 0; it < kOut; ++it) {
+            const int e = threadIdx.x + nthreads * it;
+            const int group = e / (R * kRowLen);
+            const int rem = e - group * R * kRowLen;
+            const int sl = group * R + rem % R;
+            const int k2 = rem / R;
+            if (sl >= nslots) continue;
+            const int row = slot_row(sl, t, R, n1);
+            const int64_t kk = (int64_t)row + (int64_t)n1 * k2;
+            const int64_t m = kk < half ? kk : kk - nf;
+            const int64_t i = m + i_c;
+            if (i < 0 || i >= I) continue;
+            __stcs(Pb + i, pacc[it] * invK);
+        }
+    }
+}
+
+Tw32 make_tw32() {
+    Tw32 t;
+    for (int e = 0; e < 16; ++e) {
+        const double a = 2.0 * 3.141592653589793238462643383279502884 * e / 32.0;
+        t.w[e] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    return t;
+}
+
+template <int KP>
+m2_status launch_spread_packed(m2nufft_plan_s* p, const float* x, int nb, cudaStream_t st) {
+    const Geometry& g = p->g;
+    dim3 grid((unsigned)g.ntiles, (unsigned)nb);
+    spread_packed_kernel<KP><<<grid, kSpreadTile, 0, st>>>(
+        x, g.N, p->d_pt_src, p->d_pt_cell, reinterpret_cast<const float*>(p->d_pt_off),
+        reinterpret_cast<const float*>(p->d_taper), g.P, p->d_tile_pb, p->d_tile_pe, g.K, g.kp, g.width,
+        (float)(2.0 / g.width), (float)g.beta, g.Lg, reinterpret_cast<float2*>(p->d_g));
+    M2_CUDA_TRY(cudaGetLastError());
+    return M2_OK;
+}
+
+template <int F>
+m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw) {
+    const Geometry& g = p->g;
+    const int twa_len = (int)(g.nf >> g.twb_bits);
+    const size_t smem = sizeof(float2) * ((size_t)g.rows * 32 + g.n1 + ((size_t)1 << g.twb_bits) + twa_len);
+    auto kern = cols_fast_kernel<F>;
+    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)(kRowLen / 32), (unsigned)g.kp, (unsigned)nb);
+    kern<<<grid, 32 * kColWarps, smem, st>>>(reinterpret_cast<const float2*>(p->d_g), g.Lg, (int)g.rows,
+                                              (int)g.n1, g.kp, reinterpret_cast<const float2*>(p->d_twn1),
+                                              reinterpret_cast<const float2*>(p->d_twa),
+                                              reinterpret_cast<const float2*>(p->d_twb), g.twb_bits, twa_len, tw,
+                                              reinterpret_cast<float2*>(p->d_Z));
+    M2_CUDA_TRY(cudaGetLastError());
+    return M2_OK;
+}
+
+}  // namespace
+
+m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, cudaStream_t st) {
+    const Geometry& g = p->g;
+    static const Tw32 tw = make_tw32();
+
+    mark(p, 0, 0, st);
+    if (g.kp <= 2) M2_TRY(launch_spread_packed<2>(p, x, nb, st));
+    else if (g.kp <= 4) M2_TRY(launch_spread_packed<4>(p, x, nb, st));
+    else M2_TRY(launch_spread_packed<8>(p, x, nb, st));
+    mark(p, 0, 1, st);
+
+    mark(p, 1, 0, st);
+    switch (std::min<int64_t>(g.n1, 32)) {
+        case 2: M2_TRY(launch_cols_fast<2>(p, nb, st, tw)); break;
+        case 4: M2_TRY(launch_cols_fast<4>(p, nb, st, tw)); break;
+        case 8: M2_TRY(launch_cols_fast<8>(p, nb, st, tw)); break;
+        case 16: M2_TRY(launch_cols_fast<16>(p, nb, st, tw)); break;
+        default: M2_TRY(launch_cols_fast<32>(p, nb, st, tw)); break;
+    }
+    mark(p, 1, 1, st);
+
+    {
+        const int R = (int)std::min<int64_t>(kRowsR, g.n1 / 2);
+        const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)2 * kRowsR * kRowPad);
+        M2_CUDA_TRY(cudaFuncSetAttribute(rows_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((unsigned)(g.n1 / (2 * R)), (unsigned)nb);
+        mark(p, 2, 0, st);
+        rows_fast_kernel<<<grid, 64 * kRowsR, smem, st>>>(
+            reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, R, g.kp, g.K, g.I, g.i_c, g.nf,
+            reinterpret_cast<const float2*>(p->d_tw1024), tw, reinterpret_cast<const float2*>(p->d_deconv), J, E,
+            P);
+        M2_CUDA_TRY(cudaGetLastError());
+        mark(p, 2, 1, st);
+    }
+    return M2_OK;
+}
+
+}  // namespace m2

@@ -561,10 +561,6 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     g.beta = 2.30 * g.width;
     g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
     g.log_nf = ilog2(g.nf);
-    g.log_n1 = g.log_nf / 2;
-    g.log_n2 = g.log_nf - g.log_n1;
-    g.n1 = int64_t(1) << g.log_n1;
-    g.n2 = int64_t(1) << g.log_n2;
     const double s_cells = (double)g.nf * g.df;  // exact: nf is a power of two
     g.h = 1.0 / s_cells;
     const double span_cells = (ts.back() - ts.front()) * s_cells;
@@ -609,11 +605,37 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                 ext.push_back(c);
             }
         pts.swap(ext);
-        g.rows = g.n1;
-    } else {
-        const int64_t last = pts.back().cell + g.width;  // one past the last written cell
-        g.rows = std::min<int64_t>(g.n1, (last + g.n2 - 1) / g.n2);
     }
+    // ---- exec path and the nf = n1 * n2 split ----
+    // rows(n2): nonzero input rows of the column DFTs for a row length n2
+    const int64_t last_cell = g.wrap ? g.nf : pts.back().cell + g.width;  // one past the last written cell
+    auto rows_for = [&](int64_t n2) {
+        const int64_t n1 = g.nf / n2;
+        return g.wrap ? n1 : std::min<int64_t>(n1, (last_cell + n2 - 1) / n2);
+    };
+    if (opts.path < 0 || opts.path > 2) {
+        set_error("opts.path must be 0, 1 or 2");
+        return bail(M2_ERR_ARG);
+    }
+    const bool packed_ok = opts.precision == 32 && g.real_taper && g.nf >= 2048 && g.nf <= (int64_t(1) << 21) &&
+                           rows_for(1024) <= 64;
+    if (opts.path == 2 && !packed_ok) {
+        set_error("the packed FP32 path needs precision 32, a real modulated taper (f_lo + (I/2) df = 0), "
+                  "2048 <= nf <= 2^21 and a support of at most 64 rows of 1024 cells");
+        return bail(M2_ERR_ARG);
+    }
+    g.path = (opts.path == 1 || !packed_ok) ? 1 : 2;
+    if (g.path == 2) {
+        g.log_n2 = 10;
+        g.log_n1 = g.log_nf - 10;
+    } else {
+        g.log_n1 = g.log_nf / 2;
+        g.log_n2 = g.log_nf - g.log_n1;
+    }
+    g.n1 = int64_t(1) << g.log_n1;
+    g.n2 = int64_t(1) << g.log_n2;
+    g.rows = rows_for(g.n2);
+    g.kp = g.path == 2 ? (K + 1) / 2 : K;
     g.Lg = g.rows * g.n2;
     g.P = (int64_t)pts.size();
     g.ntiles = (g.Lg + kSpreadTile - 1) / kSpreadTile;
@@ -624,8 +646,9 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const size_t csz = opts.precision == 32 ? 8 : 16;
     {
         // chunk so that the FFT workspace of a chunk stays well inside L2
-        const size_t z_per_signal = (size_t)K * g.nf * csz;
-        int64_t chunk = std::max<int64_t>(1, (int64_t)((48u << 20) / std::max<size_t>(z_per_signal, 1)));
+        const size_t z_per_signal = (size_t)g.kp * g.nf * csz;
+        const size_t target = g.path == 2 ? (64u << 20) : (48u << 20);
+        int64_t chunk = std::max<int64_t>(1, (int64_t)(target / std::max<size_t>(z_per_signal, 1)));
         chunk = std::min<int64_t>(chunk, 1024);
         if (opts.max_batch > 0) chunk = std::min<int64_t>(chunk, opts.max_batch);
         g.chunk = (int)chunk;
@@ -686,6 +709,10 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twa,
                              unit_roots(g.nf >> g.twb_bits, g.nf, int64_t(1) << g.twb_bits)));
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twb, unit_roots(int64_t(1) << g.twb_bits, g.nf, 1)));
+    if (g.path == 2) {
+        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twn1, unit_roots(g.n1, g.n1, 1)));
+        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, unit_roots(1024, 1024, 1)));
+    }
 
     // ---- deconvolution / re-phasing factors ----
     {
@@ -781,14 +808,14 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     // ---- workspace ----
     if (opts.precision == 32) {
         float2 *dg = nullptr, *dZ = nullptr;
-        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * K * g.Lg));
-        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * K * g.nf));
+        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * g.kp * g.Lg));
+        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * g.kp * g.nf));
         p->d_g = dg;
         p->d_Z = dZ;
     } else {
         double2 *dg = nullptr, *dZ = nullptr;
-        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * K * g.Lg));
-        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * K * g.nf));
+        M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * g.kp * g.Lg));
+        M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * g.kp * g.nf));
         p->d_g = dg;
         p->d_Z = dZ;
     }
@@ -872,6 +899,7 @@ extern "C" m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info) {
     info->real_taper = g.real_taper;
     info->integer_grid = p->integer_grid;
     info->chunk = g.chunk;
+    info->path = g.path;
     info->device_bytes = p->device_bytes;
     info->gep_seconds = p->gep_seconds;
     return M2_OK;

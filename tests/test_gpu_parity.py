@@ -49,12 +49,17 @@ def oracle_all(t, X, w, f_lo, df, I, idx=None):
 # ---------------------------------------------------------------------------
 # full-array parity at oracle-friendly sizes
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", [64, 32])
-def test_grid1024_full_parity(dev, prec):
+PATHS = [(64, 1), (32, 1), (32, 2)]  # (precision, exec path): generic FP64 / generic FP32 / packed FP32
+
+
+@pytest.mark.parametrize("prec,path", PATHS)
+def test_grid1024_full_parity(dev, prec, path):
     """N=1024 grid with 20% Bernoulli missing, 3 tones + noise, K=6, I=1024."""
     wl = synth.workload("grid1024", batch=3)
     w, lam = ogpss.nominal_tapers(wl.t, wl.fs, wl.f_w, wl.K)
-    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=prec, tapers=w, lam=lam)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=prec, tapers=w, lam=lam,
+                    path=path)
+    assert plan.info["path"] == path
     out = run_plan(plan, wl.x, dev)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I)
     assert rel_l2(out["J"], Jr) <= TOL[prec]
@@ -63,15 +68,15 @@ def test_grid1024_full_parity(dev, prec):
     assert plan.info["wrap"] == 1  # span ~ period: wrap-around spreading
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-def test_jittered_medium_full_parity(dev, prec):
+@pytest.mark.parametrize("prec,path", PATHS)
+def test_jittered_medium_full_parity(dev, prec, path):
     """Jittered N=2048 (+-0.4), AR(4)-like tones, K=8, I=2^14: zero-padded
     grid (support 1/8 of the period) spanning many tiles and FFT rows."""
     t = synth.jittered(2048, 0.4, 21)
     X = np.stack([synth.tones(t, (0.1, 0.31), (2.0, 1.0), 1.0, 30 + b) for b in range(2)])
     K, fw, I = 8, 5.0 / 2048, 1 << 14
     w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
-    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=prec, tapers=w, lam=lam)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=prec, tapers=w, lam=lam, path=path)
     out = run_plan(plan, X, dev)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
     assert plan.info["wrap"] == 0 and plan.info["rows"] < plan.info["n1"]
@@ -134,17 +139,48 @@ def test_many_chunks_and_empty_batch(dev):
     torch.cuda.synchronize()
 
 
-def test_batch_equals_alone_bitwise(dev):
+@pytest.mark.parametrize("path", [1, 2])
+def test_batch_equals_alone_bitwise(dev, path):
     """Deterministic kernels: a signal gives bit-identical J and P-hat alone
     and inside a batch (no atomics, fixed summation order)."""
     t = synth.jittered(1500, 0.4, 13)
     X = np.stack([synth.white(t, 1.0, 60 + b) for b in range(4)])
     w = seeded_tapers(6, 1500, 3)
-    plan = pkg.Plan(t, 1.0, 0.004, 6, -0.5, 1 / 8192, 8192, precision=32, tapers=w)
+    plan = pkg.Plan(t, 1.0, 0.004, 6, -0.5, 1 / 8192, 8192, precision=32, tapers=w, path=path)
     allb = run_plan(plan, X, dev)
     one = run_plan(plan, X[2:3], dev)
     assert np.array_equal(allb["J"][2], one["J"][0])
     assert np.array_equal(allb["P"][2], one["P"][0])
+
+
+@pytest.mark.parametrize("K,I,N", [(1, 1024, 400), (5, 1024, 700), (3, 2048, 900), (7, 4096, 1500),
+                                   (2, 3000, 1000), (9, 20000, 4000)])
+def test_packed_path_edge_cases(dev, K, I, N):
+    """Packed FP32 path: odd K (last pair half empty), K = 1, the smallest row
+    counts n1 = 2, 4, 8 (self-paired rows 0 and n1/2), wrap-around (span
+    longer than the period) and I not a power of two; against the oracle and
+    against the generic FP32 path."""
+    t = synth.jittered(N, 0.4, K + N)
+    X = np.stack([synth.white(t, 1.0, 70 + b) for b in range(3)])
+    w = seeded_tapers(K, N, K)
+    p2 = pkg.Plan(t, 1.0, 2.0 / N, K, -0.5, 1.0 / I, I, precision=32, tapers=w, path=2, max_batch=2)
+    p1 = pkg.Plan(t, 1.0, 2.0 / N, K, -0.5, 1.0 / I, I, precision=32, tapers=w, path=1)
+    o2 = run_plan(p2, X, dev)
+    o1 = run_plan(p1, X, dev)
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
+    assert rel_l2(o2["J"], Jr) <= TOL[32]
+    assert rel_l2(o2["P"], Pr) <= TOL[32]
+    assert rel_l2(o2["E"], np.abs(Jr) ** 2) <= TOL[32]
+    assert rel_l2(o2["P"], o1["P"]) <= TOL[32]
+
+
+def test_packed_path_rejects_complex_taper(dev):
+    t = synth.jittered(300, 0.4, 1)
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.Plan(t, 1.0, 0.01, 2, 0.01, 1 / 1024, 1024, precision=32, tapers=seeded_tapers(2, 300, 0), path=2)
+    assert e.value.status == 1
+    with pytest.raises(pkg.M2Error):
+        pkg.Plan(t, 1.0, 0.01, 2, -0.5, 1 / 1024, 1024, precision=64, tapers=seeded_tapers(2, 300, 0), path=2)
 
 
 # ---------------------------------------------------------------------------
@@ -226,13 +262,14 @@ def test_leakage_rate_mismatch_matches_oracle(dev):
 # ---------------------------------------------------------------------------
 # full-size workloads (sampled outputs)
 # ---------------------------------------------------------------------------
-def test_jitter16k_full_size_fp32(dev):
+@pytest.mark.parametrize("path", [1, 2])
+def test_jitter16k_full_size_fp32(dev, path):
     """N = 16384 jittered, K = 8, I = 2^18 (the benchmark workload): FP32
     path with FP64-split coordinates against the direct FP64 sum on sampled
     band centres; seeded tapers (any real taper is a valid input)."""
     wl = synth.workload("jitter16k", batch=2)
     w = seeded_tapers(wl.K, wl.N, 7)
-    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=path)
     out = run_plan(plan, wl.x, dev)
     idx = sample_bands(wl.I, 384, 1)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
@@ -263,11 +300,12 @@ def test_jitter16k_gep_on_gpu(dev):
     np.testing.assert_allclose(w @ RBw, 2 * wl.f_w * np.eye(wl.K), atol=1e-10)
 
 
-def test_periodic16k_full_size_fp32(dev):
+@pytest.mark.parametrize("path", [1, 2])
+def test_periodic16k_full_size_fp32(dev, path):
     """N = 16384 grid, blocks of 8 drop 2 (12288 kept), K = 10, I = 2^20."""
     wl = synth.workload("periodic16k")
     w = seeded_tapers(wl.K, wl.N, 9)
-    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=path)
     out = run_plan(plan, wl.x, dev)
     idx = sample_bands(wl.I, 256, 2)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
