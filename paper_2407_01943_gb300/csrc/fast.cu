@@ -196,55 +196,66 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
 // ---------------------------------------------------------------------------
 // row pass + unpack + epilogue
 // ---------------------------------------------------------------------------
-// Row owned by slot s of CTA t (R = rows per group): slots [0, R) are the low rows
-// k1 = t R + s; slots [R, 2R) their mirrors n1 - k1, except that the mirror slot of
-// k1 = 0 holds the other self-paired row n1/2.
-__device__ __forceinline__ int slot_row(int slot, int t, int R, int n1) {
+// CTA t owns R low rows k1 = t R + lr (lr < R) and their mirrors n1 - k1; the
+// mirror of k1 = 0 is replaced by the other self-paired row n1/2.  Warp s
+// transforms the row of slot s (slots [0, R) low, [R, 2R) mirror).
+template <int R>
+__device__ __forceinline__ int slot_row(int slot, int t, int n1) {
     if (slot < R) return t * R + slot;
     const int k1 = t * R + (slot - R);
     return k1 == 0 ? (n1 >> 1) : n1 - k1;
 }
 
-__global__ void __launch_bounds__(64 * kRowsR, 2)
-rows_fast_kernel(const float2* __restrict__ Z, int n1, int R, int Kp, int K, int64_t I, int64_t i_c, int64_t nf,
+template <int R>
+__global__ void __launch_bounds__(64 * R, (R <= 4 ? 2 : 1))
+rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int i_c, int nf,
                  const float2* __restrict__ tw1024 /*[1024] full circle*/, Tw32 tw,
                  const float2* __restrict__ deconv, float2* __restrict__ J, float* __restrict__ E,
                  float* __restrict__ Pout) {
+    constexpr int NT = 64 * R;           // threads
+    constexpr int STEP = NT / R;         // k2 stride between a thread's outputs (64)
+    constexpr int NIT = kRowLen / STEP;  // outputs per thread per row group (16)
     extern __shared__ float2 smem_f2[];
-    float2* s_tw = smem_f2;                 // [1024]
-    float2* s_row = s_tw + kRowLen;         // [2R][kRowPad]
+    float2* s_tw = smem_f2;              // [1024]
+    float2* s_row = s_tw + kRowLen;      // [2R][kRowPad]
+    float* s_pacc = reinterpret_cast<float*>(s_row + 2 * R * kRowPad);  // [2 NIT][NT], thread-private columns
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;      // slot of the row this warp transforms
+    const int warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
     const int b = blockIdx.y;
-    const int nslots = 2 * R;
-    const int64_t half = nf >> 1;
-    const int nthreads = blockDim.x;
+    const int half = nf >> 1;
 
-    for (int q = threadIdx.x; q < kRowLen; q += nthreads) s_tw[q] = tw1024[q];
+    for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = tw1024[q];
 
-    // outputs owned by this thread: e = threadIdx.x + nthreads * it, slot-major within groups:
-    // within a group of R rows, consecutive threads take consecutive rows, then k2.
-    constexpr int kOut = (2 * kRowsR * kRowLen) / (64 * kRowsR);  // 32 when blockDim = 64 R
-    float pacc[kOut];
+    // epilogue ownership: low slot lr and its mirror slot R + lr, columns k2_0 + STEP * it
+    const int lr = threadIdx.x % R;
+    const int k2_0 = threadIdx.x / R;
+    const int rowL = t * R + lr;
+    const bool zero_row = rowL == 0;
+    const int rowM = zero_row ? (n1 >> 1) : n1 - rowL;
+    const int offL = lr * kRowPad, offM = (R + lr) * kRowPad;
+    const int pbL = zero_row ? offL : offM;  // slot holding Zp[nf - k] for the low row
+    const int pbM = zero_row ? offM : offL;  // ... and for the mirror row
+
+    float* pacc = s_pacc + threadIdx.x;  // pacc[e * NT]
 #pragma unroll
-    for (int it = 0; it < kOut; ++it) pacc[it] = 0.f;
+    for (int e = 0; e < 2 * NIT; ++e) pacc[e * NT] = 0.f;
 
-    const int my_row = warp < nslots ? slot_row(warp, t, R, n1) : 0;
+    const int my_row = slot_row<R>(warp, t, n1);
     float2* S = s_row + warp * kRowPad;
 
     for (int j = 0; j < Kp; ++j) {
         __syncthreads();  // previous epilogue done with s_row (and s_tw ready on j = 0)
-        if (warp < nslots) {
+        {
             const float2* Zr = Z + (((int64_t)b * Kp + j) * n1 + my_row) * kRowLen;
             float2 v[32];
 #pragma unroll
             for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zr + 32 * a + lane);
-            fft_reg<32>(v, tw);  // over a, column b = lane: v[q] = Y[lane][brev(q)]
+            fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int c = brev(q, 5);
-                S[c * 33 + lane] = cmulf(v[q], s_tw[(lane * c) & 1023]);
+                S[c * 33 + lane] = cmulf(v[q], s_tw[lane * c]);
             }
             __syncwarp();
 #pragma unroll
@@ -256,75 +267,59 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int R, int Kp, int K, int
         }
         __syncthreads();
 
-        // epilogue: every owned output (slot, k2) once
         const bool has_odd = (2 * j + 1) < K;
         float2* J0 = J ? J + ((int64_t)b * K + 2 * j) * I : nullptr;
         float2* J1 = (J && has_odd) ? J + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
         float* E0 = E ? E + ((int64_t)b * K + 2 * j) * I : nullptr;
         float* E1 = (E && has_odd) ? E + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
-#pragma unroll
-        for (int it = 0; it < kOut; ++it) {
-            const int e = threadIdx.x + nthreads * it;
-            const int group = e / (R * kRowLen);          // 0 = low rows, 1 = mirror rows
-            const int rem = e - group * R * kRowLen;
-            const int sl = group * R + rem % R;
-            const int k2 = rem / R;
-            if (sl >= nslots) continue;
-            const int row = slot_row(sl, t, R, n1);
-            // partner slot / column holding Zp[nf - k]
-            int psl, pk2;
-            if (row == 0) {
-                psl = sl;
-                pk2 = (kRowLen - k2) & (kRowLen - 1);
-            } else if (row == (n1 >> 1)) {
-                psl = sl;
-                pk2 = kRowLen - 1 - k2;
-            } else {
-                psl = sl < R ? sl + R : sl - R;
-                pk2 = kRowLen - 1 - k2;
+#pragma unroll 1
+        for (int g2 = 0; g2 < 2; ++g2) {
+            const int row = g2 ? rowM : rowL;
+            const int own = g2 ? offM : offL;
+            const int pbase = g2 ? pbM : pbL;
+            const bool zero_col = (g2 == 0) && zero_row;  // row 0 pairs k2 with (1024 - k2) mod 1024
+#pragma unroll 4
+            for (int it = 0; it < NIT; ++it) {
+                const int k2 = k2_0 + STEP * it;
+                const int kk = row + n1 * k2;
+                const int i = (kk < half ? kk : kk - nf) + i_c;
+                if ((unsigned)i >= (unsigned)I) continue;
+                const int pk2 = zero_col ? ((kRowLen - k2) & (kRowLen - 1)) : (kRowLen - 1 - k2);
+                const float2 A = s_row[own + k2];
+                const float2 Bc = s_row[pbase + pk2];
+                // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
+                const float2 xe = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y));
+                const float2 s = __ldg(deconv + i);
+                const float2 j0 = cmulf(xe, s);
+                const float p0 = j0.x * j0.x + j0.y * j0.y;
+                if (J0) __stcs(J0 + i, j0);
+                if (E0) __stcs(E0 + i, p0);
+                float pp = p0;
+                if (has_odd) {
+                    const float2 xo = make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x));
+                    const float2 j1 = cmulf(xo, s);
+                    const float p1 = j1.x * j1.x + j1.y * j1.y;
+                    if (J1) __stcs(J1 + i, j1);
+                    if (E1) __stcs(E1 + i, p1);
+                    pp += p1;
+                }
+                pacc[(g2 * NIT + it) * NT] += pp;
             }
-            const int64_t kk = (int64_t)row + (int64_t)n1 * k2;
-            const int64_t m = kk < half ? kk : kk - nf;
-            const int64_t i = m + i_c;
-            if (i < 0 || i >= I) continue;
-            const float2 A = s_row[sl * kRowPad + k2];
-            const float2 Bc = s_row[psl * kRowPad + pk2];
-            // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
-            const float2 xe = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y));
-            const float2 xo = make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x));
-            const float2 s = __ldg(deconv + i);
-            const float2 j0 = cmulf(xe, s);
-            const float p0 = j0.x * j0.x + j0.y * j0.y;
-            if (J0) __stcs(J0 + i, j0);
-            if (E0) __stcs(E0 + i, p0);
-            float pp = p0;
-            if (has_odd) {
-                const float2 j1 = cmulf(xo, s);
-                const float p1 = j1.x * j1.x + j1.y * j1.y;
-                if (J1) __stcs(J1 + i, j1);
-                if (E1) __stcs(E1 + i, p1);
-                pp += p1;
-            }
-            pacc[it] += pp;
         }
     }
     if (Pout) {
         const float invK = 1.0f / (float)K;
         float* Pb = Pout + (int64_t)b * I;
 #pragma unroll
-        for (int it = 0; it < kOut; ++it) {
-            const int e = threadIdx.x + nthreads * it;
-            const int group = e / (R * kRowLen);
-            const int rem = e - group * R * kRowLen;
-            const int sl = group * R + rem % R;
-            const int k2 = rem / R;
-            if (sl >= nslots) continue;
-            const int row = slot_row(sl, t, R, n1);
-            const int64_t kk = (int64_t)row + (int64_t)n1 * k2;
-            const int64_t m = kk < half ? kk : kk - nf;
-            const int64_t i = m + i_c;
-            if (i < 0 || i >= I) continue;
-            __stcs(Pb + i, pacc[it] * invK);
+        for (int g2 = 0; g2 < 2; ++g2) {
+            const int row = g2 ? rowM : rowL;
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int k2 = k2_0 + STEP * it;
+                const int kk = row + n1 * k2;
+                const int i = (kk < half ? kk : kk - nf) + i_c;
+                if ((unsigned)i < (unsigned)I) __stcs(Pb + i, pacc[(g2 * NIT + it) * NT] * invK);
+            }
         }
     }
 }
@@ -367,6 +362,22 @@ m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
     return M2_OK;
 }
 
+template <int R>
+m2_status launch_rows_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw, float2* J, float* E,
+                           float* P) {
+    const Geometry& g = p->g;
+    const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)2 * R * kRowPad) +
+                        sizeof(float) * (size_t)2 * kRowLen * R;  // P-hat accumulators [2 NIT][NT]
+    auto kern = rows_fast_kernel<R>;
+    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)(g.n1 / (2 * R)), (unsigned)nb);
+    kern<<<grid, 64 * R, smem, st>>>(reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, g.kp, g.K, (int)g.I,
+                                     (int)g.i_c, (int)g.nf, reinterpret_cast<const float2*>(p->d_tw1024), tw,
+                                     reinterpret_cast<const float2*>(p->d_deconv), J, E, P);
+    M2_CUDA_TRY(cudaGetLastError());
+    return M2_OK;
+}
+
 }  // namespace
 
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, cudaStream_t st) {
@@ -389,19 +400,14 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     }
     mark(p, 1, 1, st);
 
+    mark(p, 2, 0, st);
     {
         const int R = (int)std::min<int64_t>(kRowsR, g.n1 / 2);
-        const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)2 * kRowsR * kRowPad);
-        M2_CUDA_TRY(cudaFuncSetAttribute(rows_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((unsigned)(g.n1 / (2 * R)), (unsigned)nb);
-        mark(p, 2, 0, st);
-        rows_fast_kernel<<<grid, 64 * kRowsR, smem, st>>>(
-            reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, R, g.kp, g.K, g.I, g.i_c, g.nf,
-            reinterpret_cast<const float2*>(p->d_tw1024), tw, reinterpret_cast<const float2*>(p->d_deconv), J, E,
-            P);
-        M2_CUDA_TRY(cudaGetLastError());
-        mark(p, 2, 1, st);
+        if (R == 4) M2_TRY(launch_rows_fast<4>(p, nb, st, tw, J, E, P));
+        else if (R == 2) M2_TRY(launch_rows_fast<2>(p, nb, st, tw, J, E, P));
+        else M2_TRY(launch_rows_fast<1>(p, nb, st, tw, J, E, P));
     }
+    mark(p, 2, 1, st);
     return M2_OK;
 }
 

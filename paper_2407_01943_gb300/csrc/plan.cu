@@ -556,7 +556,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     }
     double tmax_abs = 0;
     for (double v : ts) tmax_abs = std::max(tmax_abs, std::fabs(v));
-    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < 1e-14 ? 1 : 0;
+    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < 1e-12 ? 1 : 0;
     g.width = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
     g.beta = 2.30 * g.width;
     g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
