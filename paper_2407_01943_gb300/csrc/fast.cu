@@ -29,7 +29,9 @@ namespace m2 {
 namespace {
 
 constexpr int kRowLen = 1024;     // n2 of the packed path
-constexpr int kRowPad = 33 * 32;  // per-warp transpose / row buffer (padded 32 x 33)
+constexpr int kRowPad = 1060;     // per-warp transpose / row buffer: >= 32 x 33, and 2*1060 = 8 (mod 32)
+                                  // words so the epilogue's 4 rows x 4 columns per half-warp hit
+                                  // 32 distinct banks
 constexpr int kRowsR = 4;         // low rows per CTA of the row pass (plus as many mirror rows)
 constexpr int kColWarps = 4;      // warps per CTA of the column pass
 
@@ -137,34 +139,38 @@ spread_packed_kernel(const float* __restrict__ x, int64_t N, const int32_t* __re
 // ---------------------------------------------------------------------------
 // column pass: Z[b][j][k1][l2] = W_nf^{l2 k1} sum_{l1 < rows} gp[b][j][l1 n2 + l2] W_n1^{l1 k1}
 // CTA = 32 columns x all cosets; lane = column; F-point FFT per coset in registers.
+// The output twiddle W_nf^{l2 (r + C q)} = W_nf^{l2 r} * T_lane[q] uses a per-lane
+// table T_lane[q] = W_nf^{l2 C q} stored [q][lane] (conflict-free) and one base
+// factor per coset.
 // ---------------------------------------------------------------------------
 template <int F>
 __global__ void __launch_bounds__(32 * kColWarps)
 cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, int Kp,
                  const float2* __restrict__ tw_n1 /*[n1] full circle*/, const float2* __restrict__ twa,
-                 const float2* __restrict__ twb, int twb_bits, int twa_len, Tw32 tw, float2* __restrict__ Z) {
+                 const float2* __restrict__ twb, int twb_bits, Tw32 tw, float2* __restrict__ Z) {
     extern __shared__ float2 smem_f2[];
-    float2* s_in = smem_f2;                     // [rows][32]
-    float2* s_tw = s_in + rows * 32;            // [n1]
-    float2* s_twb = s_tw + n1;                  // [1 << twb_bits]
-    float2* s_twa = s_twb + (1 << twb_bits);    // [twa_len]
+    float2* s_in = smem_f2;           // [rows][32]
+    float2* s_tw = s_in + rows * 32;  // [n1]
+    float2* s_T = s_tw + n1;          // [F][32]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int l2 = blockIdx.x * 32 + lane;
     const int j = blockIdx.y;
     const int b = blockIdx.z;
     const int64_t n2 = kRowLen;
+    const int C = n1 / F;
+    const int mask = (1 << twb_bits) - 1;
     const float2* gj = gp + ((int64_t)b * Kp + j) * Lg;
     float2* Zj = Z + ((int64_t)b * Kp + j) * (int64_t)n1 * n2;
 
     for (int l1 = warp; l1 < rows; l1 += kColWarps) s_in[l1 * 32 + lane] = gj[(int64_t)l1 * n2 + l2];
     for (int q = threadIdx.x; q < n1; q += blockDim.x) s_tw[q] = tw_n1[q];
-    for (int q = threadIdx.x; q < (1 << twb_bits); q += blockDim.x) s_twb[q] = twb[q];
-    for (int q = threadIdx.x; q < twa_len; q += blockDim.x) s_twa[q] = twa[q];
+    for (int q = warp; q < F; q += kColWarps) {
+        const int e = l2 * C * q;  // < nf
+        s_T[q * 32 + lane] = cmulf(__ldg(twa + (e >> twb_bits)), __ldg(twb + (e & mask)));
+    }
     __syncthreads();
 
-    const int C = n1 / F;
-    const int mask = (1 << twb_bits) - 1;
     const int nfold = (rows + F - 1) / F;
     for (int r = warp; r < C; r += kColWarps) {
         float2 v[F];
@@ -183,11 +189,12 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
             }
         }
         fft_reg<F>(v, tw);
+        const int eb = l2 * r;
+        const float2 base = cmulf(__ldg(twa + (eb >> twb_bits)), __ldg(twb + (eb & mask)));
 #pragma unroll
         for (int q = 0; q < F; ++q) {
             const int k1 = r + C * q;
-            const int e = l2 * k1;  // < nf <= 2^21
-            const float2 t = cmulf(s_twa[e >> twb_bits], s_twb[e & mask]);
+            const float2 t = cmulf(base, s_T[q * 32 + lane]);
             Zj[(int64_t)k1 * n2 + l2] = cmulf(v[brev(q, ilog2c(F))], t);
         }
     }
@@ -216,7 +223,7 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
     constexpr int STEP = NT / R;         // k2 stride between a thread's outputs (64)
     constexpr int NIT = kRowLen / STEP;  // outputs per thread per row group (16)
     extern __shared__ float2 smem_f2[];
-    float2* s_tw = smem_f2;              // [1024]
+    float2* s_tw = smem_f2;              // [32 c][32 lane]: W_1024^{lane c}
     float2* s_row = s_tw + kRowLen;      // [2R][kRowPad]
     float* s_pacc = reinterpret_cast<float*>(s_row + 2 * R * kRowPad);  // [2 NIT][NT], thread-private columns
     const int lane = threadIdx.x & 31;
@@ -225,7 +232,7 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
     const int b = blockIdx.y;
     const int half = nf >> 1;
 
-    for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = tw1024[q];
+    for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = tw1024[(q >> 5) * (q & 31)];
 
     // epilogue ownership: low slot lr and its mirror slot R + lr, columns k2_0 + STEP * it
     const int lr = threadIdx.x % R;
@@ -243,19 +250,23 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
 
     const int my_row = slot_row<R>(warp, t, n1);
     float2* S = s_row + warp * kRowPad;
+    const float2* Zrow = Z + ((int64_t)b * Kp * n1 + my_row) * kRowLen + lane;
+    const int64_t zpair = (int64_t)n1 * kRowLen;  // stride between taper pairs
+
+    // row of pair 0, prefetched into registers; the next pair's row is loaded while
+    // the current epilogue runs
+    float2 v[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zrow + 32 * a);
 
     for (int j = 0; j < Kp; ++j) {
         __syncthreads();  // previous epilogue done with s_row (and s_tw ready on j = 0)
         {
-            const float2* Zr = Z + (((int64_t)b * Kp + j) * n1 + my_row) * kRowLen;
-            float2 v[32];
-#pragma unroll
-            for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zr + 32 * a + lane);
             fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int c = brev(q, 5);
-                S[c * 33 + lane] = cmulf(v[q], s_tw[lane * c]);
+                S[c * 33 + lane] = cmulf(v[q], s_tw[c * 32 + lane]);
             }
             __syncwarp();
 #pragma unroll
@@ -266,6 +277,11 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
             for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
         }
         __syncthreads();
+        if (j + 1 < Kp) {
+            const float2* Zn = Zrow + (int64_t)(j + 1) * zpair;
+#pragma unroll
+            for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zn + 32 * a);
+        }
 
         const bool has_odd = (2 * j + 1) < K;
         float2* J0 = J ? J + ((int64_t)b * K + 2 * j) * I : nullptr;
@@ -348,15 +364,14 @@ m2_status launch_spread_packed(m2nufft_plan_s* p, const float* x, int nb, cudaSt
 template <int F>
 m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw) {
     const Geometry& g = p->g;
-    const int twa_len = (int)(g.nf >> g.twb_bits);
-    const size_t smem = sizeof(float2) * ((size_t)g.rows * 32 + g.n1 + ((size_t)1 << g.twb_bits) + twa_len);
+    const size_t smem = sizeof(float2) * ((size_t)g.rows * 32 + g.n1 + (size_t)F * 32);
     auto kern = cols_fast_kernel<F>;
     M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)(kRowLen / 32), (unsigned)g.kp, (unsigned)nb);
     kern<<<grid, 32 * kColWarps, smem, st>>>(reinterpret_cast<const float2*>(p->d_g), g.Lg, (int)g.rows,
                                               (int)g.n1, g.kp, reinterpret_cast<const float2*>(p->d_twn1),
                                               reinterpret_cast<const float2*>(p->d_twa),
-                                              reinterpret_cast<const float2*>(p->d_twb), g.twb_bits, twa_len, tw,
+                                              reinterpret_cast<const float2*>(p->d_twb), g.twb_bits, tw,
                                               reinterpret_cast<float2*>(p->d_Z));
     M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
