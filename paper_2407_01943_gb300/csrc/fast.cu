@@ -213,6 +213,13 @@ __device__ __forceinline__ int slot_row(int slot, int t, int n1) {
     return k1 == 0 ? (n1 >> 1) : n1 - k1;
 }
 
+// Epilogue symmetry: the two tapers of a pair are real, so X(nf - k) = conj(X(k)) for
+// each of them, and the deconvolution factors satisfy s(-m) = conj(s(m)) (phi-hat is
+// real and even).  Hence J(-m) = conj(J(m)), |J(-m)|^2 = |J(m)|^2 and P(-m) = P(m):
+// each thread unpacks one position k of a low row (from Zp[k] and Zp[nf - k], the
+// latter in the mirror row) and writes both the output at k and the one at nf - k.
+// Rows 0 and n1/2 pair with themselves; the thread that owns them (CTA 0, lr = 0)
+// walks row 0 for k2 in [0, 512] and row n1/2 for k2 in [0, 512).
 template <int R>
 __global__ void __launch_bounds__(64 * R, (R <= 4 ? 2 : 1))
 rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int i_c, int nf,
@@ -220,12 +227,12 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
                  const float2* __restrict__ deconv, float2* __restrict__ J, float* __restrict__ E,
                  float* __restrict__ Pout) {
     constexpr int NT = 64 * R;           // threads
-    constexpr int STEP = NT / R;         // k2 stride between a thread's outputs (64)
-    constexpr int NIT = kRowLen / STEP;  // outputs per thread per row group (16)
+    constexpr int STEP = NT / R;         // k2 stride between a thread's positions (64)
+    constexpr int NIT = kRowLen / STEP;  // positions per thread (16; 17 for the self-paired owner)
     extern __shared__ float2 smem_f2[];
     float2* s_tw = smem_f2;              // [32 c][32 lane]: W_1024^{lane c}
     float2* s_row = s_tw + kRowLen;      // [2R][kRowPad]
-    float* s_pacc = reinterpret_cast<float*>(s_row + 2 * R * kRowPad);  // [2 NIT][NT], thread-private columns
+    float* s_pacc = reinterpret_cast<float*>(s_row + 2 * R * kRowPad);  // [NIT + 1][NT], thread-private
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int t = blockIdx.x;
@@ -234,19 +241,16 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
 
     for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = tw1024[(q >> 5) * (q & 31)];
 
-    // epilogue ownership: low slot lr and its mirror slot R + lr, columns k2_0 + STEP * it
     const int lr = threadIdx.x % R;
     const int k2_0 = threadIdx.x / R;
     const int rowL = t * R + lr;
-    const bool zero_row = rowL == 0;
-    const int rowM = zero_row ? (n1 >> 1) : n1 - rowL;
+    const bool self = rowL == 0;         // owner of the self-paired rows 0 and n1/2
+    const int rowM = self ? (n1 >> 1) : n1 - rowL;
     const int offL = lr * kRowPad, offM = (R + lr) * kRowPad;
-    const int pbL = zero_row ? offL : offM;  // slot holding Zp[nf - k] for the low row
-    const int pbM = zero_row ? offM : offL;  // ... and for the mirror row
+    const int npos = self ? NIT + 1 : NIT;
 
-    float* pacc = s_pacc + threadIdx.x;  // pacc[e * NT]
-#pragma unroll
-    for (int e = 0; e < 2 * NIT; ++e) pacc[e * NT] = 0.f;
+    float* pacc = s_pacc + threadIdx.x;  // pacc[it * NT]
+    for (int it = 0; it < npos; ++it) pacc[it * NT] = 0.f;
 
     const int my_row = slot_row<R>(warp, t, n1);
     float2* S = s_row + warp * kRowPad;
@@ -288,54 +292,88 @@ rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int
         float2* J1 = (J && has_odd) ? J + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
         float* E0 = E ? E + ((int64_t)b * K + 2 * j) * I : nullptr;
         float* E1 = (E && has_odd) ? E + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
-#pragma unroll 1
-        for (int g2 = 0; g2 < 2; ++g2) {
-            const int row = g2 ? rowM : rowL;
-            const int own = g2 ? offM : offL;
-            const int pbase = g2 ? pbM : pbL;
-            const bool zero_col = (g2 == 0) && zero_row;  // row 0 pairs k2 with (1024 - k2) mod 1024
 #pragma unroll 4
-            for (int it = 0; it < NIT; ++it) {
-                const int k2 = k2_0 + STEP * it;
-                const int kk = row + n1 * k2;
-                const int i = (kk < half ? kk : kk - nf) + i_c;
-                if ((unsigned)i >= (unsigned)I) continue;
-                const int pk2 = zero_col ? ((kRowLen - k2) & (kRowLen - 1)) : (kRowLen - 1 - k2);
-                const float2 A = s_row[own + k2];
-                const float2 Bc = s_row[pbase + pk2];
-                // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
-                const float2 xe = make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y));
-                const float2 s = __ldg(deconv + i);
-                const float2 j0 = cmulf(xe, s);
-                const float p0 = j0.x * j0.x + j0.y * j0.y;
-                if (J0) __stcs(J0 + i, j0);
-                if (E0) __stcs(E0 + i, p0);
-                float pp = p0;
-                if (has_odd) {
-                    const float2 xo = make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x));
-                    const float2 j1 = cmulf(xo, s);
-                    const float p1 = j1.x * j1.x + j1.y * j1.y;
-                    if (J1) __stcs(J1 + i, j1);
-                    if (E1) __stcs(E1 + i, p1);
-                    pp += p1;
-                }
-                pacc[(g2 * NIT + it) * NT] += pp;
+        for (int it = 0; it < npos; ++it) {
+            // position (slot offset, column) of k and of its partner nf - k
+            int o1, c1, o2, c2, r1, r2;
+            if (!self) {
+                c1 = k2_0 + STEP * it;
+                o1 = offL; r1 = rowL;
+                o2 = offM; r2 = rowM; c2 = kRowLen - 1 - c1;
+            } else if (it <= NIT / 2) {  // row 0, k2 in [0, 512]
+                c1 = k2_0 + STEP * it;
+                o1 = offL; r1 = 0;
+                o2 = offL; r2 = 0; c2 = (kRowLen - c1) & (kRowLen - 1);
+                if (c1 > kRowLen / 2) continue;
+            } else {                     // row n1/2, k2 in [0, 512)
+                c1 = k2_0 + STEP * (it - NIT / 2 - 1);
+                o1 = offM; r1 = rowM;
+                o2 = offM; r2 = rowM; c2 = kRowLen - 1 - c1;
             }
+            const int kk1 = r1 + n1 * c1;
+            const int kk2 = r2 + n1 * c2;
+            const int i1 = (kk1 < half ? kk1 : kk1 - nf) + i_c;
+            const int i2 = (kk2 < half ? kk2 : kk2 - nf) + i_c;
+            const bool v1 = (unsigned)i1 < (unsigned)I;
+            const bool v2 = (unsigned)i2 < (unsigned)I && kk2 != kk1;
+            if (!v1 && !v2) continue;
+            const float2 A = s_row[o1 + c1];
+            const float2 Bc = s_row[o2 + c2];
+            float2 sd;
+            if (v1) {
+                sd = __ldg(deconv + i1);
+            } else {
+                sd = __ldg(deconv + i2);
+                sd.y = -sd.y;
+            }
+            // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
+            const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd);
+            const float p0 = j0.x * j0.x + j0.y * j0.y;
+            if (v1) {
+                if (J0) __stcs(J0 + i1, j0);
+                if (E0) __stcs(E0 + i1, p0);
+            }
+            if (v2) {
+                if (J0) __stcs(J0 + i2, make_float2(j0.x, -j0.y));
+                if (E0) __stcs(E0 + i2, p0);
+            }
+            float pp = p0;
+            if (has_odd) {
+                const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd);
+                const float p1 = j1.x * j1.x + j1.y * j1.y;
+                if (v1) {
+                    if (J1) __stcs(J1 + i1, j1);
+                    if (E1) __stcs(E1 + i1, p1);
+                }
+                if (v2) {
+                    if (J1) __stcs(J1 + i2, make_float2(j1.x, -j1.y));
+                    if (E1) __stcs(E1 + i2, p1);
+                }
+                pp += p1;
+            }
+            pacc[it * NT] += pp;
         }
     }
     if (Pout) {
         const float invK = 1.0f / (float)K;
         float* Pb = Pout + (int64_t)b * I;
-#pragma unroll
-        for (int g2 = 0; g2 < 2; ++g2) {
-            const int row = g2 ? rowM : rowL;
-#pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int k2 = k2_0 + STEP * it;
-                const int kk = row + n1 * k2;
-                const int i = (kk < half ? kk : kk - nf) + i_c;
-                if ((unsigned)i < (unsigned)I) __stcs(Pb + i, pacc[(g2 * NIT + it) * NT] * invK);
+        for (int it = 0; it < npos; ++it) {
+            int c1, c2, r1, r2;
+            if (!self) {
+                c1 = k2_0 + STEP * it; r1 = rowL; r2 = rowM; c2 = kRowLen - 1 - c1;
+            } else if (it <= NIT / 2) {
+                c1 = k2_0 + STEP * it; r1 = 0; r2 = 0; c2 = (kRowLen - c1) & (kRowLen - 1);
+                if (c1 > kRowLen / 2) continue;
+            } else {
+                c1 = k2_0 + STEP * (it - NIT / 2 - 1); r1 = rowM; r2 = rowM; c2 = kRowLen - 1 - c1;
             }
+            const int kk1 = r1 + n1 * c1;
+            const int kk2 = r2 + n1 * c2;
+            const int i1 = (kk1 < half ? kk1 : kk1 - nf) + i_c;
+            const int i2 = (kk2 < half ? kk2 : kk2 - nf) + i_c;
+            const float pv = pacc[it * NT] * invK;
+            if ((unsigned)i1 < (unsigned)I) __stcs(Pb + i1, pv);
+            if ((unsigned)i2 < (unsigned)I && kk2 != kk1) __stcs(Pb + i2, pv);
         }
     }
 }
@@ -382,7 +420,7 @@ m2_status launch_rows_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
                            float* P) {
     const Geometry& g = p->g;
     const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)2 * R * kRowPad) +
-                        sizeof(float) * (size_t)2 * kRowLen * R;  // P-hat accumulators [2 NIT][NT]
+                        sizeof(float) * (size_t)(kRowLen / 64 + 1) * 64 * R;  // P-hat accumulators [NIT + 1][NT]
     auto kern = rows_fast_kernel<R>;
     M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)(g.n1 / (2 * R)), (unsigned)nb);
