@@ -176,16 +176,19 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
         float2 v[F];
 #pragma unroll
         for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
+        int tix = 0;  // (l1 * r) mod n1, advanced incrementally
         for (int f = 0; f < nfold; ++f) {
 #pragma unroll
             for (int q = 0; q < F; ++q) {
                 const int l1 = f * F + q;
                 if (l1 < rows) {
                     const float2 a = s_in[l1 * 32 + lane];
-                    const float2 t = s_tw[(l1 * r) & (n1 - 1)];
+                    const float2 t = s_tw[tix];
                     v[q].x += a.x * t.x - a.y * t.y;
                     v[q].y += a.x * t.y + a.y * t.x;
                 }
+                tix += r;
+                if (tix >= n1) tix -= n1;
             }
         }
         fft_reg<F>(v, tw);
@@ -444,7 +447,9 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     mark(p, 0, 1, st);
 
     mark(p, 1, 0, st);
-    switch (std::min<int64_t>(g.n1, 32)) {
+    int64_t fdiv = 1;
+    while (fdiv < 32 && g.n1 % (fdiv * 2) == 0) fdiv *= 2;
+    switch (fdiv) {
         case 2: M2_TRY(launch_cols_fast<2>(p, nb, st, tw)); break;
         case 4: M2_TRY(launch_cols_fast<4>(p, nb, st, tw)); break;
         case 8: M2_TRY(launch_cols_fast<8>(p, nb, st, tw)); break;
@@ -455,7 +460,8 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
 
     mark(p, 2, 0, st);
     {
-        const int R = (int)std::min<int64_t>(kRowsR, g.n1 / 2);
+        int R = 1;  // low rows per CTA: largest power of two <= 4 dividing n1 / 2
+        while (R < kRowsR && (g.n1 / 2) % (R * 2) == 0) R *= 2;
         if (R == 4) M2_TRY(launch_rows_fast<4>(p, nb, st, tw, J, E, P));
         else if (R == 2) M2_TRY(launch_rows_fast<2>(p, nb, st, tw, J, E, P));
         else M2_TRY(launch_rows_fast<1>(p, nb, st, tw, J, E, P));

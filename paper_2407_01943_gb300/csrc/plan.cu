@@ -557,11 +557,47 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     double tmax_abs = 0;
     for (double v : ts) tmax_abs = std::max(tmax_abs, std::fabs(v));
     g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < 1e-12 ? 1 : 0;
-    g.width = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
-    g.beta = 2.30 * g.width;
-    g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
-    g.log_nf = ilog2(g.nf);
-    const double s_cells = (double)g.nf * g.df;  // exact: nf is a power of two
+    // ---- exec path, fine-grid length and spreading kernel ----
+    // generic path: nf = power of two >= 2 I (sigma in [2, 4)), w = ceil(log10(1/tol)) + 1, beta = 2.30 w.
+    // packed FP32 path: nf = smallest 2^a or 3 * 2^a >= 1.5 I (sigma in [1.5, 2)), w = ceil(1.25 log10(1/tol)) + 1,
+    // beta = 0.97 pi (1 - 1/(2 sigma)) w (exponential-of-semicircle kernel, Barnett et al. 2019).
+    if (opts.path < 0 || opts.path > 2) {
+        set_error("opts.path must be 0, 1 or 2");
+        return bail(M2_ERR_ARG);
+    }
+    const double span_t = ts.back() - ts.front();
+    bool packed_ok = false;
+    int64_t nf_packed = 0;
+    const int w_packed = std::min(16, std::max(2, (int)std::ceil(1.25 * std::log10(1.0 / p->tol)) + 1));
+    if (opts.precision == 32 && g.real_taper && opts.path != 1) {
+        const double target = std::max(1.5 * (double)g.I, 2048.0);
+        int64_t a2 = 2048, a3 = 3 * 2048;  // nf = 1024 * n1 with n1 even
+        while ((double)a2 < target) a2 <<= 1;
+        while ((double)a3 < target) a3 <<= 1;
+        nf_packed = std::min(a2, a3);
+        const double span = span_t * (double)nf_packed * g.df;
+        const bool wrap_p = span + w_packed + 2.0 >= (double)nf_packed;
+        const int64_t rows_p = wrap_p ? nf_packed / 1024 : (int64_t)std::ceil((span + w_packed + 2.0) / 1024.0);
+        packed_ok = nf_packed % 2048 == 0 && nf_packed <= (int64_t(3) << 20) && rows_p <= 64;
+    }
+    if (opts.path == 2 && !packed_ok) {
+        set_error("the packed FP32 path needs precision 32, a real modulated taper (f_lo + (I/2) df = 0), "
+                  "I <= 2^21 and a support of at most 64 rows of 1024 cells");
+        return bail(M2_ERR_ARG);
+    }
+    g.path = packed_ok ? 2 : 1;
+    if (g.path == 2) {
+        g.nf = nf_packed;
+        g.width = w_packed;
+        const double sigma = (double)g.nf / (double)g.I;
+        g.beta = 0.97 * kPi * (1.0 - 0.5 / sigma) * g.width;
+    } else {
+        g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
+        g.width = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
+        g.beta = 2.30 * g.width;
+    }
+    g.log_nf = ilog2(g.nf);                      // ceil(log2 nf)
+    const double s_cells = (double)g.nf * g.df;  // cells per unit time
     g.h = 1.0 / s_cells;
     const double span_cells = (ts.back() - ts.front()) * s_cells;
     g.wrap = (span_cells + g.width + 2.0 >= (double)g.nf) ? 1 : 0;
@@ -581,7 +617,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         const double d = ts[j] - g.t_ref;
         double uh, ul;
         two_prod(d, s_cells, uh, ul);
-        if (g.wrap) uh -= std::floor(uh / nf_d) * nf_d;  // exact: nf is a power of two
+        if (g.wrap) uh -= std::floor(uh / nf_d) * nf_d;  // exact: the result is a multiple of ulp(uh)
         const int64_t i0 = (int64_t)std::ceil(uh - half_w);
         const double off = ((double)i0 - uh) - ul;
         pts[j] = {i0, off, ord[j], j, uh};
@@ -613,28 +649,22 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         const int64_t n1 = g.nf / n2;
         return g.wrap ? n1 : std::min<int64_t>(n1, (last_cell + n2 - 1) / n2);
     };
-    if (opts.path < 0 || opts.path > 2) {
-        set_error("opts.path must be 0, 1 or 2");
-        return bail(M2_ERR_ARG);
-    }
-    const bool packed_ok = opts.precision == 32 && g.real_taper && g.nf >= 2048 && g.nf <= (int64_t(1) << 21) &&
-                           rows_for(1024) <= 64;
-    if (opts.path == 2 && !packed_ok) {
-        set_error("the packed FP32 path needs precision 32, a real modulated taper (f_lo + (I/2) df = 0), "
-                  "2048 <= nf <= 2^21 and a support of at most 64 rows of 1024 cells");
-        return bail(M2_ERR_ARG);
-    }
-    g.path = (opts.path == 1 || !packed_ok) ? 1 : 2;
     if (g.path == 2) {
+        g.n2 = 1024;
+        g.n1 = g.nf / 1024;
         g.log_n2 = 10;
-        g.log_n1 = g.log_nf - 10;
+        g.log_n1 = ilog2(g.n1);  // not used by the packed kernels (n1 = 2^a or 3 * 2^a)
     } else {
         g.log_n1 = g.log_nf / 2;
         g.log_n2 = g.log_nf - g.log_n1;
+        g.n1 = int64_t(1) << g.log_n1;
+        g.n2 = int64_t(1) << g.log_n2;
     }
-    g.n1 = int64_t(1) << g.log_n1;
-    g.n2 = int64_t(1) << g.log_n2;
     g.rows = rows_for(g.n2);
+    if (g.path == 2 && g.rows > 64) {
+        set_error("internal: packed path support exceeds 64 rows");
+        return bail(M2_ERR_ARG);
+    }
     g.kp = g.path == 2 ? (K + 1) / 2 : K;
     g.Lg = g.rows * g.n2;
     g.P = (int64_t)pts.size();
@@ -707,7 +737,8 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1, unit_roots(g.n1 / 2, g.n1, 1)));
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw2, unit_roots(g.n2 / 2, g.n2, 1)));
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twa,
-                             unit_roots(g.nf >> g.twb_bits, g.nf, int64_t(1) << g.twb_bits)));
+                             unit_roots((g.nf + (int64_t(1) << g.twb_bits) - 1) >> g.twb_bits, g.nf,
+                                        int64_t(1) << g.twb_bits)));
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twb, unit_roots(int64_t(1) << g.twb_bits, g.nf, 1)));
     if (g.path == 2) {
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twn1, unit_roots(g.n1, g.n1, 1)));
