@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--outputs", default="JEP",
+                    help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat)")
     ap.add_argument("--skip-gep", action="store_true",
                     help="plan from taper-shaped inputs instead of the FP64 GEP (profiling runs; "
                          "the exec kernels and their shapes are identical)")
@@ -127,7 +129,7 @@ class ClockSampler:
         return out
 
 
-def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int) -> float:
+def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: str = "JEP") -> float:
     """Compulsory bytes one launch of each exec kernel must move (per chunk of nb signals).
 
     spread : read x (N reals) + point records (cell int32, offset, source int32) + tapers (K x P),
@@ -145,7 +147,8 @@ def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int) -> float:
     if kernel == "cols":
         return nb * (grid + K * info["nf"] * csz)
     if kernel == "rows":
-        return nb * (K * I * csz + K * I * rsz + I * rsz) + I * csz
+        per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
+        return nb * per + I * csz
     raise KeyError(kernel)
 
 
@@ -237,8 +240,8 @@ def run_ours(args):
     info = plan.info
 
     x = torch.from_numpy(wl.x.astype(np.float32 if args.precision == 32 else np.float64)).to(dev)
-    J = torch.empty((B, wl.K, wl.I), dtype=cdt, device=dev)
-    E = torch.empty((B, wl.K, wl.I), dtype=rdt, device=dev)
+    J = torch.empty((B, wl.K, wl.I), dtype=cdt, device=dev) if "J" in args.outputs else None
+    E = torch.empty((B, wl.K, wl.I), dtype=rdt, device=dev) if "E" in args.outputs else None
     P = torch.empty((B, wl.I), dtype=rdt, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -293,7 +296,7 @@ def run_ours(args):
             continue
         avg_ms = kms[i] / klaunch[i]
         nb = min(B, info["chunk"])
-        byts = algorithmic_bytes(info, n, nb, csz, rsz)
+        byts = algorithmic_bytes(info, n, nb, csz, rsz, args.outputs)
         kern[n] = {"launches": int(klaunch[i]), "total_ms": float(kms[i]), "avg_us": 1e3 * avg_ms,
                    "alg_bytes_per_launch": byts, "gbs": byts / (avg_ms * 1e-3) / 1e9,
                    "share": float(kms[i] / max(sum(kms), 1e-12))}
@@ -353,6 +356,7 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: N={wl.N} samples ({'jittered' if 'jitter' in args.workload else 'grid'}), "
                                    f"K={wl.K}, f_w={wl.f_w:.3g}, I={wl.I}, B={B} signals per GPU per step",
                        "signals_per_gpu_per_step": B, "N": wl.N, "K": wl.K, "I": wl.I, "nf": info["nf"],
+                       "outputs": args.outputs,
                        "kernel_width": info["width"], "chunk": info["chunk"],
                        "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "gpu_launches": launches,

@@ -71,6 +71,7 @@ struct Geometry {
     int twb_bits = 0;     // low-bit width of the two-level nf twiddle table
     int path = 1;         // 1 = generic kernels, 2 = packed FP32 kernels
     int kp = 0;           // FFT signals per signal: K (generic) or ceil(K/2) taper pairs (packed)
+    int colF = 0;         // packed path: coset FFT length F (largest power of two <= 32 dividing n1)
 };
 
 }  // namespace m2
@@ -115,6 +116,8 @@ struct m2nufft_plan_s {
     void* d_twb = nullptr;         // [1 << twb_bits]  C: exp(-i 2 pi q / nf)
     void* d_twn1 = nullptr;        // packed path: [n1] C, exp(-i 2 pi q / n1) full circle
     void* d_tw1024 = nullptr;      // packed path: [1024] C, exp(-i 2 pi q / 1024) full circle
+    void* d_colT = nullptr;        // packed path: [F][1024] C, exp(-i 2 pi l2 C q / nf) (column-FFT output twiddle)
+    void* d_colB = nullptr;        // packed path: [C][1024] C, exp(-i 2 pi l2 r / nf) (per-coset factor)
     double* d_Lhat = nullptr;      // [K][I]
     double* d_Ehat = nullptr;      // [I]
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C

@@ -32,7 +32,8 @@ constexpr int kRowLen = 1024;     // n2 of the packed path
 constexpr int kRowPad = 1060;     // per-warp transpose / row buffer: >= 32 x 33, and 2*1060 = 8 (mod 32)
                                   // words so the epilogue's 4 rows x 4 columns per half-warp hit
                                   // 32 distinct banks
-constexpr int kRowsR = 4;         // low rows per CTA of the row pass (plus as many mirror rows)
+constexpr int kRowsR = 8;         // low rows per CTA of the row pass (plus as many mirror rows): runs of
+                                  // 8 consecutive bands, i.e. whole 32-byte sectors for |J|^2 and P-hat
 constexpr int kColWarps = 4;      // warps per CTA of the column pass
 
 struct Tw32 {
@@ -146,8 +147,9 @@ spread_packed_kernel(const float* __restrict__ x, int64_t N, const int32_t* __re
 template <int F>
 __global__ void __launch_bounds__(32 * kColWarps)
 cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, int Kp,
-                 const float2* __restrict__ tw_n1 /*[n1] full circle*/, const float2* __restrict__ twa,
-                 const float2* __restrict__ twb, int twb_bits, Tw32 tw, float2* __restrict__ Z) {
+                 const float2* __restrict__ tw_n1 /*[n1] full circle*/,
+                 const float2* __restrict__ colT /*[F][1024]: W_nf^{l2 C q}*/,
+                 const float2* __restrict__ colB /*[C][1024]: W_nf^{l2 r}*/, Tw32 tw, float2* __restrict__ Z) {
     extern __shared__ float2 smem_f2[];
     float2* s_in = smem_f2;           // [rows][32]
     float2* s_tw = s_in + rows * 32;  // [n1]
@@ -159,20 +161,17 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
     const int b = blockIdx.z;
     const int64_t n2 = kRowLen;
     const int C = n1 / F;
-    const int mask = (1 << twb_bits) - 1;
     const float2* gj = gp + ((int64_t)b * Kp + j) * Lg;
     float2* Zj = Z + ((int64_t)b * Kp + j) * (int64_t)n1 * n2;
 
     for (int l1 = warp; l1 < rows; l1 += kColWarps) s_in[l1 * 32 + lane] = gj[(int64_t)l1 * n2 + l2];
     for (int q = threadIdx.x; q < n1; q += blockDim.x) s_tw[q] = tw_n1[q];
-    for (int q = warp; q < F; q += kColWarps) {
-        const int e = l2 * C * q;  // < nf
-        s_T[q * 32 + lane] = cmulf(__ldg(twa + (e >> twb_bits)), __ldg(twb + (e & mask)));
-    }
+    for (int q = warp; q < F; q += kColWarps) s_T[q * 32 + lane] = colT[q * kRowLen + l2];
     __syncthreads();
 
     const int nfold = (rows + F - 1) / F;
     for (int r = warp; r < C; r += kColWarps) {
+        const float2 base = colB[(int64_t)r * kRowLen + l2];
         float2 v[F];
 #pragma unroll
         for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
@@ -192,8 +191,6 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
             }
         }
         fft_reg<F>(v, tw);
-        const int eb = l2 * r;
-        const float2 base = cmulf(__ldg(twa + (eb >> twb_bits)), __ldg(twb + (eb & mask)));
 #pragma unroll
         for (int q = 0; q < F; ++q) {
             const int k1 = r + C * q;
@@ -411,8 +408,8 @@ m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
     dim3 grid((unsigned)(kRowLen / 32), (unsigned)g.kp, (unsigned)nb);
     kern<<<grid, 32 * kColWarps, smem, st>>>(reinterpret_cast<const float2*>(p->d_g), g.Lg, (int)g.rows,
                                               (int)g.n1, g.kp, reinterpret_cast<const float2*>(p->d_twn1),
-                                              reinterpret_cast<const float2*>(p->d_twa),
-                                              reinterpret_cast<const float2*>(p->d_twb), g.twb_bits, tw,
+                                              reinterpret_cast<const float2*>(p->d_colT),
+                                              reinterpret_cast<const float2*>(p->d_colB), tw,
                                               reinterpret_cast<float2*>(p->d_Z));
     M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
@@ -462,7 +459,8 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     {
         int R = 1;  // low rows per CTA: largest power of two <= 4 dividing n1 / 2
         while (R < kRowsR && (g.n1 / 2) % (R * 2) == 0) R *= 2;
-        if (R == 4) M2_TRY(launch_rows_fast<4>(p, nb, st, tw, J, E, P));
+        if (R == 8) M2_TRY(launch_rows_fast<8>(p, nb, st, tw, J, E, P));
+        else if (R == 4) M2_TRY(launch_rows_fast<4>(p, nb, st, tw, J, E, P));
         else if (R == 2) M2_TRY(launch_rows_fast<2>(p, nb, st, tw, J, E, P));
         else M2_TRY(launch_rows_fast<1>(p, nb, st, tw, J, E, P));
     }

@@ -743,6 +743,28 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     if (g.path == 2) {
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twn1, unit_roots(g.n1, g.n1, 1)));
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, unit_roots(1024, 1024, 1)));
+        int64_t F = 1;
+        while (F < 32 && g.n1 % (F * 2) == 0) F *= 2;
+        g.colF = (int)F;
+        const int64_t C = g.n1 / F;
+        // colT[q][l2] = W_nf^{l2 C q}, colB[r][l2] = W_nf^{l2 r}
+        std::vector<double> tT(2 * F * 1024), tB(2 * C * 1024);
+        for (int64_t q = 0; q < F; ++q)
+            for (int64_t l2 = 0; l2 < 1024; ++l2) {
+                const int64_t e = (l2 * C * q) % g.nf;
+                const double x = 2.0 * (double)e / (double)g.nf;
+                tT[2 * (q * 1024 + l2)] = std::cos(kPi * x);
+                tT[2 * (q * 1024 + l2) + 1] = -std::sin(kPi * x);
+            }
+        for (int64_t r = 0; r < C; ++r)
+            for (int64_t l2 = 0; l2 < 1024; ++l2) {
+                const int64_t e = (l2 * r) % g.nf;
+                const double x = 2.0 * (double)e / (double)g.nf;
+                tB[2 * (r * 1024 + l2)] = std::cos(kPi * x);
+                tB[2 * (r * 1024 + l2) + 1] = -std::sin(kPi * x);
+            }
+        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_colT, tT));
+        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_colB, tB));
     }
 
     // ---- deconvolution / re-phasing factors ----
