@@ -147,6 +147,11 @@ def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: s
     if kernel == "cols":
         return nb * (grid + K * info["nf"] * csz)
     if kernel == "rows":
+        if info["path"] == 2:  # packed path: row FFTs only (L2-resident input and output)
+            return nb * 2 * ((K + 1) // 2) * info["nf"] * csz
+        per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
+        return nb * per + I * csz
+    if kernel == "epi":
         per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
         return nb * per + I * csz
     raise KeyError(kernel)
@@ -285,10 +290,10 @@ def run_ours(args):
     units_per_signal = wl.K * wl.N * wl.I
     value = world * args.steps * B * units_per_signal / (total_ms * 1e-3)
     chunks = -(-B // info["chunk"])
-    launches = args.steps * chunks * 3
+    launches = args.steps * chunks * (4 if info["path"] == 2 else 3)
 
     # ---- per-kernel roofline from the live event timing ----
-    names = ["spread", "cols", "rows"]
+    names = ["spread", "cols", "rows", "epi"]
     hbm_peak, peak_kind = measured_peaks()
     kern = {}
     for i, n in enumerate(names):

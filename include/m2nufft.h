@@ -188,11 +188,12 @@ m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info);
  * Instrumentation (no counterpart in the paper): per-kernel device timing.
  * While enabled, exec records a CUDA event pair around every kernel launch on
  * the launching stream.  m2nufft_get_timing waits for those events, returns
- * the summed milliseconds and launch counts of the three exec kernels
- * (index 0 = spread, 1 = column FFT, 2 = row FFT + epilogue) accumulated since
- * the previous call, and resets the accumulators.
- *   ms        host [3] or NULL
- *   launches  host [3] or NULL
+ * the summed milliseconds and launch counts of the exec kernels accumulated
+ * since the previous call (index 0 = spread, 1 = column FFT, 2 = row FFT,
+ * 3 = separate epilogue of the packed path; the generic path fuses its
+ * epilogue into index 2), and resets the accumulators.
+ *   ms        host [4] or NULL
+ *   launches  host [4] or NULL
  */
 m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable);
 m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);

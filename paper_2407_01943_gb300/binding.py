@@ -225,9 +225,9 @@ class Plan:
         _check(load().m2nufft_set_timing(self._h, 1 if enable else 0), "m2nufft_set_timing")
 
     def get_timing(self):
-        """(ms[3], launches[3]) of spread / column FFT / row FFT+epilogue since the last call."""
-        ms = np.zeros(3)
-        n = np.zeros(3, dtype=np.int64)
+        """(ms[4], launches[4]) of spread / column FFT / row FFT / packed epilogue since the last call."""
+        ms = np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
         _check(load().m2nufft_get_timing(self._h, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                "m2nufft_get_timing")
         return ms, n

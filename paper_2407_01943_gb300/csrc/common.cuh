@@ -122,12 +122,13 @@ struct m2nufft_plan_s {
     double* d_Ehat = nullptr;      // [I]
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C
     void* d_Z = nullptr;           // workspace [chunk][K][nf] C
+    void* d_X = nullptr;           // packed path workspace [chunk][K/2][1024][n1] C: row transforms, transposed
     std::vector<void*> allocations;
 
     // per-kernel timing (instrumentation): event pairs recorded by exec
     int timing = 0;
     std::vector<cudaEvent_t> ev_pool;       // free events
-    std::vector<cudaEvent_t> ev_rec[3][2];  // [kernel][begin/end] in launch order
-    double timing_ms[3] = {0, 0, 0};
-    int64_t timing_launches[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev_rec[4][2];  // [kernel][begin/end] in launch order
+    double timing_ms[4] = {0, 0, 0, 0};
+    int64_t timing_launches[4] = {0, 0, 0, 0};
 };

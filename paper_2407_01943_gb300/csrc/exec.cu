@@ -518,7 +518,7 @@ extern "C" m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* l
         return M2_ERR_ARG;
     }
     m2::DeviceGuard guard(p->device);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         auto& b = p->ev_rec[k][0];
         auto& e = p->ev_rec[k][1];
         const size_t n = std::min(b.size(), e.size());
@@ -534,7 +534,7 @@ extern "C" m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* l
         b.clear();
         e.clear();
     }
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         if (ms) ms[k] = p->timing_ms[k];
         if (launches) launches[k] = p->timing_launches[k];
         p->timing_ms[k] = 0;

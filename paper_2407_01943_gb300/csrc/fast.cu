@@ -32,8 +32,6 @@ constexpr int kRowLen = 1024;     // n2 of the packed path
 constexpr int kRowPad = 1060;     // per-warp transpose / row buffer: >= 32 x 33, and 2*1060 = 8 (mod 32)
                                   // words so the epilogue's 4 rows x 4 columns per half-warp hit
                                   // 32 distinct banks
-constexpr int kRowsR = 8;         // low rows per CTA of the row pass (plus as many mirror rows): runs of
-                                  // 8 consecutive bands, i.e. whole 32-byte sectors for |J|^2 and P-hat
 constexpr int kColWarps = 4;      // warps per CTA of the column pass
 
 struct Tw32 {
@@ -201,180 +199,139 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
 }
 
 // ---------------------------------------------------------------------------
-// row pass + unpack + epilogue
+// row pass: X[k1 + n1 k2] = sum_{l2} Z[k1][l2] W_1024^{l2 k2}, written transposed as
+// Xt[k2][k1] so that the epilogue reads and writes long contiguous runs.
+// CTA = R consecutive rows of one (signal, pair); one warp per row, 32 x 32 in
+// registers with one padded shared-memory transpose; the transformed rows are
+// staged in shared memory and written R rows at a time per k2.
 // ---------------------------------------------------------------------------
-// CTA t owns R low rows k1 = t R + lr (lr < R) and their mirrors n1 - k1; the
-// mirror of k1 = 0 is replaced by the other self-paired row n1/2.  Warp s
-// transforms the row of slot s (slots [0, R) low, [R, 2R) mirror).
 template <int R>
-__device__ __forceinline__ int slot_row(int slot, int t, int n1) {
-    if (slot < R) return t * R + slot;
-    const int k1 = t * R + (slot - R);
-    return k1 == 0 ? (n1 >> 1) : n1 - k1;
-}
-
-// Epilogue symmetry: the two tapers of a pair are real, so X(nf - k) = conj(X(k)) for
-// each of them, and the deconvolution factors satisfy s(-m) = conj(s(m)) (phi-hat is
-// real and even).  Hence J(-m) = conj(J(m)), |J(-m)|^2 = |J(m)|^2 and P(-m) = P(m):
-// each thread unpacks one position k of a low row (from Zp[k] and Zp[nf - k], the
-// latter in the mirror row) and writes both the output at k and the one at nf - k.
-// Rows 0 and n1/2 pair with themselves; the thread that owns them (CTA 0, lr = 0)
-// walks row 0 for k2 in [0, 512] and row n1/2 for k2 in [0, 512).
-template <int R>
-__global__ void __launch_bounds__(64 * R, (R <= 4 ? 2 : 1))
-rows_fast_kernel(const float2* __restrict__ Z, int n1, int Kp, int K, int I, int i_c, int nf,
-                 const float2* __restrict__ tw1024 /*[1024] full circle*/, Tw32 tw,
-                 const float2* __restrict__ deconv, float2* __restrict__ J, float* __restrict__ E,
-                 float* __restrict__ Pout) {
-    constexpr int NT = 64 * R;           // threads
-    constexpr int STEP = NT / R;         // k2 stride between a thread's positions (64)
-    constexpr int NIT = kRowLen / STEP;  // positions per thread (16; 17 for the self-paired owner)
+__global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1))
+rowfft_kernel(const float2* __restrict__ Z, int n1, int Kp, const float2* __restrict__ tw1024, Tw32 tw,
+              float2* __restrict__ Xt) {
+    constexpr int NT = 32 * R;
     extern __shared__ float2 smem_f2[];
-    float2* s_tw = smem_f2;              // [32 c][32 lane]: W_1024^{lane c}
-    float2* s_row = s_tw + kRowLen;      // [2R][kRowPad]
-    float* s_pacc = reinterpret_cast<float*>(s_row + 2 * R * kRowPad);  // [NIT + 1][NT], thread-private
+    float2* s_tw = smem_f2;          // [32 c][32 lane]: W_1024^{lane c}
+    float2* s_row = s_tw + kRowLen;  // [R][kRowPad]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int t = blockIdx.x;
-    const int b = blockIdx.y;
-    const int half = nf >> 1;
+    const int r0 = blockIdx.x * R;
+    const int j = blockIdx.y;
+    const int b = blockIdx.z;
+    const int64_t base = ((int64_t)b * Kp + j) * (int64_t)n1 * kRowLen;
 
     for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = tw1024[(q >> 5) * (q & 31)];
 
-    const int lr = threadIdx.x % R;
-    const int k2_0 = threadIdx.x / R;
-    const int rowL = t * R + lr;
-    const bool self = rowL == 0;         // owner of the self-paired rows 0 and n1/2
-    const int rowM = self ? (n1 >> 1) : n1 - rowL;
-    const int offL = lr * kRowPad, offM = (R + lr) * kRowPad;
-    const int npos = self ? NIT + 1 : NIT;
-
-    float* pacc = s_pacc + threadIdx.x;  // pacc[it * NT]
-    for (int it = 0; it < npos; ++it) pacc[it * NT] = 0.f;
-
-    const int my_row = slot_row<R>(warp, t, n1);
-    float2* S = s_row + warp * kRowPad;
-    const float2* Zrow = Z + ((int64_t)b * Kp * n1 + my_row) * kRowLen + lane;
-    const int64_t zpair = (int64_t)n1 * kRowLen;  // stride between taper pairs
-
-    // row of pair 0, prefetched into registers; the next pair's row is loaded while
-    // the current epilogue runs
+    const float2* Zr = Z + base + (int64_t)(r0 + warp) * kRowLen + lane;
     float2 v[32];
 #pragma unroll
-    for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zrow + 32 * a);
-
-    for (int j = 0; j < Kp; ++j) {
-        __syncthreads();  // previous epilogue done with s_row (and s_tw ready on j = 0)
-        {
-            fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
+    for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zr + 32 * a);
+    __syncthreads();  // s_tw ready
+    float2* S = s_row + warp * kRowPad;
+    fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int c = brev(q, 5);
-                S[c * 33 + lane] = cmulf(v[q], s_tw[c * 32 + lane]);
-            }
-            __syncwarp();
+    for (int q = 0; q < 32; ++q) {
+        const int c = brev(q, 5);
+        S[c * 33 + lane] = cmulf(v[q], s_tw[c * 32 + lane]);
+    }
+    __syncwarp();
 #pragma unroll
-            for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
-            __syncwarp();
-            fft_reg<32>(v, tw);  // over b for column c = lane: v[q] = X[lane + 32 brev(q)]
+    for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
+    __syncwarp();
+    fft_reg<32>(v, tw);  // over b for column c = lane: v[q] = X[lane + 32 brev(q)]
 #pragma unroll
-            for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
-        }
-        __syncthreads();
-        if (j + 1 < Kp) {
-            const float2* Zn = Zrow + (int64_t)(j + 1) * zpair;
-#pragma unroll
-            for (int a = 0; a < 32; ++a) v[a] = __ldcs(Zn + 32 * a);
-        }
-
-        const bool has_odd = (2 * j + 1) < K;
-        float2* J0 = J ? J + ((int64_t)b * K + 2 * j) * I : nullptr;
-        float2* J1 = (J && has_odd) ? J + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
-        float* E0 = E ? E + ((int64_t)b * K + 2 * j) * I : nullptr;
-        float* E1 = (E && has_odd) ? E + ((int64_t)b * K + 2 * j + 1) * I : nullptr;
+    for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
+    __syncthreads();
+    // Xt[k2][r0 + rr] for rr < R: consecutive threads take consecutive rows
+    float2* Xb = Xt + base + r0;
 #pragma unroll 4
-        for (int it = 0; it < npos; ++it) {
-            // position (slot offset, column) of k and of its partner nf - k
-            int o1, c1, o2, c2, r1, r2;
-            if (!self) {
-                c1 = k2_0 + STEP * it;
-                o1 = offL; r1 = rowL;
-                o2 = offM; r2 = rowM; c2 = kRowLen - 1 - c1;
-            } else if (it <= NIT / 2) {  // row 0, k2 in [0, 512]
-                c1 = k2_0 + STEP * it;
-                o1 = offL; r1 = 0;
-                o2 = offL; r2 = 0; c2 = (kRowLen - c1) & (kRowLen - 1);
-                if (c1 > kRowLen / 2) continue;
-            } else {                     // row n1/2, k2 in [0, 512)
-                c1 = k2_0 + STEP * (it - NIT / 2 - 1);
-                o1 = offM; r1 = rowM;
-                o2 = offM; r2 = rowM; c2 = kRowLen - 1 - c1;
+    for (int e = threadIdx.x; e < R * kRowLen; e += NT) {
+        const int rr = e % R, k2 = e / R;
+        Xb[(int64_t)k2 * n1 + rr] = s_row[rr * kRowPad + k2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epilogue: unpack the taper pairs, deconvolve, write J and |J|^2, average P-hat.
+// Thread = position k = k1 + n1 k2 with k2 <= k2max (k in the upper half-spectrum
+// side m >= 0) together with its partner nf - k = (n1 - k1, 1023 - k2), or
+// (0, 1024 - k2) for k1 = 0.  Both tapers of a pair are real, so X(nf - k) =
+// conj X(k) per taper and s(-m) = conj s(m): one thread computes J at k and
+// writes J(m) and conj J(m) = J(-m).  The deconvolution factor is loaded once
+// and reused for all K/2 pairs; P-hat is summed in registers.  Consecutive
+// threads take consecutive k1, so every load and store is a contiguous run.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+epi_kernel(const float2* __restrict__ Xt, int n1, int Kp, int K, int I, int i_c, int nf,
+           const float2* __restrict__ deconv, float2* __restrict__ J, float* __restrict__ E,
+           float* __restrict__ Pout) {
+    const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k2 = blockIdx.y;
+    const int b = blockIdx.z;
+    if (k1 >= n1) return;
+    const int half = nf >> 1;
+    int pk1, pk2;
+    if (k1 == 0) {
+        pk1 = 0;
+        pk2 = (kRowLen - k2) & (kRowLen - 1);
+    } else {
+        pk1 = n1 - k1;
+        pk2 = kRowLen - 1 - k2;
+    }
+    const int kk1 = k1 + n1 * k2;
+    const int kk2 = pk1 + n1 * pk2;
+    const int i1 = (kk1 < half ? kk1 : kk1 - nf) + i_c;
+    const int i2 = (kk2 < half ? kk2 : kk2 - nf) + i_c;
+    const bool v1 = (unsigned)i1 < (unsigned)I;
+    const bool v2 = (unsigned)i2 < (unsigned)I && kk2 != kk1;
+    if (!v1 && !v2) return;
+    float2 sd;
+    if (v1) {
+        sd = __ldg(deconv + i1);
+    } else {
+        sd = __ldg(deconv + i2);
+        sd.y = -sd.y;
+    }
+    const int64_t plane = (int64_t)n1 * kRowLen;
+    const float2* X1 = Xt + (int64_t)b * Kp * plane + (int64_t)k2 * n1 + k1;
+    const float2* X2 = Xt + (int64_t)b * Kp * plane + (int64_t)pk2 * n1 + pk1;
+    float pacc = 0.f;
+    for (int j = 0; j < Kp; ++j) {
+        const float2 A = __ldcs(X1 + (int64_t)j * plane);
+        const float2 Bc = __ldcs(X2 + (int64_t)j * plane);
+        // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
+        const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd);
+        const float p0 = j0.x * j0.x + j0.y * j0.y;
+        const int64_t o0 = ((int64_t)b * K + 2 * j) * I;
+        if (J) {
+            if (v1) __stcs(J + o0 + i1, j0);
+            if (v2) __stcs(J + o0 + i2, make_float2(j0.x, -j0.y));
+        }
+        if (E) {
+            if (v1) __stcs(E + o0 + i1, p0);
+            if (v2) __stcs(E + o0 + i2, p0);
+        }
+        pacc += p0;
+        if (2 * j + 1 < K) {
+            const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd);
+            const float p1 = j1.x * j1.x + j1.y * j1.y;
+            const int64_t o1 = o0 + I;
+            if (J) {
+                if (v1) __stcs(J + o1 + i1, j1);
+                if (v2) __stcs(J + o1 + i2, make_float2(j1.x, -j1.y));
             }
-            const int kk1 = r1 + n1 * c1;
-            const int kk2 = r2 + n1 * c2;
-            const int i1 = (kk1 < half ? kk1 : kk1 - nf) + i_c;
-            const int i2 = (kk2 < half ? kk2 : kk2 - nf) + i_c;
-            const bool v1 = (unsigned)i1 < (unsigned)I;
-            const bool v2 = (unsigned)i2 < (unsigned)I && kk2 != kk1;
-            if (!v1 && !v2) continue;
-            const float2 A = s_row[o1 + c1];
-            const float2 Bc = s_row[o2 + c2];
-            float2 sd;
-            if (v1) {
-                sd = __ldg(deconv + i1);
-            } else {
-                sd = __ldg(deconv + i2);
-                sd.y = -sd.y;
+            if (E) {
+                if (v1) __stcs(E + o1 + i1, p1);
+                if (v2) __stcs(E + o1 + i2, p1);
             }
-            // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
-            const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd);
-            const float p0 = j0.x * j0.x + j0.y * j0.y;
-            if (v1) {
-                if (J0) __stcs(J0 + i1, j0);
-                if (E0) __stcs(E0 + i1, p0);
-            }
-            if (v2) {
-                if (J0) __stcs(J0 + i2, make_float2(j0.x, -j0.y));
-                if (E0) __stcs(E0 + i2, p0);
-            }
-            float pp = p0;
-            if (has_odd) {
-                const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd);
-                const float p1 = j1.x * j1.x + j1.y * j1.y;
-                if (v1) {
-                    if (J1) __stcs(J1 + i1, j1);
-                    if (E1) __stcs(E1 + i1, p1);
-                }
-                if (v2) {
-                    if (J1) __stcs(J1 + i2, make_float2(j1.x, -j1.y));
-                    if (E1) __stcs(E1 + i2, p1);
-                }
-                pp += p1;
-            }
-            pacc[it * NT] += pp;
+            pacc += p1;
         }
     }
     if (Pout) {
-        const float invK = 1.0f / (float)K;
+        const float pv = pacc * (1.0f / (float)K);
         float* Pb = Pout + (int64_t)b * I;
-        for (int it = 0; it < npos; ++it) {
-            int c1, c2, r1, r2;
-            if (!self) {
-                c1 = k2_0 + STEP * it; r1 = rowL; r2 = rowM; c2 = kRowLen - 1 - c1;
-            } else if (it <= NIT / 2) {
-                c1 = k2_0 + STEP * it; r1 = 0; r2 = 0; c2 = (kRowLen - c1) & (kRowLen - 1);
-                if (c1 > kRowLen / 2) continue;
-            } else {
-                c1 = k2_0 + STEP * (it - NIT / 2 - 1); r1 = rowM; r2 = rowM; c2 = kRowLen - 1 - c1;
-            }
-            const int kk1 = r1 + n1 * c1;
-            const int kk2 = r2 + n1 * c2;
-            const int i1 = (kk1 < half ? kk1 : kk1 - nf) + i_c;
-            const int i2 = (kk2 < half ? kk2 : kk2 - nf) + i_c;
-            const float pv = pacc[it * NT] * invK;
-            if ((unsigned)i1 < (unsigned)I) __stcs(Pb + i1, pv);
-            if ((unsigned)i2 < (unsigned)I && kk2 != kk1) __stcs(Pb + i2, pv);
-        }
+        if (v1) __stcs(Pb + i1, pv);
+        if (v2) __stcs(Pb + i2, pv);
     }
 }
 
@@ -416,17 +373,15 @@ m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
 }
 
 template <int R>
-m2_status launch_rows_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw, float2* J, float* E,
-                           float* P) {
+m2_status launch_rowfft(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw) {
     const Geometry& g = p->g;
-    const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)2 * R * kRowPad) +
-                        sizeof(float) * (size_t)(kRowLen / 64 + 1) * 64 * R;  // P-hat accumulators [NIT + 1][NT]
-    auto kern = rows_fast_kernel<R>;
+    const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)R * kRowPad);
+    auto kern = rowfft_kernel<R>;
     M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)(g.n1 / (2 * R)), (unsigned)nb);
-    kern<<<grid, 64 * R, smem, st>>>(reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, g.kp, g.K, (int)g.I,
-                                     (int)g.i_c, (int)g.nf, reinterpret_cast<const float2*>(p->d_tw1024), tw,
-                                     reinterpret_cast<const float2*>(p->d_deconv), J, E, P);
+    dim3 grid((unsigned)(g.n1 / R), (unsigned)g.kp, (unsigned)nb);
+    kern<<<grid, 32 * R, smem, st>>>(reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, g.kp,
+                                     reinterpret_cast<const float2*>(p->d_tw1024), tw,
+                                     reinterpret_cast<float2*>(p->d_X));
     M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
 }
@@ -457,14 +412,25 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
 
     mark(p, 2, 0, st);
     {
-        int R = 1;  // low rows per CTA: largest power of two <= 4 dividing n1 / 2
-        while (R < kRowsR && (g.n1 / 2) % (R * 2) == 0) R *= 2;
-        if (R == 8) M2_TRY(launch_rows_fast<8>(p, nb, st, tw, J, E, P));
-        else if (R == 4) M2_TRY(launch_rows_fast<4>(p, nb, st, tw, J, E, P));
-        else if (R == 2) M2_TRY(launch_rows_fast<2>(p, nb, st, tw, J, E, P));
-        else M2_TRY(launch_rows_fast<1>(p, nb, st, tw, J, E, P));
+        int R = 1;  // rows per CTA: largest power of two <= 8 dividing n1
+        while (R < 8 && g.n1 % (R * 2) == 0) R *= 2;
+        if (R == 8) M2_TRY(launch_rowfft<8>(p, nb, st, tw));
+        else if (R == 4) M2_TRY(launch_rowfft<4>(p, nb, st, tw));
+        else M2_TRY(launch_rowfft<2>(p, nb, st, tw));
     }
     mark(p, 2, 1, st);
+
+    mark(p, 3, 0, st);
+    {
+        // positions k = k1 + n1 k2 on the m >= 0 side: k2 <= k2max where n1 k2 < I - i_c
+        const int64_t k2max = std::min<int64_t>(kRowLen / 2, (g.I - g.i_c + g.n1 - 1) / g.n1);
+        dim3 grid((unsigned)((g.n1 + 127) / 128), (unsigned)(k2max + 1), (unsigned)nb);
+        epi_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<const float2*>(p->d_X), (int)g.n1, g.kp, g.K, (int)g.I,
+                                         (int)g.i_c, (int)g.nf, reinterpret_cast<const float2*>(p->d_deconv), J,
+                                         E, P);
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    mark(p, 3, 1, st);
     return M2_OK;
 }
 

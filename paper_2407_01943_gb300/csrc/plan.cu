@@ -676,8 +676,9 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const size_t csz = opts.precision == 32 ? 8 : 16;
     {
         // chunk so that the FFT workspace of a chunk stays well inside L2
-        const size_t z_per_signal = (size_t)g.kp * g.nf * csz;
-        const size_t target = g.path == 2 ? (64u << 20) : (48u << 20);
+        // packed path: Z and the transposed row transforms are both live in L2
+        const size_t z_per_signal = (size_t)g.kp * g.nf * csz * (g.path == 2 ? 2 : 1);
+        const size_t target = g.path == 2 ? (72u << 20) : (48u << 20);
         int64_t chunk = std::max<int64_t>(1, (int64_t)(target / std::max<size_t>(z_per_signal, 1)));
         chunk = std::min<int64_t>(chunk, 1024);
         if (opts.max_batch > 0) chunk = std::min<int64_t>(chunk, opts.max_batch);
@@ -865,6 +866,11 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * g.kp * g.nf));
         p->d_g = dg;
         p->d_Z = dZ;
+        if (g.path == 2) {
+            float2* dX = nullptr;
+            M2_TRY_OR(pb.alloc(&dX, (size_t)g.chunk * g.kp * g.nf));
+            p->d_X = dX;
+        }
     } else {
         double2 *dg = nullptr, *dZ = nullptr;
         M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * g.kp * g.Lg));
