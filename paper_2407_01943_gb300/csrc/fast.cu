@@ -208,7 +208,7 @@ cols_fast_kernel(const float2* __restrict__ gp, int64_t Lg, int rows, int n1, in
 template <int R>
 __global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1))
 rowfft_kernel(const float2* __restrict__ Z, int n1, int Kp, const float2* __restrict__ tw1024, Tw32 tw,
-              float2* __restrict__ Xt) {
+              int k2max, float2* __restrict__ Xt) {
     constexpr int NT = 32 * R;
     extern __shared__ float2 smem_f2[];
     float2* s_tw = smem_f2;          // [32 c][32 lane]: W_1024^{lane c}
@@ -242,11 +242,16 @@ rowfft_kernel(const float2* __restrict__ Z, int n1, int Kp, const float2* __rest
 #pragma unroll
     for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
     __syncthreads();
-    // Xt[k2][r0 + rr] for rr < R: consecutive threads take consecutive rows
+    // Xt[k2][r0 + rr] for rr < R: consecutive threads take consecutive rows.  Only the
+    // columns the epilogue reads are written: k2 <= k2max and their partners k2 >= 1023 - k2max
+    // (and 1024 - k2 for row 0, which lies in the same two ranges).
     float2* Xb = Xt + base + r0;
+    const int nlo = k2max + 1;                  // k2 in [0, nlo)
+    const int nout = 2 * nlo;                   // plus k2 in [1024 - nlo, 1024)
 #pragma unroll 4
-    for (int e = threadIdx.x; e < R * kRowLen; e += NT) {
-        const int rr = e % R, k2 = e / R;
+    for (int e = threadIdx.x; e < R * nout; e += NT) {
+        const int rr = e % R, q = e / R;
+        const int k2 = q < nlo ? q : kRowLen - nout + q;
         Xb[(int64_t)k2 * n1 + rr] = s_row[rr * kRowPad + k2];
     }
 }
@@ -373,14 +378,14 @@ m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
 }
 
 template <int R>
-m2_status launch_rowfft(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw) {
+m2_status launch_rowfft(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& tw, int k2max) {
     const Geometry& g = p->g;
     const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)R * kRowPad);
     auto kern = rowfft_kernel<R>;
     M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)(g.n1 / R), (unsigned)g.kp, (unsigned)nb);
     kern<<<grid, 32 * R, smem, st>>>(reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, g.kp,
-                                     reinterpret_cast<const float2*>(p->d_tw1024), tw,
+                                     reinterpret_cast<const float2*>(p->d_tw1024), tw, k2max,
                                      reinterpret_cast<float2*>(p->d_X));
     M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
@@ -410,20 +415,20 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     }
     mark(p, 1, 1, st);
 
+    // positions k = k1 + n1 k2 on the m >= 0 side: k2 <= k2max where n1 k2 < I - i_c
+    const int k2max = (int)std::min<int64_t>(kRowLen / 2 - 1, (g.I - g.i_c + g.n1 - 1) / g.n1);
     mark(p, 2, 0, st);
     {
         int R = 1;  // rows per CTA: largest power of two <= 8 dividing n1
         while (R < 8 && g.n1 % (R * 2) == 0) R *= 2;
-        if (R == 8) M2_TRY(launch_rowfft<8>(p, nb, st, tw));
-        else if (R == 4) M2_TRY(launch_rowfft<4>(p, nb, st, tw));
-        else M2_TRY(launch_rowfft<2>(p, nb, st, tw));
+        if (R == 8) M2_TRY(launch_rowfft<8>(p, nb, st, tw, k2max));
+        else if (R == 4) M2_TRY(launch_rowfft<4>(p, nb, st, tw, k2max));
+        else M2_TRY(launch_rowfft<2>(p, nb, st, tw, k2max));
     }
     mark(p, 2, 1, st);
 
     mark(p, 3, 0, st);
     {
-        // positions k = k1 + n1 k2 on the m >= 0 side: k2 <= k2max where n1 k2 < I - i_c
-        const int64_t k2max = std::min<int64_t>(kRowLen / 2, (g.I - g.i_c + g.n1 - 1) / g.n1);
         dim3 grid((unsigned)((g.n1 + 127) / 128), (unsigned)(k2max + 1), (unsigned)nb);
         epi_kernel<<<grid, 128, 0, st>>>(reinterpret_cast<const float2*>(p->d_X), (int)g.n1, g.kp, g.K, (int)g.I,
                                          (int)g.i_c, (int)g.nf, reinterpret_cast<const float2*>(p->d_deconv), J,

@@ -676,11 +676,17 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const size_t csz = opts.precision == 32 ? 8 : 16;
     {
         // chunk so that the FFT workspace of a chunk stays well inside L2
-        // packed path: Z and the transposed row transforms are both live in L2
+        // generic path: keep a chunk's workspace within L2.  Packed path: its kernels need
+        // large grids more than L2 residency, so a chunk is up to 16 signals (workspace
+        // 2 * K/2 * nf complex per signal)
         const size_t z_per_signal = (size_t)g.kp * g.nf * csz * (g.path == 2 ? 2 : 1);
-        const size_t target = g.path == 2 ? (72u << 20) : (48u << 20);
-        int64_t chunk = std::max<int64_t>(1, (int64_t)(target / std::max<size_t>(z_per_signal, 1)));
-        chunk = std::min<int64_t>(chunk, 1024);
+        int64_t chunk;
+        if (g.path == 2) {
+            chunk = std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)((size_t(1) << 30) / z_per_signal)));
+        } else {
+            chunk = std::max<int64_t>(1, (int64_t)((48u << 20) / std::max<size_t>(z_per_signal, 1)));
+            chunk = std::min<int64_t>(chunk, 1024);
+        }
         if (opts.max_batch > 0) chunk = std::min<int64_t>(chunk, opts.max_batch);
         g.chunk = (int)chunk;
     }
