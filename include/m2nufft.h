@@ -198,6 +198,44 @@ m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info);
 m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable);
 m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);
 
+/*
+ * Leakage estimate without a plan and without allocating (the paper has no
+ * counterpart to this entry point; it computes the same L-hat / E-hat as the
+ * plan, App. B Eq. lambda_hat_ki, by the direct pair sum).
+ *
+ * For callers that may not call cudaMalloc: code running where the device
+ * allocator is off limits, e.g. worker threads of a host that reserves all
+ * device memory at start-up and hands out buffers from its own pool, or
+ * latency-critical loops where an allocation could synchronise the device
+ * and stall other work.  Such callers cannot create a plan (planning
+ * allocates), so everything here is passed in: the caller's own device
+ * buffers for inputs and outputs, plus a fixed 32 MiB scratch array that is
+ * part of this library's device image (every GPU that loads the library holds
+ * it until the process exits).  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *
+ *   t       device [N] FP64 sampling times (any order)
+ *   N       1 <= N <= 2^20
+ *   fs,f_w  as for m2nufft_plan (signal band |f| <= fs/2, 0 < f_w < fs/2)
+ *   K       1 <= K <= 16
+ *   fc      host, band-centre grid f_i = f_lo + i df, i < I
+ *   w       device [K][N] FP64 tapers in the order of t
+ *   lambda  device [K] FP64 nominal eigenvalues
+ *   Lhat    device [K][I] FP64 output, L_k^i = |lambda_k - lambda_k 2 f_w / D_k^i|
+ *   Ehat    device [I] FP64 output, E_i = (1/K) sum_k L_k^i
+ *   stream  cudaStream_t (NULL = legacy default stream); asynchronous
+ * Work is O(N^2 I K).  The scratch holds ceil(N/64) partial sums of K x I
+ * doubles: calls needing more than 32 MiB return M2_ERR_ARG with a message.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's partial sums (each call writes every entry it later reads), so
+ * calls that overlap on the GPU race: order them on one stream.
+ */
+m2_status m2nufft_leakage_static(const double* t, int64_t N, double fs, double f_w, int K,
+                                 const m2_fgrid* fc, const double* w, const double* lambda,
+                                 double* Lhat, double* Ehat, void* stream);
+
 /* Release every resource of the plan (synchronises its device first).  NULL is a no-op. */
 m2_status m2nufft_destroy(m2nufft_plan_t p);
 

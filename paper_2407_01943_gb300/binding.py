@@ -62,6 +62,8 @@ EXPORTS = [
     ("m2nufft_get_info", ctypes.c_int, [_VP, ctypes.POINTER(m2_info)]),
     ("m2nufft_set_timing", ctypes.c_int, [_VP, ctypes.c_int]),
     ("m2nufft_get_timing", ctypes.c_int, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    ("m2nufft_leakage_static", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              ctypes.POINTER(m2_fgrid), _VP, _VP, _VP, _VP, _VP]),
     ("m2nufft_destroy", ctypes.c_int, [_VP]),
     ("m2nufft_last_error", ctypes.c_char_p, []),
     ("m2nufft_version", ctypes.c_char_p, []),
@@ -261,6 +263,16 @@ def exec_batch(plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, stream=None
     hP = arr([_tptr(q) for q in Ps]) if Ps is not None else None
     st = load().m2nufft_exec_batch(hp, hx, n, hJ, hE, hP, _stream_handle(stream))
     _check(st, "m2nufft_exec_batch")
+
+
+def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: int, Lhat, Ehat, stream=None):
+    """L-hat [K, I] and E-hat [I] without a plan or any allocation (torch CUDA float64
+    tensors for t [N], w [K, N], lam [K], Lhat, Ehat)."""
+    K, N = int(w.shape[0]), int(w.shape[1])
+    fg = m2_fgrid(float(f_lo), float(df), int(I))
+    st = load().m2nufft_leakage_static(_tptr(t), N, float(fs), float(f_w), K, ctypes.byref(fg), _tptr(w),
+                                       _tptr(lam), _tptr(Lhat), _tptr(Ehat), _stream_handle(stream))
+    _check(st, "m2nufft_leakage_static")
 
 
 def version() -> str:
