@@ -192,6 +192,82 @@ __global__ void leakage_direct_kernel(int N, int K, int64_t I, const double* __r
     Eh[i] = s / K;
 }
 
+// Windowed leakage (general sampling at scale).  R(B|n,m) is the integral of
+// exp(i 2 pi nu (t_n - t_m)) over the signal band (Eq. gpss_matrix_b), so
+//   D_k(f) = integral over [f - f_max, f + f_max] of |W_k(phi)|^2 dphi,
+//   W_k(phi) = sum_n w_k(t_n) exp(-i 2 pi phi t_n).
+// |W_k|^2 is band-limited (its "time" support is |tau| <= T, the sampling
+// span), so sampled on a grid with spacing delta < 1/(2T) it is reproduced
+// exactly by a smooth band-limited interpolator; integrating that interpolant
+// over each window gives weight delta for interior samples and tabulated edge
+// weights within M samples of the two ends.
+// G[k][j] = |W_k(phi_j)|^2 and S[k][j] = sum_{q < j} G[k][q] (one CTA per taper).
+__global__ void leak_prefix_kernel(int64_t Jn, const double2* __restrict__ Wv, double* __restrict__ G,
+                                   double* __restrict__ S) {
+    __shared__ double s_part[1024];
+    const int k = blockIdx.x;
+    const double2* Wk = Wv + (int64_t)k * Jn;
+    double* Gk = G + (int64_t)k * Jn;
+    double* Sk = S + (int64_t)k * (Jn + 1);
+    const int64_t per = (Jn + blockDim.x - 1) / blockDim.x;
+    const int64_t j0 = (int64_t)threadIdx.x * per, j1 = min(Jn, j0 + per);
+    double acc = 0.0;
+    for (int64_t j = j0; j < j1; ++j) {
+        const double2 v = Wk[j];
+        const double g = v.x * v.x + v.y * v.y;
+        Gk[j] = g;
+        acc += g;
+    }
+    s_part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {  // fixed-order exclusive scan of the segment sums
+        double run = 0.0;
+        for (int q = 0; q < (int)blockDim.x; ++q) {
+            const double v = s_part[q];
+            s_part[q] = run;
+            run += v;
+        }
+        Sk[Jn] = run;
+    }
+    __syncthreads();
+    double run = s_part[threadIdx.x];
+    for (int64_t j = j0; j < j1; ++j) {
+        Sk[j] = run;
+        run += Gk[j];
+    }
+}
+
+// D_k(f_i) from the prefix sums and the edge weights; then L-hat / E-hat.
+__global__ void leak_window_kernel(int K, int64_t I, int64_t Jn, int r, int M, int Wi, double delta,
+                                   const double* __restrict__ G, const double* __restrict__ S,
+                                   const double* __restrict__ left /*[2M-1], p = -M+1..M-1*/,
+                                   const double* __restrict__ right /*[2M], p = Wi-M+1..Wi+M*/,
+                                   const double* __restrict__ lam, double fw, double* __restrict__ L,
+                                   double* __restrict__ Eh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    const int64_t base = M + i * r;
+    double sum = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double* Gk = G + (int64_t)k * Jn;
+        const double* Sk = S + (int64_t)k * (Jn + 1);
+        double D = delta * (Sk[base + Wi - M + 1] - Sk[base + M]);
+        for (int q = 0; q < 2 * M - 1; ++q) D += left[q] * Gk[base - M + 1 + q];
+        for (int q = 0; q < 2 * M; ++q) D += right[q] * Gk[base + Wi - M + 1 + q];
+        const double lh = lam[k] * 2.0 * fw / D;
+        const double l = fabs(lam[k] - lh);
+        L[(int64_t)k * I + i] = l;
+        sum += l;
+    }
+    Eh[i] = sum / K;
+}
+
+// fill a device array with ones (the unit signal whose eigencoefficients are the taper transforms)
+__global__ void ones_kernel(double* v, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // device allocation helpers
 // ---------------------------------------------------------------------------
@@ -374,6 +450,108 @@ int ilog2(int64_t v) {
     int l = 0;
     while ((int64_t(1) << l) < v) ++l;
     return l;
+}
+
+// Kcum(x) = integral_{-inf}^{x} kappa(u) du for the band-limited interpolator with transform
+// kappa_hat(tau) = delta psi(tau): psi = 1 for |tau| <= Tb, an erfc roll-off to 0 at tau_c = 1/delta - Tb.
+double kcum(double x, double delta, double Tb, const std::vector<double>& gx, const std::vector<double>& gw) {
+    const double tau_c = 1.0 / delta - Tb;
+    const double sig = (tau_c - Tb) / 16.0, mid = 0.5 * (Tb + tau_c);
+    double acc = 0.0;
+    for (size_t q = 0; q < gx.size(); ++q) {
+        const double tau = 0.5 * (gx[q] + 1.0) * tau_c;
+        const double psi = tau <= Tb ? 1.0 : 0.5 * std::erfc((tau - mid) / (std::sqrt(2.0) * sig));
+        acc += 0.5 * tau_c * gw[q] * psi * std::sin(2.0 * kPi * x * tau) / (kPi * tau);
+    }
+    return delta * (0.5 + acc);
+}
+
+// L-hat / E-hat for general sampling at scale (see leak_window_kernel).
+m2_status windowed_leakage(m2nufft_plan_s* p, const std::vector<double>& ts) {
+    const Geometry& g = p->g;
+    const int K = g.K;
+    const int64_t N = g.N, I = g.I;
+    const double fmax = 0.5 * p->fs;
+    const double T = std::max(ts.back() - ts.front(), 1e-300);
+    const int r = (int)std::max<double>(1.0, std::ceil(3.0 * T * g.df));  // delta <= 1/(3T)
+    const double delta = g.df / r;
+    const int M = 48;
+    const double Wd = 2.0 * fmax / delta;
+    const int Wi = (int)std::floor(Wd);
+    if (Wi < 2 * M + 2) {
+        set_error("windowed leakage needs fs/delta >= %d", 2 * M + 2);
+        return M2_ERR_ARG;
+    }
+    const int64_t Jn = (I - 1) * r + Wi + 2 * M + 2;
+    const double phi0 = g.f_lo - fmax - M * delta;
+
+    // edge weights
+    std::vector<double> gx, gw;
+    gauss_legendre(2000, gx, gw);
+    std::vector<double> left(2 * M - 1), right(2 * M);
+    for (int q = 0; q < 2 * M - 1; ++q) {
+        const int pp = -M + 1 + q;
+        left[q] = delta - kcum(-pp * delta, delta, T, gx, gw);
+    }
+    for (int q = 0; q < 2 * M; ++q) {
+        const int pp = Wi - M + 1 + q;
+        right[q] = kcum((Wd - pp) * delta, delta, T, gx, gw);
+    }
+
+    // W_k on the extended grid with the library's FP64 NuFFT (a temporary plan with the same tapers)
+    m2_fgrid fg{phi0, delta, Jn};
+    m2_opts o{};
+    o.precision = 64;
+    o.tol = 1e-13;
+    o.device = p->device;
+    o.max_batch = 1;
+    o.path = 1;
+    m2nufft_plan_t tp = nullptr;
+    m2_status st = m2nufft_plan_with_tapers(p->t.data(), N, p->fs, p->f_w, K, &fg, p->w.data(), nullptr, &o, &tp);
+    if (st != M2_OK) return st;
+    double *d_x = nullptr, *d_G = nullptr, *d_S = nullptr, *d_l = nullptr, *d_r = nullptr, *d_lam = nullptr;
+    double2* d_W = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        cudaFree(d_x);
+        cudaFree(d_G);
+        cudaFree(d_S);
+        cudaFree(d_l);
+        cudaFree(d_r);
+        cudaFree(d_lam);
+        cudaFree(d_W);
+        m2nufft_destroy(tp);
+    };
+    if ((e = cudaMalloc(&d_x, sizeof(double) * N)) != cudaSuccess ||
+        (e = cudaMalloc(&d_W, sizeof(double2) * K * Jn)) != cudaSuccess ||
+        (e = cudaMalloc(&d_G, sizeof(double) * K * Jn)) != cudaSuccess ||
+        (e = cudaMalloc(&d_S, sizeof(double) * K * (Jn + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&d_l, sizeof(double) * left.size())) != cudaSuccess ||
+        (e = cudaMalloc(&d_r, sizeof(double) * right.size())) != cudaSuccess ||
+        (e = cudaMalloc(&d_lam, sizeof(double) * K)) != cudaSuccess) {
+        cleanup();
+        set_error("windowed leakage allocation failed: %s", cudaGetErrorString(e));
+        return M2_ERR_NOMEM;
+    }
+    cudaMemcpy(d_l, left.data(), sizeof(double) * left.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_r, right.data(), sizeof(double) * right.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(d_lam, p->lambda.data(), sizeof(double) * K, cudaMemcpyHostToDevice);
+    ones_kernel<<<(unsigned)((N + 255) / 256), 256>>>(d_x, N);
+    st = m2nufft_exec(tp, d_x, 1, d_W, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != M2_OK) {
+        cleanup();
+        return st;
+    }
+    leak_prefix_kernel<<<K, 1024>>>(Jn, d_W, d_G, d_S);
+    leak_window_kernel<<<(unsigned)((I + 127) / 128), 128>>>(K, I, Jn, r, M, Wi, delta, d_G, d_S, d_l, d_r, d_lam,
+                                                             p->f_w, p->d_Lhat, p->d_Ehat);
+    e = cudaDeviceSynchronize();
+    cleanup();
+    if (e != cudaSuccess) {
+        set_error("windowed leakage kernels failed: %s", cudaGetErrorString(e));
+        return M2_ERR_CUDA;
+    }
+    return M2_OK;
 }
 
 template <typename R>
@@ -838,7 +1016,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                 return bail(M2_ERR_CUDA);
             }
             p->have_leakage = 1;
-        } else if ((double)N * (double)N * (double)g.I <= 2.0e10) {
+        } else if ((double)N * (double)N * (double)g.I <= 1.0e9) {
             double tbar = 0;
             for (double v : ts) tbar += v;
             tbar /= (double)N;
@@ -861,6 +1039,9 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                 set_error("leakage kernel failed: %s", cudaGetErrorString(e));
                 return bail(M2_ERR_CUDA);
             }
+            p->have_leakage = 1;
+        } else {
+            M2_TRY_OR(windowed_leakage(p, ts));
             p->have_leakage = 1;
         }
     }

@@ -342,3 +342,38 @@ def test_exec_batch_uneven_matches_single(dev):
         single = p.run(x[None, :], want=("J", "P"))
         torch.cuda.synchronize()
         assert torch.equal(single["J"][0], J) and torch.equal(single["P"][0], P)
+
+
+def test_leakage_windowed_matches_oracle_medium(dev):
+    """General sampling above the direct-sum size (N = 2048 jittered, I = 2^14):
+    D_k(f) by the windowed band-limited quadrature of |W_k|^2 (App. B,
+    Eq. lambda_hat_ki), against the oracle's dense pair sum on sampled bands."""
+    t = synth.jittered(2048, 0.4, 41)
+    fw, K, I = 5.0 / 2048, 8, 1 << 14
+    w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=64, tapers=w, lam=lam)
+    L, E = plan.leakage()
+    idx = sample_bands(I, 40, 5)
+    Lr, Er = oleak.leakage_at(t, w, lam, 1.0, fw, -0.5 + idx / I)
+    assert np.max(np.abs(L[:, idx] - Lr)) <= 1e-10 * max(np.max(np.abs(Lr)), 1e-3)
+    assert np.max(np.abs(E[idx] - Er)) <= 1e-10 * max(np.max(np.abs(Er)), 1e-3)
+    # the nominal band centre f = 0 has D = 2 f_w exactly (normalisation), so L = 0 there
+    assert np.max(np.abs(L[:, I // 2])) < 1e-9
+
+
+def test_leakage_windowed_full_size(dev):
+    """N = 16384 jittered, I = 2^18 (the benchmark workload): L-hat and E-hat
+    exist and match the oracle's pair sum on sampled bands (taper-shaped
+    inputs and fixed eigenvalues, so no GPU result feeds the oracle)."""
+    wl = synth.workload("jitter16k")
+    w = seeded_tapers(wl.K, wl.N, 11)
+    # scale each row so w^T R(B) w is near 2 f_w (keeps D near the paper's regime)
+    w = w * np.sqrt(2 * wl.f_w / np.sum(w ** 2, axis=1))[:, None]
+    lam = np.linspace(0.999, 0.95, wl.K)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, lam=lam)
+    L, E = plan.leakage()
+    idx = sample_bands(wl.I, 4, 9)[:6]
+    Lr, Er = oleak.leakage_at(wl.t, w, lam, 1.0, wl.f_w, wl.f_lo + idx * wl.df)
+    assert np.max(np.abs(L[:, idx] - Lr)) <= 1e-9 * max(np.max(np.abs(Lr)), 1e-3)
+    out = run_plan(plan, wl.x, dev, want=("Lhat", "Ehat"))
+    np.testing.assert_array_equal(out["Ehat"], E)
