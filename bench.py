@@ -51,8 +51,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="signals per internal chunk (0 = the plan's choice)")
-    ap.add_argument("--outputs", default="JEP",
-                    help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat)")
+    ap.add_argument("--outputs", default="JEPL",
+                    help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat), "
+                         "L (leakage estimates L-hat, E-hat)")
     ap.add_argument("--skip-gep", action="store_true",
                     help="plan from taper-shaped inputs instead of the FP64 GEP (profiling runs; "
                          "the exec kernels and their shapes are identical)")
@@ -250,6 +251,9 @@ def run_ours(args):
     J = torch.empty((B, wl.K, wl.I), dtype=cdt, device=dev) if "J" in args.outputs else None
     E = torch.empty((B, wl.K, wl.I), dtype=rdt, device=dev) if "E" in args.outputs else None
     P = torch.empty((B, wl.I), dtype=rdt, device=dev)
+    # leakage estimates (plan constants, App. B) are handed out with every exec
+    Lh = torch.empty((wl.K, wl.I), dtype=torch.float64, device=dev) if "L" in args.outputs else None
+    Eh = torch.empty((wl.I,), dtype=torch.float64, device=dev) if "L" in args.outputs else None
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def flush_l2():
@@ -265,7 +269,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         flush_l2()
-        plan.exec(x, J, E, P, stream=stream)
+        plan.exec(x, J, E, P, Lh, Eh, stream=stream)
     torch.cuda.synchronize()
 
     # ---- timed region: K device-timed steps, L2 flushed between them ----
@@ -281,7 +285,7 @@ def run_ours(args):
     for s in range(args.steps):
         flush_l2()
         evs[s][0].record(stream)
-        plan.exec(x, J, E, P, stream=stream)
+        plan.exec(x, J, E, P, Lh, Eh, stream=stream)
         evs[s][1].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -329,7 +333,7 @@ def run_ours(args):
         xd = torch.empty_like(x)
         for _ in range(2):
             xd.copy_(xh, non_blocking=True)
-            plan.exec(xd, J, E, P, stream=stream)
+            plan.exec(xd, J, E, P, Lh, Eh, stream=stream)
             ph.copy_(P, non_blocking=True)
         torch.cuda.synchronize()
         ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -339,7 +343,7 @@ def run_ours(args):
             flush_l2()
             ev_e[s][0].record(stream)
             xd.copy_(xh, non_blocking=True)
-            plan.exec(xd, J, E, P, stream=stream)
+            plan.exec(xd, J, E, P, Lh, Eh, stream=stream)
             ph.copy_(P, non_blocking=True)
             ev_e[s][1].record(stream)
         torch.cuda.synchronize()
