@@ -167,8 +167,13 @@ m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void
  *   Js, Es, Ps  host [nsig] device pointers ([K_s][I_s] complex, [K_s][I_s]
  *          real, [I_s] real); an entry or a whole array may be NULL
  *   stream as for m2nufft_exec
- * All plans must share one precision and one device.  Work is enqueued
- * in order on the stream; the same ordering rule as m2nufft_exec applies.
+ * All plans must share one precision and one device.  The whole batch runs
+ * as one CUDA graph launched on `stream`: signals of different plans run
+ * concurrently on internal streams inside the graph (signals of one plan in
+ * order), and the graph is cached per (plans, buffer pointers) and replayed
+ * on later calls with the same arguments (the first call for a new set of
+ * arguments captures and instantiates it).  A plan in the batch must not be
+ * used by other work that overlaps the batch on the device.
  */
 m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
                              void* const* Js, void* const* Es, void* const* Ps, void* stream);

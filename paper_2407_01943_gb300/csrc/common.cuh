@@ -82,6 +82,12 @@ namespace m2 {
 // Instrumentation: records a CUDA event (begin = 0 / end = 1) around kernel `kernel`
 // on stream `st` while timing is enabled for the plan.
 void mark(m2nufft_plan_s* p, int kernel, int which, cudaStream_t st);
+// Drop cached exec_batch graphs that reference plan p.
+void purge_batch_graphs(const m2nufft_plan_s* p);
+// One-time per-device set-up of the exec kernels' dynamic shared-memory limits.
+m2_status init_exec_kernels(int smem_optin);
+m2_status init_fast_kernels(int smem_optin);
+m2_status init_device_kernels(int device);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P,
                           cudaStream_t st);

@@ -15,7 +15,10 @@
 //             |J|^2 over the K tapers of the signal inside the CTA to form
 //             P-hat without atomics.
 #include <algorithm>
+#include <list>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -315,7 +318,6 @@ m2_status launch_spread(const m2nufft_plan_s* p, const R* x, int nb, cudaStream_
     const Geometry& g = p->g;
     const size_t smem = spread_smem<R>(g.K, CPLX);
     auto kern = spread_kernel<R, CPLX, KM>;
-    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)g.ntiles, (unsigned)nb);
     kern<<<grid, kSpreadTile, smem, st>>>(
         x, g.N, p->d_pt_src, p->d_pt_cell, reinterpret_cast<const R*>(p->d_pt_off), p->d_taper, g.P,
@@ -346,7 +348,6 @@ m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J
     {
         const size_t smem = cols_smem<R>(g);
         auto kern = cols_kernel<R>;
-        M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         dim3 grid((unsigned)(g.n2 / g.cw), (unsigned)g.K, (unsigned)nb);
         mark(p, 1, 0, st);
         kern<<<grid, 256, smem, st>>>(reinterpret_cast<const C*>(p->d_g), g.Lg, (int)g.rows, (int)g.n1,
@@ -361,7 +362,6 @@ m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J
     {
         const size_t smem = rows_smem<R>(g);
         auto kern = rows_kernel<R>;
-        M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         dim3 grid((unsigned)(g.n1 / g.rw), (unsigned)nb);
         mark(p, 2, 0, st);
         kern<<<grid, 256, smem, st>>>(reinterpret_cast<const C*>(p->d_Z), (int)g.n1, (int)g.n2, g.log_n2,
@@ -441,6 +441,24 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
 
 }  // namespace
 
+// Raise the dynamic shared-memory limit of every generic exec kernel to the device's opt-in
+// maximum, once per device (so no launch needs an attribute call).
+m2_status init_exec_kernels(int smem_optin) {
+    const void* funcs[] = {
+        (const void*)spread_kernel<float, false, 4>,  (const void*)spread_kernel<float, false, 8>,
+        (const void*)spread_kernel<float, false, 16>, (const void*)spread_kernel<float, true, 4>,
+        (const void*)spread_kernel<float, true, 8>,   (const void*)spread_kernel<float, true, 16>,
+        (const void*)spread_kernel<double, false, 4>, (const void*)spread_kernel<double, false, 8>,
+        (const void*)spread_kernel<double, false, 16>, (const void*)spread_kernel<double, true, 4>,
+        (const void*)spread_kernel<double, true, 8>,  (const void*)spread_kernel<double, true, 16>,
+        (const void*)cols_kernel<float>,              (const void*)cols_kernel<double>,
+        (const void*)rows_kernel<float>,              (const void*)rows_kernel<double>,
+    };
+    for (const void* f : funcs)
+        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+    return M2_OK;
+}
+
 cudaEvent_t take_event(m2nufft_plan_s* p) {
     cudaEvent_t e = nullptr;
     if (!p->ev_pool.empty()) {
@@ -473,6 +491,121 @@ extern "C" m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, vo
     return m2::exec_one(p, x, B, J, E, P, Lhat, Ehat, reinterpret_cast<cudaStream_t>(stream));
 }
 
+namespace m2 {
+namespace {
+
+// Uneven batches run as one cached CUDA graph: the per-signal work is captured with signals of
+// different plans on different internal streams (signals of one plan share a stream, since they
+// share that plan's workspace), joined back, instantiated once per distinct (plans, buffers)
+// key, and replayed with one cudaGraphLaunch on the caller's stream.
+constexpr int kBatchStreams = 8;
+constexpr size_t kMaxGraphs = 16;
+
+struct BatchResources {
+    bool ready = false;
+    cudaStream_t origin = nullptr;
+    cudaStream_t ws[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kBatchStreams] = {};
+};
+
+struct GraphEntry {
+    int device;
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+};
+
+std::mutex g_batch_mu;
+BatchResources g_batch_res[64];
+std::list<GraphEntry> g_graphs;  // most recently used first
+
+m2_status batch_resources(int dev, BatchResources** out) {
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d out of range", dev);
+        return M2_ERR_ARG;
+    }
+    BatchResources& r = g_batch_res[dev];
+    if (!r.ready) {
+        M2_CUDA_TRY(cudaStreamCreateWithFlags(&r.origin, cudaStreamNonBlocking));
+        M2_CUDA_TRY(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
+        for (int w = 0; w < kBatchStreams; ++w) {
+            M2_CUDA_TRY(cudaStreamCreateWithFlags(&r.ws[w], cudaStreamNonBlocking));
+            M2_CUDA_TRY(cudaEventCreateWithFlags(&r.join[w], cudaEventDisableTiming));
+        }
+        r.ready = true;
+    }
+    *out = &r;
+    return M2_OK;
+}
+
+m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                        void* const* Es, void* const* Ps, BatchResources& r, cudaGraphExec_t* out) {
+    // stream of each distinct plan, round robin in order of first appearance
+    std::unordered_map<const m2nufft_plan_s*, int> lane;
+    for (int64_t s = 0; s < nsig; ++s)
+        if (!lane.count(plans[s])) lane.emplace(plans[s], (int)(lane.size() % kBatchStreams));
+    M2_CUDA_TRY(cudaStreamBeginCapture(r.origin, cudaStreamCaptureModeThreadLocal));
+    m2_status st = M2_OK;
+    cudaError_t e = cudaEventRecord(r.fork, r.origin);
+    for (int w = 0; w < kBatchStreams && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(r.ws[w], r.fork, 0);
+    if (e != cudaSuccess) {
+        set_error("batch capture fork failed: %s", cudaGetErrorString(e));
+        st = M2_ERR_CUDA;
+    }
+    for (int64_t s = 0; s < nsig && st == M2_OK; ++s) {
+        m2nufft_plan_s* p = plans[s];
+        const int saved = p->timing;
+        p->timing = 0;
+        st = exec_one(p, xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr, Ps ? Ps[s] : nullptr, nullptr,
+                      nullptr, r.ws[lane[p]]);
+        p->timing = saved;
+    }
+    for (int w = 0; w < kBatchStreams && st == M2_OK; ++w) {
+        e = cudaEventRecord(r.join[w], r.ws[w]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(r.origin, r.join[w], 0);
+        if (e != cudaSuccess) {
+            set_error("batch capture join failed: %s", cudaGetErrorString(e));
+            st = M2_ERR_CUDA;
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(r.origin, &graph);
+    if (st == M2_OK && e != cudaSuccess) {
+        set_error("cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+        st = M2_ERR_CUDA;
+    }
+    if (st == M2_OK) {
+        e = cudaGraphInstantiate(out, graph, 0);
+        if (e != cudaSuccess) {
+            set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+            st = M2_ERR_CUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+}
+
+}  // namespace
+
+// Drop cached batch graphs that reference plan p (called before p is freed).
+void purge_batch_graphs(const m2nufft_plan_s* p) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        const auto& k = it->key;
+        const int64_t n = (int64_t)k[0];
+        bool hit = false;
+        for (int64_t s = 0; s < n && !hit; ++s) hit = k[1 + s] == (uintptr_t)p;
+        if (hit) {
+            cudaGraphExecDestroy(it->exec);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace m2
+
 extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
                                         void* const* Js, void* const* Es, void* const* Ps, void* stream) {
     m2::clear_error();
@@ -482,8 +615,8 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     }
     if (nsig == 0) return M2_OK;
     for (int64_t s = 0; s < nsig; ++s) {
-        if (!plans[s]) {
-            m2::set_error("m2nufft_exec_batch: plan %lld is NULL", (long long)s);
+        if (!plans[s] || !xs[s]) {
+            m2::set_error("m2nufft_exec_batch: plan or x %lld is NULL", (long long)s);
             return M2_ERR_ARG;
         }
         if (plans[s]->precision != plans[0]->precision || plans[s]->device != plans[0]->device) {
@@ -491,13 +624,36 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
             return M2_ERR_ARG;
         }
     }
-    m2::DeviceGuard guard(plans[0]->device);
+    const int dev = plans[0]->device;
+    m2::DeviceGuard guard(dev);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    for (int64_t s = 0; s < nsig; ++s) {
-        m2_status r = m2::exec_one(plans[s], xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr,
-                                   Ps ? Ps[s] : nullptr, nullptr, nullptr, st);
-        if (r != M2_OK) return r;
+    std::vector<uintptr_t> key;
+    key.reserve(1 + 5 * nsig);
+    key.push_back((uintptr_t)nsig);
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)plans[s]);
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)xs[s]);
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Js ? Js[s] : nullptr));
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Es ? Es[s] : nullptr));
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Ps ? Ps[s] : nullptr));
+
+    std::lock_guard<std::mutex> lock(m2::g_batch_mu);
+    for (auto it = m2::g_graphs.begin(); it != m2::g_graphs.end(); ++it) {
+        if (it->device == dev && it->key == key) {
+            m2::g_graphs.splice(m2::g_graphs.begin(), m2::g_graphs, it);
+            M2_CUDA_TRY(cudaGraphLaunch(m2::g_graphs.front().exec, st));
+            return M2_OK;
+        }
     }
+    m2::BatchResources* res = nullptr;
+    M2_TRY(m2::batch_resources(dev, &res));
+    cudaGraphExec_t exec = nullptr;
+    M2_TRY(m2::capture_batch(plans, xs, nsig, Js, Es, Ps, *res, &exec));
+    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec});
+    while (m2::g_graphs.size() > m2::kMaxGraphs) {
+        cudaGraphExecDestroy(m2::g_graphs.back().exec);
+        m2::g_graphs.pop_back();
+    }
+    M2_CUDA_TRY(cudaGraphLaunch(exec, st));
     return M2_OK;
 }
 

@@ -366,7 +366,6 @@ m2_status launch_cols_fast(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw3
     const Geometry& g = p->g;
     const size_t smem = sizeof(float2) * ((size_t)g.rows * 32 + g.n1 + (size_t)F * 32);
     auto kern = cols_fast_kernel<F>;
-    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)(kRowLen / 32), (unsigned)g.kp, (unsigned)nb);
     kern<<<grid, 32 * kColWarps, smem, st>>>(reinterpret_cast<const float2*>(p->d_g), g.Lg, (int)g.rows,
                                               (int)g.n1, g.kp, reinterpret_cast<const float2*>(p->d_twn1),
@@ -382,7 +381,6 @@ m2_status launch_rowfft(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& 
     const Geometry& g = p->g;
     const size_t smem = sizeof(float2) * ((size_t)kRowLen + (size_t)R * kRowPad);
     auto kern = rowfft_kernel<R>;
-    M2_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)(g.n1 / R), (unsigned)g.kp, (unsigned)nb);
     kern<<<grid, 32 * R, smem, st>>>(reinterpret_cast<const float2*>(p->d_Z), (int)g.n1, g.kp,
                                      reinterpret_cast<const float2*>(p->d_tw1024), tw, k2max,
@@ -392,6 +390,17 @@ m2_status launch_rowfft(m2nufft_plan_s* p, int nb, cudaStream_t st, const Tw32& 
 }
 
 }  // namespace
+
+m2_status init_fast_kernels(int smem_optin) {
+    const void* funcs[] = {
+        (const void*)cols_fast_kernel<2>,  (const void*)cols_fast_kernel<4>, (const void*)cols_fast_kernel<8>,
+        (const void*)cols_fast_kernel<16>, (const void*)cols_fast_kernel<32>, (const void*)rowfft_kernel<2>,
+        (const void*)rowfft_kernel<4>,     (const void*)rowfft_kernel<8>,
+    };
+    for (const void* f : funcs)
+        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+    return M2_OK;
+}
 
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, cudaStream_t st) {
     const Geometry& g = p->g;

@@ -13,6 +13,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -37,6 +38,27 @@ void set_error(const char* fmt, ...) {
     g_last_error = buf;
 }
 void clear_error() { g_last_error.clear(); }
+
+namespace {
+std::mutex g_init_mu;
+bool g_init_done[64] = {};
+}  // namespace
+
+// Called with `device` current, before any exec on it.
+m2_status init_device_kernels(int device) {
+    if (device < 0 || device >= 64) {
+        set_error("device ordinal %d out of range", device);
+        return M2_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_init_mu);
+    if (g_init_done[device]) return M2_OK;
+    int optin = 0;
+    M2_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    M2_TRY(init_exec_kernels(optin));
+    M2_TRY(init_fast_kernels(optin));
+    g_init_done[device] = true;
+    return M2_OK;
+}
 
 namespace {
 
@@ -302,6 +324,7 @@ struct PlanBuilder {
 
 void free_plan(m2nufft_plan_s* p) {
     if (!p) return;
+    purge_batch_graphs(p);
     {
         DeviceGuard guard(p->device);
         cudaDeviceSynchronize();
@@ -648,6 +671,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     int dev = opts.device;
     if (dev < 0) M2_CUDA_TRY(cudaGetDevice(&dev));
     DeviceGuard guard(dev);
+    M2_TRY(init_device_kernels(dev));
 
     auto* p = new m2nufft_plan_s();
     p->device = dev;

@@ -377,3 +377,32 @@ def test_leakage_windowed_full_size(dev):
     assert np.max(np.abs(L[:, idx] - Lr)) <= 1e-9 * max(np.max(np.abs(Lr)), 1e-3)
     out = run_plan(plan, wl.x, dev, want=("Lhat", "Ehat"))
     np.testing.assert_array_equal(out["Ehat"], E)
+
+
+def test_exec_batch_graph_replay_and_repeated_plans(dev):
+    """The cached batch graph: repeated plans in one batch (they share a
+    stream), replay on a second call, and a new graph after a plan is
+    destroyed; every result equals the per-signal exec bit for bit."""
+    ws = synth.batched_uneven(3, seed=7, n_min=300, n_max=1200)
+    plans = [pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                      tapers=seeded_tapers(wl.K, wl.N, i), max_batch=1) for i, wl in enumerate(ws)]
+    order = [0, 1, 0, 2, 1, 0]
+    rng = np.random.default_rng(1)
+    xs = [torch.from_numpy(rng.standard_normal(ws[i].N).astype(np.float32)).to(dev) for i in order]
+    Js = [torch.empty((ws[i].K, ws[i].I), dtype=torch.complex64, device=dev) for i in order]
+    Ps = [torch.empty((ws[i].I,), dtype=torch.float32, device=dev) for i in order]
+    bp = [plans[i] for i in order]
+    for _ in range(2):  # capture, then replay
+        for J in Js:
+            J.zero_()
+        pkg.exec_batch(bp, xs, Js, None, Ps)
+        torch.cuda.synchronize()
+        for i, x, J, P in zip(order, xs, Js, Ps):
+            single = plans[i].run(x[None, :], want=("J", "P"))
+            torch.cuda.synchronize()
+            assert torch.equal(single["J"][0], J) and torch.equal(single["P"][0], P)
+    plans[2].close()
+    keep = [k for k, i in enumerate(order) if i != 2]
+    pkg.exec_batch([bp[k] for k in keep], [xs[k] for k in keep], [Js[k] for k in keep], None,
+                   [Ps[k] for k in keep])
+    torch.cuda.synchronize()
