@@ -44,7 +44,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jitter16k", choices=["jitter16k", "periodic16k", "grid1024", "uneven"])
+    ap.add_argument("--workload", default="jitter16k",
+                    choices=["jitter16k", "periodic16k", "grid1024", "uneven", "serve"])
+    ap.add_argument("--requests", type=int, default=4000, help="requests of the serving trace")
+    ap.add_argument("--rate", type=float, default=2000.0, help="Poisson arrival rate of the serving trace (req/s)")
     ap.add_argument("--nsig", type=int, default=2048, help="signals of the uneven batch workload")
     ap.add_argument("--batch", type=int, default=32, help="signals per step per GPU")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
@@ -320,6 +323,61 @@ def run_uneven(args):
     return 0
 
 
+def run_serve(args):
+    """Serving (SURVEY config 5): Poisson arrivals of PSD requests over 64 fixed sampling patterns
+    (grid length uniform in [2048, 16384], jittered or Bernoulli-missing 10-30%, K = 8, I = 4G),
+    plans cached before the trace, 40 GB device-memory budget; continuous batching (4 slots,
+    up to 16 requests per launch) against the plain per-request path.  Plans use taper-shaped
+    inputs instead of 64 dense GEPs; the exec kernels and their shapes are the same."""
+    import torch
+
+    import paper_2407_01943_gb300 as pkg
+    import synth
+    from paper_2407_01943_gb300 import serve
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pkg.build()
+    pats = synth.serving_patterns(64, seed=rank)
+    t_plan = time.perf_counter()
+    plans = {i: pkg.Plan(pt["t"], 1.0, pt["f_w"], pt["K"], pt["f_lo"], pt["df"], pt["I"], precision=32,
+                         device=local, max_batch=16, tapers=synth.taper_like(pt["K"], pt["t"].shape[0], i))
+             for i, pt in enumerate(pats)}
+    t_plan = time.perf_counter() - t_plan
+
+    def trace(n, rate, seed):
+        arr = synth.poisson_arrivals(rate, n, seed) if rate > 0 else np.zeros(n)
+        rng = np.random.default_rng(seed + 1)
+        out = []
+        for k, a in enumerate(arr):
+            pid = int(rng.integers(0, len(pats)))
+            out.append(serve.Request(k, pid, rng.standard_normal(pats[pid]["t"].shape[0]).astype(np.float32),
+                                     float(a)))
+        return out
+
+    budget = 40 << 30
+    srv = serve.PSDServer(plans, mem_budget=budget, slots=4, max_batch=16, device=local)
+    srv.serve(trace(200, 0, 99))                               # warm-up (allocator, pinned pools)
+    loaded = srv.serve(trace(args.requests, args.rate, 1))
+    plain = serve.serve_plain(plans, trace(args.requests, args.rate, 1), device=local)
+    sat = srv.serve(trace(args.requests, 0, 2))               # all requests at t = 0
+    sat_plain = serve.serve_plain(plans, trace(min(args.requests, 1000), 0, 2), device=local)
+    line = {
+        "metric": METRIC, "value": sat["throughput_units_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving: 64 cached patterns, G uniform in [2048, 16384], K = 8, I = 4G; "
+                               f"{args.requests} requests; continuous batching, 4 slots, <= 16 per launch, "
+                               f"40 GB budget", "rate_req_per_s": args.rate},
+        "served_at_rate": loaded, "plain_at_rate": plain,
+        "served_saturated": sat, "plain_saturated": sat_plain,
+        "plan_seconds": t_plan,
+    }
+    print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -505,6 +563,8 @@ def main():
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -1,0 +1,66 @@
+"""Continuous-batching server: every request completes, and each result is
+the same alone (one exec with B = 1) and in the mix (batched with other
+requests and patterns, several slots in flight)."""
+import numpy as np
+import pytest
+
+import synth
+from tests._util import TOL, rel_l2
+
+torch = pytest.importorskip("torch")
+pkg = pytest.importorskip("paper_2407_01943_gb300")
+from paper_2407_01943_gb300 import serve  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _patterns(n=6):
+    pats = synth.serving_patterns(n, seed=5, n_min=300, n_max=1500)
+    plans = {}
+    for i, pt in enumerate(pats):
+        plans[i] = pkg.Plan(pt["t"], 1.0, pt["f_w"], 4, pt["f_lo"], pt["df"], pt["I"], precision=32,
+                            tapers=synth.taper_like(4, pt["t"].shape[0], i), max_batch=8)
+    return pats, plans
+
+
+def test_server_results_equal_alone():
+    torch.cuda.set_device(0)
+    pats, plans = _patterns()
+    arr = synth.poisson_arrivals(20000.0, 80, seed=3)   # bursty: batches of several requests form
+    rng = np.random.default_rng(4)
+    reqs = []
+    for k, a in enumerate(arr):
+        pid = int(rng.integers(0, len(pats)))
+        N = pats[pid]["t"].shape[0]
+        reqs.append(serve.Request(k, pid, rng.standard_normal(N).astype(np.float32), float(a)))
+    srv = serve.PSDServer(plans, mem_budget=2 << 30, slots=3, max_batch=6)
+    stats = srv.serve(reqs)
+    assert stats["requests"] == 80 and stats["p99_ms"] > 0
+    for r in reqs:
+        assert r.done >= r.arrival and r.P is not None
+        p = plans[r.pattern]
+        x = torch.from_numpy(r.x[None, :]).cuda()
+        alone = p.run(x, want=("P",))["P"].cpu().numpy()[0]
+        assert np.array_equal(alone, r.P)
+        assert rel_l2(r.P, alone) <= TOL[32]
+    for p in plans.values():
+        p.close()
+
+
+def test_server_respects_memory_budget():
+    torch.cuda.set_device(0)
+    pats, plans = _patterns(2)
+    srv = serve.PSDServer(plans, mem_budget=sum(p.info["device_bytes"] for p in plans.values())
+                          + 3 * srv_bytes(plans), slots=2, max_batch=8)
+    rng = np.random.default_rng(0)
+    reqs = [serve.Request(k, k % 2, rng.standard_normal(pats[k % 2]["t"].shape[0]).astype(np.float32), 0.0)
+            for k in range(10)]
+    stats = srv.serve(reqs)
+    assert stats["requests"] == 10
+    assert srv.in_use == 0
+    for p in plans.values():
+        p.close()
+
+
+def srv_bytes(plans):
+    return max(p.N * 4 + p.I * 4 + p.K * p.I * 12 for p in plans.values())
