@@ -358,9 +358,9 @@ def run_serve(args):
     srv = serve.PSDServer(plans, mem_budget=budget, slots=4, max_batch=16, device=local)
     srv.serve(trace(200, 0, 99))                               # warm-up (allocator, pinned pools)
     loaded = srv.serve(trace(args.requests, args.rate, 1))
-    plain = serve.serve_plain(plans, trace(args.requests, args.rate, 1), device=local)
+    plain = srv.serve_plain(trace(args.requests, args.rate, 1))
     sat = srv.serve(trace(args.requests, 0, 2))               # all requests at t = 0
-    sat_plain = serve.serve_plain(plans, trace(min(args.requests, 1000), 0, 2), device=local)
+    sat_plain = srv.serve_plain(trace(args.requests, 0, 2))
     line = {
         "metric": METRIC, "value": sat["throughput_units_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
         "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -373,6 +373,7 @@ def run_serve(args):
         "plan_seconds": t_plan,
     }
     print(json.dumps(line), flush=True)
+    srv.close()
     for p in plans.values():
         p.close()
     return 0

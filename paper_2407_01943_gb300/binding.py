@@ -17,6 +17,7 @@ import numpy as np
 from . import _build_lib
 
 M2_OK = 0
+M2_OUT_J, M2_OUT_E, M2_OUT_P = 1, 2, 4
 STATUS_NAMES = {0: "M2_OK", 1: "M2_ERR_ARG", 2: "M2_ERR_NOMEM", 3: "M2_ERR_BUDGET", 4: "M2_ERR_GEP",
                 5: "M2_ERR_CUDA", 6: "M2_ERR_TIMEOUT", 7: "M2_ERR_CANCELLED"}
 
@@ -69,6 +70,17 @@ EXPORTS = [
     ("m2nufft_version", ctypes.c_char_p, []),
 ]
 
+# entry points of include/m2serve.h
+SERVE_EXPORTS = [
+    ("m2serve_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_uint, ctypes.POINTER(_VP)]),
+    ("m2serve_run_trace", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("m2serve_stats", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("m2serve_destroy", ctypes.c_int, [_VP]),
+]
+
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
 
@@ -87,7 +99,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             if not os.path.exists(_build_lib.LIB_PATH):
                 raise RuntimeError("libm2nufft.so is not built; run paper_2407_01943_gb300.build()")
             L = ctypes.CDLL(_build_lib.LIB_PATH)
-            for name, res, args in EXPORTS:
+            for name, res, args in EXPORTS + SERVE_EXPORTS:
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
@@ -273,6 +285,39 @@ def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: 
     st = load().m2nufft_leakage_static(_tptr(t), N, float(fs), float(f_w), K, ctypes.byref(fg), _tptr(w),
                                        _tptr(lam), _tptr(Lhat), _tptr(Ehat), _stream_handle(stream))
     _check(st, "m2nufft_leakage_static")
+
+
+def server_create(plans, mem_budget: int, slots: int, max_batch: int, outputs: int):
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle.value for p in plans])
+    h = _VP()
+    _check(load().m2serve_create(hp, n, mem_budget, slots, max_batch, outputs, ctypes.byref(h)), "m2serve_create")
+    return h
+
+
+def server_run(h, patterns, arrivals, xs, ps, plain: bool):
+    """Replay a trace; xs / ps are lists of float32 numpy arrays (inputs / P-hat destinations)."""
+    n = len(patterns)
+    pat = np.ascontiguousarray(patterns, dtype=np.int32)
+    arr = np.ascontiguousarray(arrivals, dtype=np.float64)
+    hx = (_VP * n)(*[x.ctypes.data for x in xs])
+    hpo = (_VP * n)(*[q.ctypes.data for q in ps])
+    lat = np.zeros(n)
+    st = load().m2serve_run_trace(h, n, pat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(arr), hx, hpo,
+                                  _dptr(lat), 1 if plain else 0)
+    _check(st, "m2serve_run_trace")
+    return lat
+
+
+def server_stats(h):
+    a = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check(load().m2serve_stats(h, ctypes.byref(a), ctypes.byref(b)), "m2serve_stats")
+    return a.value, b.value
+
+
+def server_destroy(h):
+    load().m2serve_destroy(h)
 
 
 def version() -> str:

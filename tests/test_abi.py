@@ -14,10 +14,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "m2nufft.h")
 
 
-def declared_functions():
-    src = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="m2nufft_"):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(m2nufft_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"\w+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -49,3 +49,12 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(binding.m2_opts) == 40
     assert binding.m2_opts.path.offset == 32
     assert binding.m2_opts.tol.offset == 8 and binding.m2_opts.mem_budget.offset == 16
+
+
+def test_server_header_exports():
+    hdr = os.path.join(ROOT, "include", "m2serve.h")
+    names = declared_functions(hdr, "m2serve_")
+    assert names == sorted(n for n, _, _ in binding.SERVE_EXPORTS)
+    lib = ctypes.CDLL(pkg.build())
+    for n in names:
+        assert hasattr(lib, n), n

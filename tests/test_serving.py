@@ -35,6 +35,7 @@ def test_server_results_equal_alone():
         reqs.append(serve.Request(k, pid, rng.standard_normal(N).astype(np.float32), float(a)))
     srv = serve.PSDServer(plans, mem_budget=2 << 30, slots=3, max_batch=6)
     stats = srv.serve(reqs)
+    assert stats["launches"] < 80  # requests were batched
     assert stats["requests"] == 80 and stats["p99_ms"] > 0
     for r in reqs:
         assert r.done >= r.arrival and r.P is not None
@@ -43,6 +44,12 @@ def test_server_results_equal_alone():
         alone = p.run(x, want=("P",))["P"].cpu().numpy()[0]
         assert np.array_equal(alone, r.P)
         assert rel_l2(r.P, alone) <= TOL[32]
+    # the plain path on the same server gives the same results too
+    plain_reqs = [serve.Request(r.rid, r.pattern, r.x, r.arrival) for r in reqs]
+    srv.serve_plain(plain_reqs)
+    for a, b in zip(reqs, plain_reqs):
+        assert np.array_equal(a.P, b.P)
+    srv.close()
     for p in plans.values():
         p.close()
 
@@ -57,7 +64,10 @@ def test_server_respects_memory_budget():
             for k in range(10)]
     stats = srv.serve(reqs)
     assert stats["requests"] == 10
-    assert srv.in_use == 0
+    srv.close()
+    with pytest.raises(pkg.M2Error) as e:  # not even one request per slot fits
+        serve.PSDServer(plans, mem_budget=sum(p.info["device_bytes"] for p in plans.values()) + 1000, slots=2)
+    assert e.value.status == 3
     for p in plans.values():
         p.close()
 
