@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--chunk", type=int, default=0, help="signals per internal chunk (0 = the plan's choice)")
+    ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="exec path: 0 automatic, 1 generic, 2 packed four-kernel, 3 packed persistent kernel")
     ap.add_argument("--outputs", default="JEPL",
                     help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat), "
                          "L (leakage estimates L-hat, E-hat)")
@@ -140,7 +142,7 @@ def profiled_traffic(workload: str, kernel: str, nb: int):
     signals per launch; None if there is no capture for this kernel/workload or the kernel source
     changed since it was taken."""
     import hashlib
-    names = {"epi": "epi_kernel"}
+    names = {"epi": "epi_kernel", "pipe": "pipe_kernel"}
     if kernel not in names:
         return None
     path = os.path.join(ROOT, "profiles", f"{names[kernel]}_{workload}_traffic.json")
@@ -180,6 +182,13 @@ def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: s
     if kernel == "epi":
         per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
         return nb * per + I * csz
+    if kernel == "pipe":
+        # the whole path in one launch over nb signals: read x, write J, |J|^2, P-hat; the plan's
+        # point records, tapers and deconvolution factors once; the intermediates (spread grids,
+        # column-FFT and row-FFT workspaces) are consumed from L2 and are not compulsory traffic
+        per = N * rsz + I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
+        shared = N * (8 + rsz) + K * N * rsz + I * csz
+        return nb * per + shared
     raise KeyError(kernel)
 
 
@@ -294,7 +303,15 @@ def run_uneven(args):
     pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: capture + instantiate
     torch.cuda.synchronize()
     t_capture = time.perf_counter() - t0
+    pkg.binding.batch_pipe_profile()  # reset the stage accounting
     ms_batch = timed(lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream))
+    stage_split = None
+    if all(p.info["path"] >= 2 for p in plans):
+        busy, waitms, nitems = pkg.binding.batch_pipe_profile()
+        tot = max(float(busy.sum()), 1e-12)
+        stage_split = {n: {"items": int(nitems[i]), "busy_ms_sum": float(busy[i]), "share": float(busy[i] / tot),
+                           "avg_item_us": float(1e3 * busy[i] / max(nitems[i], 1)), "wait_ms_sum": float(waitms[i])}
+                       for i, n in enumerate(["spread", "cols", "rows", "epi"])}
 
     def plain():
         for p, x, J, E, P in zip(plans, xs, Js, Es, Ps):
@@ -308,13 +325,17 @@ def run_uneven(args):
         "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"uneven batch: {args.nsig} signals, grid length log-uniform in [1024, 16384], "
-                               f"Markov gaps 15%, K in {{4,6,8}}, I = 4G; m2nufft_exec_batch (one CUDA graph)",
+                               f"Markov gaps 15%, K in {{4,6,8}}, I = 4G; m2nufft_exec_batch (one CUDA graph: "
+                               f"one persistent-kernel launch over all signals)",
                    "signals": args.nsig, "units_per_step": units,
                    "l2": "flushed between timed steps (512 MiB write + read-back)"},
         "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                              "host_wall_s": wall_plain},
         "batch_over_plain": ms_plain / ms_batch,
-        "gpu_launches": 4 * args.nsig,
+        "pipe_stages": stage_split,
+        "gpu_launches": 1 if all(p.info["path"] >= 2 for p in plans) else 4 * args.nsig,
+        "plain_gpu_launches_per_step": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
+                                           for p in plans),
         "plan_seconds": t_plan, "capture_seconds": t_capture,
     }
     print(json.dumps(line), flush=True)
@@ -404,10 +425,10 @@ def run_ours(args):
         # taper-shaped rows and placeholder eigenvalues: the exec kernels and their shapes are the same
         plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local,
                         tapers=synth.taper_like(wl.K, wl.N, 0), lam=np.linspace(0.999, 0.99, wl.K),
-                        max_batch=args.chunk)
+                        max_batch=args.chunk, path=args.path)
     else:
         plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local,
-                        max_batch=args.chunk)
+                        max_batch=args.chunk, path=args.path)
     t_plan = time.perf_counter() - t_plan
     info = plan.info
 
@@ -456,6 +477,13 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     plan.set_timing(False)
     kms, klaunch = plan.get_timing()
+    stage_split = None
+    if info["path"] == 3:
+        busy, waitms, nitems = plan.get_pipe_profile()
+        tot = max(float(busy.sum()), 1e-12)
+        stage_split = {n: {"items": int(nitems[i]), "busy_ms_sum": float(busy[i]), "share": float(busy[i] / tot),
+                           "avg_item_us": float(1e3 * busy[i] / max(nitems[i], 1)), "wait_ms_sum": float(waitms[i])}
+                       for i, n in enumerate(["spread", "cols", "rows", "epi"])}
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
@@ -466,18 +494,19 @@ def run_ours(args):
     units_per_signal = wl.K * wl.N * wl.I
     value = world * args.steps * B * units_per_signal / (total_ms * 1e-3)
     chunks = -(-B // info["chunk"])
-    launches = args.steps * chunks * (4 if info["path"] == 2 else 3)
+    pipelined = info["path"] == 3
+    launches = args.steps * (1 if pipelined else chunks * (4 if info["path"] == 2 else 3))
+    per_launch = B if pipelined else min(B, info["chunk"])
 
     # ---- per-kernel roofline from the live event timing ----
-    names = ["spread", "cols", "rows", "epi"]
+    names = ["pipe", "", "", ""] if pipelined else ["spread", "cols", "rows", "epi"]
     hbm_peak, peak_kind = measured_peaks()
     kern = {}
     for i, n in enumerate(names):
         if klaunch[i] == 0:
             continue
         avg_ms = kms[i] / klaunch[i]
-        nb = min(B, info["chunk"])
-        byts = algorithmic_bytes(info, n, nb, csz, rsz, args.outputs)
+        byts = algorithmic_bytes(info, n, per_launch, csz, rsz, args.outputs)
         kern[n] = {"launches": int(klaunch[i]), "total_ms": float(kms[i]), "avg_us": 1e3 * avg_ms,
                    "alg_bytes_per_launch": byts, "gbs": byts / (avg_ms * 1e-3) / 1e9,
                    "share": float(kms[i] / max(sum(kms), 1e-12))}
@@ -488,7 +517,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
                     "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"],
-                    "traffic": profiled_traffic(args.workload, dom, min(B, info["chunk"]))}
+                    "traffic": profiled_traffic(args.workload, dom, per_launch)}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -539,11 +568,12 @@ def run_ours(args):
                                    f"K={wl.K}, f_w={wl.f_w:.3g}, I={wl.I}, B={B} signals per GPU per step",
                        "signals_per_gpu_per_step": B, "N": wl.N, "K": wl.K, "I": wl.I, "nf": info["nf"],
                        "outputs": args.outputs,
-                       "kernel_width": info["width"], "chunk": info["chunk"],
+                       "kernel_width": info["width"], "chunk": info["chunk"], "exec_path": info["path"],
                        "l2": "flushed between timed steps (512 MiB write + read-back)", "parallelism": f"replicas x{world}"},
             "gpu_launches": launches,
             "roofline": roofline,
             "kernels": kern,
+            "pipe_stages": stage_split,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

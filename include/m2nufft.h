@@ -88,9 +88,12 @@ typedef struct {
                            (including GEP scratch); 0 = unlimited */
     int device;         /* CUDA device ordinal; < 0 = the caller's current device */
     int max_batch;      /* signals processed per internal chunk; <= 0 = automatic */
-    int path;           /* exec kernels: 0 = automatic, 1 = generic (any precision/grid),
-                           2 = packed FP32 path (real tapers, nf >= 2048, support <= 64 rows
-                           of 1024 cells; M2_ERR_ARG if the plan does not qualify) */
+    int path;           /* exec kernels: 0 = automatic (3 where the plan qualifies, else 1),
+                           1 = generic (any precision/grid),
+                           2 = packed FP32 path as four kernels per chunk of signals,
+                           3 = packed FP32 path as one persistent pipelined kernel per exec;
+                           2 and 3 need real tapers, nf >= 2048 and a support of <= 64 rows
+                           of 1024 cells (M2_ERR_ARG if the plan does not qualify) */
 } m2_opts;
 
 /* Geometry of a plan, for callers that size buffers or compute rooflines. */
@@ -108,7 +111,8 @@ typedef struct {
     int real_taper;      /* 1 when the modulated tapers are real (f_lo + (I/2) df == 0) */
     int integer_grid;    /* 1 when fs * t_n are all integers, so R(B) = I */
     int chunk;           /* signals per internal chunk */
-    int path;            /* exec kernels in use: 1 = generic, 2 = packed FP32 */
+    int path;            /* exec kernels in use: 1 = generic, 2 = packed FP32 (four kernels),
+                            3 = packed FP32 (persistent pipelined kernel) */
     size_t device_bytes; /* device memory held by the plan */
     double gep_seconds;  /* wall time of the GEP during planning (0 if tapers were given) */
 } m2_info;
@@ -156,6 +160,10 @@ m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double
  * reported here; device faults surface at the caller's next synchronisation.
  * Calls on one plan must not overlap on the device (they share the plan's
  * workspace); order them on one stream or synchronise between streams.
+ * Path 3 runs all B signals in one launch; the first call for a new B builds
+ * that launch's work list (synchronous upload, not allowed during stream
+ * capture).  Its inter-CTA waits are bounded (2 s each): a launch that gave up
+ * writes a status word, and the next exec on the plan returns M2_ERR_TIMEOUT.
  */
 m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P,
                        double* Lhat, double* Ehat, void* stream);
@@ -168,12 +176,16 @@ m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void
  *          real, [I_s] real); an entry or a whole array may be NULL
  *   stream as for m2nufft_exec
  * All plans must share one precision and one device.  The whole batch runs
- * as one CUDA graph launched on `stream`: signals of different plans run
- * concurrently on internal streams inside the graph (signals of one plan in
- * order), and the graph is cached per (plans, buffer pointers) and replayed
- * on later calls with the same arguments (the first call for a new set of
- * arguments captures and instantiates it).  A plan in the batch must not be
- * used by other work that overlaps the batch on the device.
+ * as one CUDA graph launched on `stream`, cached per (plans, buffer pointers)
+ * and replayed on later calls with the same arguments (the first call for a
+ * new set of arguments builds and instantiates it).  When every plan is a
+ * packed FP32 plan (path 2 or 3) the graph is a single launch of the
+ * persistent pipelined kernel over all nsig signals, with its own workspace
+ * ring (the plans' workspaces are not used); otherwise signals of different
+ * plans run concurrently on internal streams inside the graph (signals of one
+ * plan in order).  A plan in the batch must not be used by other work that
+ * overlaps the batch on the device.  M2_ERR_TIMEOUT: an earlier replay of this
+ * batch gave up a bounded wait (see m2nufft_exec).
  */
 m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
                              void* const* Js, void* const* Es, void* const* Ps, void* stream);
@@ -196,12 +208,27 @@ m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info);
  * the summed milliseconds and launch counts of the exec kernels accumulated
  * since the previous call (index 0 = spread, 1 = column FFT, 2 = row FFT,
  * 3 = separate epilogue of the packed path; the generic path fuses its
- * epilogue into index 2), and resets the accumulators.
+ * epilogue into index 2; path 3 records its single persistent kernel at
+ * index 0), and resets the accumulators.
  *   ms        host [4] or NULL
  *   launches  host [4] or NULL
  */
 m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable);
 m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);
+
+/*
+ * Instrumentation of the persistent pipelined kernel: each work item adds
+ * its duration (after its dependency wait), and the time spent waiting for
+ * that dependency, to per-stage sums.  For a plan p (path 3) the sums cover
+ * its exec launches made while timing was enabled (m2nufft_set_timing); for
+ * p = NULL they cover the launches of the most recently launched
+ * all-packed m2nufft_exec_batch graph.  Returns the sums since the previous
+ * call and resets them; synchronises the device.  Index 0 = spread,
+ * 1 = column DFTs, 2 = row FFTs, 3 = epilogue.  Durations are summed over
+ * work items (CTA time, not wall time): their ratios give the stage split.
+ *   busy_ms, wait_ms  host [4] or NULL;  items  host [4] or NULL
+ */
+m2_status m2nufft_get_pipe_profile(m2nufft_plan_t p, double* busy_ms, double* wait_ms, int64_t* items);
 
 /*
  * Leakage estimate without a plan and without allocating (the paper has no
@@ -240,6 +267,17 @@ m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);
 m2_status m2nufft_leakage_static(const double* t, int64_t N, double fs, double f_w, int K,
                                  const m2_fgrid* fc, const double* w, const double* lambda,
                                  double* Lhat, double* Ehat, void* stream);
+
+/*
+ * Self-test of the bounded waits of the persistent pipelined kernel (no
+ * counterpart in the paper).  Launches that kernel on one work item whose
+ * dependency counter is never incremented, waits for it on `stream`, and
+ * returns M2_ERR_TIMEOUT when the wait gave up after timeout_ms (1..10000),
+ * the kernel returned and its status word names work item 0 -- the expected
+ * outcome; any other outcome returns M2_ERR_CUDA.  Faults and hangs nothing:
+ * the wait is bounded by the device's global timer.  Synchronous.
+ */
+m2_status m2nufft_pipe_selftest(int timeout_ms, void* stream);
 
 /* Release every resource of the plan (synchronises its device first).  NULL is a no-op. */
 m2_status m2nufft_destroy(m2nufft_plan_t p);

@@ -65,6 +65,8 @@ EXPORTS = [
     ("m2nufft_get_timing", ctypes.c_int, [_VP, _DP, ctypes.POINTER(ctypes.c_int64)]),
     ("m2nufft_leakage_static", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               ctypes.POINTER(m2_fgrid), _VP, _VP, _VP, _VP, _VP]),
+    ("m2nufft_pipe_selftest", ctypes.c_int, [ctypes.c_int, _VP]),
+    ("m2nufft_get_pipe_profile", ctypes.c_int, [_VP, _DP, _DP, ctypes.POINTER(ctypes.c_int64)]),
     ("m2nufft_destroy", ctypes.c_int, [_VP]),
     ("m2nufft_last_error", ctypes.c_char_p, []),
     ("m2nufft_version", ctypes.c_char_p, []),
@@ -246,6 +248,16 @@ class Plan:
                "m2nufft_get_timing")
         return ms, n
 
+    def get_pipe_profile(self):
+        """Persistent kernel (path 3): per-stage (spread, columns, rows, epilogue) summed item
+        time in ms, summed dependency-wait time in ms and item counts since the last call."""
+        busy, wait = np.zeros(4), np.zeros(4)
+        n = np.zeros(4, dtype=np.int64)
+        _check(load().m2nufft_get_pipe_profile(self._h, _dptr(busy), _dptr(wait),
+                                               n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "m2nufft_get_pipe_profile")
+        return busy, wait, n
+
     def close(self):
         if getattr(self, "_h", None):
             load().m2nufft_destroy(self._h)
@@ -285,6 +297,23 @@ def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: 
     st = load().m2nufft_leakage_static(_tptr(t), N, float(fs), float(f_w), K, ctypes.byref(fg), _tptr(w),
                                        _tptr(lam), _tptr(Lhat), _tptr(Ehat), _stream_handle(stream))
     _check(st, "m2nufft_leakage_static")
+
+
+def batch_pipe_profile():
+    """Stage accounting (busy ms, wait ms, items per stage) of the most recently launched
+    all-packed exec_batch graph, since the previous call."""
+    busy, wait = np.zeros(4), np.zeros(4)
+    n = np.zeros(4, dtype=np.int64)
+    _check(load().m2nufft_get_pipe_profile(None, _dptr(busy), _dptr(wait),
+                                           n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+           "m2nufft_get_pipe_profile")
+    return busy, wait, n
+
+
+def pipe_selftest(timeout_ms: int, stream=None) -> int:
+    """Bounded-wait self-test of the persistent kernel; returns the raw status
+    (M2_ERR_TIMEOUT is the expected outcome)."""
+    return int(load().m2nufft_pipe_selftest(int(timeout_ms), _stream_handle(stream)))
 
 
 def server_create(plans, mem_budget: int, slots: int, max_batch: int, outputs: int):

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -69,7 +70,7 @@ struct Geometry {
     int rw = 0;           // rows per CTA in the row pass
     int chunk = 1;        // signals per chunk
     int twb_bits = 0;     // low-bit width of the two-level nf twiddle table
-    int path = 1;         // 1 = generic kernels, 2 = packed FP32 kernels
+    int path = 1;         // 1 = generic kernels, 2 = packed FP32 kernels, 3 = packed, persistent pipelined kernel
     int kp = 0;           // FFT signals per signal: K (generic) or ceil(K/2) taper pairs (packed)
     int colF = 0;         // packed path: coset FFT length F (largest power of two <= 32 dividing n1)
 };
@@ -87,10 +88,28 @@ void purge_batch_graphs(const m2nufft_plan_s* p);
 // One-time per-device set-up of the exec kernels' dynamic shared-memory limits.
 m2_status init_exec_kernels(int smem_optin);
 m2_status init_fast_kernels(int smem_optin);
+m2_status init_pipe_kernels(int smem_optin);
 m2_status init_device_kernels(int device);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P,
                           cudaStream_t st);
+// Persistent pipelined kernel of the packed path (pipe.cu).
+struct PipeLaunch;
+void pipe_free(PipeLaunch* L);
+// all B signals of plan p in one launch (cached launch configuration per B)
+m2_status exec_pipe(m2nufft_plan_s* p, const float* x, int64_t B, float2* J, float* E, float* P, cudaStream_t st);
+// create the cached launch configuration for B signals (not allowed during stream capture)
+m2_status pipe_prepare(m2nufft_plan_s* p, int64_t B);
+// uneven batch of packed plans: signal s of plans[s]; owns its ring workspace
+m2_status pipe_batch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                            void* const* Es, void* const* Ps, PipeLaunch** out);
+m2_status pipe_batch_run(PipeLaunch* L, cudaStream_t st);
+// M2_ERR_TIMEOUT (once) if an earlier launch of L gave up waiting
+m2_status pipe_check(PipeLaunch* L);
+// a cached batch graph containing L was launched (its stage accounting is the one reported for NULL)
+void pipe_batch_mark_launched(PipeLaunch* L);
+// stage accounting of the most recently launched batch (device buffer of 12 counters), or NULL
+unsigned long long* pipe_last_batch_profile(int* device);
 }  // namespace m2
 
 struct m2nufft_plan_s {
@@ -130,6 +149,11 @@ struct m2nufft_plan_s {
     void* d_Z = nullptr;           // workspace [chunk][K][nf] C
     void* d_X = nullptr;           // packed path workspace [chunk][K/2][1024][n1] C: row transforms, transposed
     std::vector<void*> allocations;
+    // persistent pipelined path: launch configurations by batch size, and a mapped pinned
+    // status word [abort, status, item] that a launch writes if a wait gives up
+    std::map<int64_t, m2::PipeLaunch*> pipe_cache;
+    int* pipe_status = nullptr;
+    unsigned long long* d_pipe_prof = nullptr;  // per-stage busy/wait accounting while timing is enabled
 
     // per-kernel timing (instrumentation): event pairs recorded by exec
     int timing = 0;

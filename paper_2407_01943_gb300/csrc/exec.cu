@@ -383,6 +383,9 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     C* J = reinterpret_cast<C*>(Jv);
     R* E = reinterpret_cast<R*>(Ev);
     R* P = reinterpret_cast<R*>(Pv);
+    if constexpr (std::is_same<R, float>::value) {
+        if (g.path == 3) return exec_pipe(p, x, B, J, E, P, st);  // all B signals in one launch
+    }
     for (int64_t b0 = 0; b0 < B; b0 += g.chunk) {
         const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
         C* Jc = J ? J + b0 * g.K * g.I : nullptr;
@@ -513,7 +516,13 @@ struct GraphEntry {
     int device;
     std::vector<uintptr_t> key;
     cudaGraphExec_t exec;
+    PipeLaunch* pipe;  // persistent-kernel batch (owned), or NULL for a captured per-signal batch
 };
+
+void drop_entry(GraphEntry& e) {
+    cudaGraphExecDestroy(e.exec);
+    if (e.pipe) pipe_free(e.pipe);
+}
 
 std::mutex g_batch_mu;
 BatchResources g_batch_res[64];
@@ -544,6 +553,9 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
     std::unordered_map<const m2nufft_plan_s*, int> lane;
     for (int64_t s = 0; s < nsig; ++s)
         if (!lane.count(plans[s])) lane.emplace(plans[s], (int)(lane.size() % kBatchStreams));
+    // launch configurations of pipelined plans are created before the capture (they allocate)
+    for (const auto& kv : lane)
+        if (kv.first->g.path == 3) M2_TRY(pipe_prepare(const_cast<m2nufft_plan_s*>(kv.first), 1));
     M2_CUDA_TRY(cudaStreamBeginCapture(r.origin, cudaStreamCaptureModeThreadLocal));
     m2_status st = M2_OK;
     cudaError_t e = cudaEventRecord(r.fork, r.origin);
@@ -585,6 +597,27 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
     return st;
 }
 
+// All-packed batch: one persistent-kernel launch (counter reset + kernel) captured as a graph.
+m2_status capture_pipe_batch(PipeLaunch* L, BatchResources& r, cudaGraphExec_t* out) {
+    M2_CUDA_TRY(cudaStreamBeginCapture(r.origin, cudaStreamCaptureModeThreadLocal));
+    m2_status st = pipe_batch_run(L, r.origin);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(r.origin, &graph);
+    if (st == M2_OK && e != cudaSuccess) {
+        set_error("cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+        st = M2_ERR_CUDA;
+    }
+    if (st == M2_OK) {
+        e = cudaGraphInstantiate(out, graph, 0);
+        if (e != cudaSuccess) {
+            set_error("cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+            st = M2_ERR_CUDA;
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+}
+
 }  // namespace
 
 // Drop cached batch graphs that reference plan p (called before p is freed).
@@ -596,7 +629,7 @@ void purge_batch_graphs(const m2nufft_plan_s* p) {
         bool hit = false;
         for (int64_t s = 0; s < n && !hit; ++s) hit = k[1 + s] == (uintptr_t)p;
         if (hit) {
-            cudaGraphExecDestroy(it->exec);
+            drop_entry(*it);
             it = g_graphs.erase(it);
         } else {
             ++it;
@@ -640,6 +673,10 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     for (auto it = m2::g_graphs.begin(); it != m2::g_graphs.end(); ++it) {
         if (it->device == dev && it->key == key) {
             m2::g_graphs.splice(m2::g_graphs.begin(), m2::g_graphs, it);
+            if (m2::g_graphs.front().pipe) {
+                M2_TRY(m2::pipe_check(m2::g_graphs.front().pipe));
+                m2::pipe_batch_mark_launched(m2::g_graphs.front().pipe);
+            }
             M2_CUDA_TRY(cudaGraphLaunch(m2::g_graphs.front().exec, st));
             return M2_OK;
         }
@@ -647,10 +684,22 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     m2::BatchResources* res = nullptr;
     M2_TRY(m2::batch_resources(dev, &res));
     cudaGraphExec_t exec = nullptr;
-    M2_TRY(m2::capture_batch(plans, xs, nsig, Js, Es, Ps, *res, &exec));
-    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec});
+    m2::PipeLaunch* pipe = nullptr;
+    bool all_packed = plans[0]->precision == 32;
+    for (int64_t s = 0; s < nsig && all_packed; ++s) all_packed = plans[s]->g.path >= 2;
+    if (all_packed) {
+        M2_TRY(m2::pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
+        const m2_status cs = m2::capture_pipe_batch(pipe, *res, &exec);
+        if (cs != M2_OK) {
+            m2::pipe_free(pipe);
+            return cs;
+        }
+    } else {
+        M2_TRY(m2::capture_batch(plans, xs, nsig, Js, Es, Ps, *res, &exec));
+    }
+    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec, pipe});
     while (m2::g_graphs.size() > m2::kMaxGraphs) {
-        cudaGraphExecDestroy(m2::g_graphs.back().exec);
+        m2::drop_entry(m2::g_graphs.back());
         m2::g_graphs.pop_back();
     }
     M2_CUDA_TRY(cudaGraphLaunch(exec, st));

@@ -56,6 +56,7 @@ m2_status init_device_kernels(int device) {
     M2_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     M2_TRY(init_exec_kernels(optin));
     M2_TRY(init_fast_kernels(optin));
+    M2_TRY(init_pipe_kernels(optin));
     g_init_done[device] = true;
     return M2_OK;
 }
@@ -328,6 +329,9 @@ void free_plan(m2nufft_plan_s* p) {
     {
         DeviceGuard guard(p->device);
         cudaDeviceSynchronize();
+        for (auto& kv : p->pipe_cache) pipe_free(kv.second);
+        if (p->pipe_status) cudaFreeHost(p->pipe_status);
+        if (p->d_pipe_prof) cudaFree(p->d_pipe_prof);
         for (void* d : p->allocations) cudaFree(d);
         for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
         for (auto& kk : p->ev_rec)
@@ -758,13 +762,17 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     }
     double tmax_abs = 0;
     for (double v : ts) tmax_abs = std::max(tmax_abs, std::fabs(v));
-    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < 1e-12 ? 1 : 0;
+    // the modulation exp(-i 2 pi f_mid t) is dropped when its phase stays below a threshold over the
+    // whole span: 1e-9 cycles for FP32 plans (relative effect <= 6.3e-9, far below their tolerance; a
+    // grid like f_lo = -1/2, df = 1/I leaves f_mid = O(1e-16) from the rounding of df), 1e-12 for FP64
+    const double real_thresh = opts.precision == 32 ? 1e-9 : 1e-12;
+    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < real_thresh ? 1 : 0;
     // ---- exec path, fine-grid length and spreading kernel ----
     // generic path: nf = power of two >= 2 I (sigma in [2, 4)), w = ceil(log10(1/tol)) + 1, beta = 2.30 w.
     // packed FP32 path: nf = smallest 2^a or 3 * 2^a >= 1.5 I (sigma in [1.5, 2)), w = ceil(1.25 log10(1/tol)) + 1,
     // beta = 0.97 pi (1 - 1/(2 sigma)) w (exponential-of-semicircle kernel, Barnett et al. 2019).
-    if (opts.path < 0 || opts.path > 2) {
-        set_error("opts.path must be 0, 1 or 2");
+    if (opts.path < 0 || opts.path > 3) {
+        set_error("opts.path must be 0, 1, 2 or 3");
         return bail(M2_ERR_ARG);
     }
     const double span_t = ts.back() - ts.front();
@@ -782,13 +790,14 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         const int64_t rows_p = wrap_p ? nf_packed / 1024 : (int64_t)std::ceil((span + w_packed + 2.0) / 1024.0);
         packed_ok = nf_packed % 2048 == 0 && nf_packed <= (int64_t(3) << 20) && rows_p <= 64;
     }
-    if (opts.path == 2 && !packed_ok) {
+    if (opts.path >= 2 && !packed_ok) {
         set_error("the packed FP32 path needs precision 32, a real modulated taper (f_lo + (I/2) df = 0), "
                   "I <= 2^21 and a support of at most 64 rows of 1024 cells");
         return bail(M2_ERR_ARG);
     }
-    g.path = packed_ok ? 2 : 1;
-    if (g.path == 2) {
+    // packed plans run the persistent pipelined kernel (3) unless the four-kernel form (2) is asked for
+    g.path = packed_ok ? (opts.path == 2 ? 2 : 3) : 1;
+    if (g.path >= 2) {
         g.nf = nf_packed;
         g.width = w_packed;
         const double sigma = (double)g.nf / (double)g.I;
@@ -851,7 +860,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         const int64_t n1 = g.nf / n2;
         return g.wrap ? n1 : std::min<int64_t>(n1, (last_cell + n2 - 1) / n2);
     };
-    if (g.path == 2) {
+    if (g.path >= 2) {
         g.n2 = 1024;
         g.n1 = g.nf / 1024;
         g.log_n2 = 10;
@@ -863,11 +872,11 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         g.n2 = int64_t(1) << g.log_n2;
     }
     g.rows = rows_for(g.n2);
-    if (g.path == 2 && g.rows > 64) {
+    if (g.path >= 2 && g.rows > 64) {
         set_error("internal: packed path support exceeds 64 rows");
         return bail(M2_ERR_ARG);
     }
-    g.kp = g.path == 2 ? (K + 1) / 2 : K;
+    g.kp = g.path >= 2 ? (K + 1) / 2 : K;
     g.Lg = g.rows * g.n2;
     g.P = (int64_t)pts.size();
     g.ntiles = (g.Lg + kSpreadTile - 1) / kSpreadTile;
@@ -881,9 +890,9 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         // generic path: keep a chunk's workspace within L2.  Packed path: its kernels need
         // large grids more than L2 residency, so a chunk is up to 16 signals (workspace
         // 2 * K/2 * nf complex per signal)
-        const size_t z_per_signal = (size_t)g.kp * g.nf * csz * (g.path == 2 ? 2 : 1);
+        const size_t z_per_signal = (size_t)g.kp * g.nf * csz * (g.path >= 2 ? 2 : 1);
         int64_t chunk;
-        if (g.path == 2) {
+        if (g.path >= 2) {
             chunk = std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)((size_t(1) << 30) / z_per_signal)));
         } else {
             chunk = std::max<int64_t>(1, (int64_t)((48u << 20) / std::max<size_t>(z_per_signal, 1)));
@@ -949,7 +958,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                              unit_roots((g.nf + (int64_t(1) << g.twb_bits) - 1) >> g.twb_bits, g.nf,
                                         int64_t(1) << g.twb_bits)));
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twb, unit_roots(int64_t(1) << g.twb_bits, g.nf, 1)));
-    if (g.path == 2) {
+    if (g.path >= 2) {
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twn1, unit_roots(g.n1, g.n1, 1)));
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, unit_roots(1024, 1024, 1)));
         int64_t F = 1;
@@ -1077,7 +1086,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * g.kp * g.nf));
         p->d_g = dg;
         p->d_Z = dZ;
-        if (g.path == 2) {
+        if (g.path >= 2) {
             float2* dX = nullptr;
             M2_TRY_OR(pb.alloc(&dX, (size_t)g.chunk * g.kp * g.nf));
             p->d_X = dX;

@@ -49,7 +49,8 @@ def oracle_all(t, X, w, f_lo, df, I, idx=None):
 # ---------------------------------------------------------------------------
 # full-array parity at oracle-friendly sizes
 # ---------------------------------------------------------------------------
-PATHS = [(64, 1), (32, 1), (32, 2)]  # (precision, exec path): generic FP64 / generic FP32 / packed FP32
+PATHS = [(64, 1), (32, 1), (32, 2), (32, 3)]  # (precision, exec path): generic FP64 / generic FP32 /
+# packed FP32 as four kernels / packed FP32 as one persistent pipelined kernel
 
 
 @pytest.mark.parametrize("prec,path", PATHS)
@@ -139,7 +140,7 @@ def test_many_chunks_and_empty_batch(dev):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_batch_equals_alone_bitwise(dev, path):
     """Deterministic kernels: a signal gives bit-identical J and P-hat alone
     and inside a batch (no atomics, fixed summation order)."""
@@ -167,6 +168,13 @@ def test_packed_path_edge_cases(dev, K, I, N):
     p1 = pkg.Plan(t, 1.0, 2.0 / N, K, -0.5, 1.0 / I, I, precision=32, tapers=w, path=1)
     o2 = run_plan(p2, X, dev)
     o1 = run_plan(p1, X, dev)
+    # the persistent kernel runs the same stage code: bit-identical to the four kernels, with a
+    # two-slot ring (stages of a signal back to back) and with the default seven-slot ring
+    for mb in (2, 0):
+        p3 = pkg.Plan(t, 1.0, 2.0 / N, K, -0.5, 1.0 / I, I, precision=32, tapers=w, path=3, max_batch=mb)
+        o3 = run_plan(p3, X, dev)
+        for k in ("J", "E", "P"):
+            assert np.array_equal(o3[k], o2[k]), (mb, k)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
     assert rel_l2(o2["J"], Jr) <= TOL[32]
     assert rel_l2(o2["P"], Pr) <= TOL[32]
@@ -262,7 +270,7 @@ def test_leakage_rate_mismatch_matches_oracle(dev):
 # ---------------------------------------------------------------------------
 # full-size workloads (sampled outputs)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_jitter16k_full_size_fp32(dev, path):
     """N = 16384 jittered, K = 8, I = 2^18 (the benchmark workload): FP32
     path with FP64-split coordinates against the direct FP64 sum on sampled
@@ -300,7 +308,7 @@ def test_jitter16k_gep_on_gpu(dev):
     np.testing.assert_allclose(w @ RBw, 2 * wl.f_w * np.eye(wl.K), atol=1e-10)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_periodic16k_full_size_fp32(dev, path):
     """N = 16384 grid, blocks of 8 drop 2 (12288 kept), K = 10, I = 2^20."""
     wl = synth.workload("periodic16k")
@@ -406,3 +414,103 @@ def test_exec_batch_graph_replay_and_repeated_plans(dev):
     pkg.exec_batch([bp[k] for k in keep], [xs[k] for k in keep], [Js[k] for k in keep], None,
                    [Ps[k] for k in keep])
     torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------------
+# persistent pipelined kernel (path 3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [1, 3, 9, 20])
+def test_pipe_matches_four_kernels_full_size(dev, B):
+    """N = 16384 jittered, K = 8, I = 2^18: the persistent kernel over B signals
+    (one launch; B = 9 and 20 wrap the seven-slot workspace ring) equals the
+    four-kernel path bit for bit in J, |J|^2 and P-hat."""
+    wl = synth.workload("jitter16k", batch=B, seed=B)
+    w = seeded_tapers(wl.K, wl.N, 17)
+    p2 = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=2)
+    p3 = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=3)
+    assert p3.info["path"] == 3 and p2.info["path"] == 2
+    o2 = run_plan(p2, wl.x, dev)
+    o3 = run_plan(p3, wl.x, dev)
+    for k in ("J", "E", "P"):
+        assert np.array_equal(o3[k], o2[k]), k
+    # and twice in a row on the same plan (counters reset per launch)
+    o3b = run_plan(p3, wl.x, dev, want=("P",))
+    assert np.array_equal(o3b["P"], o2["P"])
+
+
+def test_pipe_default_path_is_pipelined(dev):
+    wl = synth.workload("jitter16k")
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                    tapers=seeded_tapers(wl.K, wl.N, 1))
+    assert plan.info["path"] == 3
+
+
+def test_pipe_bounded_wait_reports_timeout(dev):
+    """A work item whose dependency never completes: the wait gives up after the
+    limit, the kernel returns M2_ERR_TIMEOUT through its status word, and the
+    context stays usable (a following exec is correct)."""
+    import time
+    t0 = time.perf_counter()
+    st = pkg.binding.pipe_selftest(50)
+    dt = time.perf_counter() - t0
+    assert st == 6, pkg.binding.load().m2nufft_last_error().decode()
+    assert dt >= 0.05
+    t = synth.jittered(900, 0.4, 5)
+    X = np.stack([synth.white(t, 1.0, 80 + b) for b in range(2)])
+    w = seeded_tapers(4, 900, 2)
+    plan = pkg.Plan(t, 1.0, 2.0 / 900, 4, -0.5, 1.0 / 2048, 2048, precision=32, tapers=w, path=3)
+    out = run_plan(plan, X, dev)
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / 2048, 2048)
+    assert rel_l2(out["J"], Jr) <= TOL[32] and rel_l2(out["P"], Pr) <= TOL[32]
+
+
+def test_exec_batch_pipe_heterogeneous_matches_oracle(dev):
+    """All-packed uneven batch (one persistent launch): plans of different N, K
+    (odd K included), I and n1 (coset FFT lengths F = 2..32), more signals than
+    ring slots; equals the four-kernel per-signal exec bit for bit and the
+    oracle within the FP32 tolerance."""
+    ws = synth.batched_uneven(11, seed=12, n_min=300, n_max=8000)
+    Ks = [1, 3, 5, 8, 6, 4, 7, 2, 8, 5, 3]
+    plans2, plans3, xs, Js, Es, Ps, ws2 = [], [], [], [], [], [], []
+    for s, (wl, K) in enumerate(zip(ws, Ks)):
+        w = seeded_tapers(K, wl.N, 40 + s)
+        args = (wl.t, wl.fs, (K / 2 + 1) / wl.N, K, wl.f_lo, wl.df, wl.I)
+        plans2.append(pkg.Plan(*args, precision=32, tapers=w, path=2))
+        plans3.append(pkg.Plan(*args, precision=32, tapers=w, path=3))
+        xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
+        Js.append(torch.empty((K, wl.I), dtype=torch.complex64, device=dev))
+        Es.append(torch.empty((K, wl.I), dtype=torch.float32, device=dev))
+        Ps.append(torch.empty((wl.I,), dtype=torch.float32, device=dev))
+        ws2.append((wl, w))
+    assert len({p.info["n1"] for p in plans3}) >= 3
+    for rep in range(2):  # build + launch, then graph replay
+        for J in Js:
+            J.zero_()
+        pkg.exec_batch(plans3, xs, Js, Es, Ps)
+        torch.cuda.synchronize()
+        for p, x, J, E, P in zip(plans2, xs, Js, Es, Ps):
+            single = p.run(x[None, :], want=("J", "E", "P"))
+            torch.cuda.synchronize()
+            assert torch.equal(single["J"][0], J) and torch.equal(single["E"][0], E)
+            assert torch.equal(single["P"][0], P)
+    for (wl, w), J, P in list(zip(ws2, Js, Ps))[:4]:
+        Jr, _, Pr = oest.m2nufft(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I)
+        assert rel_l2(J.cpu().numpy(), Jr) <= TOL[32]
+        assert rel_l2(P.cpu().numpy(), Pr) <= TOL[32]
+
+
+def test_exec_batch_mixed_generic_and_pipelined(dev):
+    """A batch with a generic-path plan among pipelined plans is captured per
+    signal; the pipelined plans' launches are prepared outside the capture."""
+    ws = synth.batched_uneven(3, seed=21, n_min=300, n_max=1200)
+    paths = [3, 1, 3]
+    plans = [pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                      tapers=seeded_tapers(wl.K, wl.N, i), path=pth) for i, (wl, pth) in enumerate(zip(ws, paths))]
+    xs = [torch.from_numpy(wl.x[0].astype(np.float32)).to(dev) for wl in ws]
+    Ps = [torch.empty((wl.I,), dtype=torch.float32, device=dev) for wl in ws]
+    pkg.exec_batch(plans, xs, None, None, Ps)
+    torch.cuda.synchronize()
+    for p, x, P in zip(plans, xs, Ps):
+        single = p.run(x[None, :], want=("P",))
+        torch.cuda.synchronize()
+        assert torch.equal(single["P"][0], P)
