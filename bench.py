@@ -299,14 +299,29 @@ def run_uneven(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in evs) / args.steps
 
+    all_packed = all(p.info["path"] >= 2 for p in plans)
+
+    def coset_len(n1):
+        f = 1
+        while f < 32 and n1 % (2 * f) == 0:
+            f *= 2
+        return f
+    kp_classes = {0 if (p.info["K"] + 1) // 2 <= 2 else (1 if (p.info["K"] + 1) // 2 <= 4 else 2) for p in plans}
+    hb_launches = len(kp_classes) + len({coset_len(p.info["n1"]) for p in plans}) + 2
     t0 = time.perf_counter()
-    pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: capture + instantiate
+    pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: build + capture + instantiate
     torch.cuda.synchronize()
     t_capture = time.perf_counter() - t0
-    pkg.binding.batch_pipe_profile()  # reset the stage accounting
     ms_batch = timed(lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream))
-    stage_split = None
-    if all(p.info["path"] >= 2 for p in plans):
+    # the same batch as one persistent pipelined kernel (batch mode 1), for comparison
+    stage_split, ms_pipe = None, None
+    if all_packed:
+        prev = pkg.binding.set_batch_mode(1)
+        pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)
+        torch.cuda.synchronize()
+        pkg.binding.batch_pipe_profile()  # reset the stage accounting
+        ms_pipe = timed(lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream))
+        pkg.binding.set_batch_mode(prev)
         busy, waitms, nitems = pkg.binding.batch_pipe_profile()
         tot = max(float(busy.sum()), 1e-12)
         stage_split = {n: {"items": int(nitems[i]), "busy_ms_sum": float(busy[i]), "share": float(busy[i] / tot),
@@ -326,14 +341,15 @@ def run_uneven(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"uneven batch: {args.nsig} signals, grid length log-uniform in [1024, 16384], "
                                f"Markov gaps 15%, K in {{4,6,8}}, I = 4G; m2nufft_exec_batch (one CUDA graph: "
-                               f"one persistent-kernel launch over all signals)",
+                               f"one launch per stage over all signals)",
                    "signals": args.nsig, "units_per_step": units,
                    "l2": "flushed between timed steps (512 MiB write + read-back)"},
         "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                              "host_wall_s": wall_plain},
         "batch_over_plain": ms_plain / ms_batch,
-        "pipe_stages": stage_split,
-        "gpu_launches": 1 if all(p.info["path"] >= 2 for p in plans) else 4 * args.nsig,
+        "persistent_kernel": None if ms_pipe is None else {
+            "value": units / (ms_pipe * 1e-3), "ms_per_step": ms_pipe, "gpu_launches": 1, "stages": stage_split},
+        "gpu_launches": hb_launches if all_packed else 4 * args.nsig,
         "plain_gpu_launches_per_step": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
                                            for p in plans),
         "plan_seconds": t_plan, "capture_seconds": t_capture,

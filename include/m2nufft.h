@@ -88,7 +88,7 @@ typedef struct {
                            (including GEP scratch); 0 = unlimited */
     int device;         /* CUDA device ordinal; < 0 = the caller's current device */
     int max_batch;      /* signals processed per internal chunk; <= 0 = automatic */
-    int path;           /* exec kernels: 0 = automatic (3 where the plan qualifies, else 1),
+    int path;           /* exec kernels: 0 = automatic (2 where the plan qualifies, else 1),
                            1 = generic (any precision/grid),
                            2 = packed FP32 path as four kernels per chunk of signals,
                            3 = packed FP32 path as one persistent pipelined kernel per exec;
@@ -176,19 +176,27 @@ m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void
  *          real, [I_s] real); an entry or a whole array may be NULL
  *   stream as for m2nufft_exec
  * All plans must share one precision and one device.  The whole batch runs
- * as one CUDA graph launched on `stream`, cached per (plans, buffer pointers)
- * and replayed on later calls with the same arguments (the first call for a
- * new set of arguments builds and instantiates it).  When every plan is a
- * packed FP32 plan (path 2 or 3) the graph is a single launch of the
- * persistent pipelined kernel over all nsig signals, with its own workspace
- * ring (the plans' workspaces are not used); otherwise signals of different
- * plans run concurrently on internal streams inside the graph (signals of one
- * plan in order).  A plan in the batch must not be used by other work that
- * overlaps the batch on the device.  M2_ERR_TIMEOUT: an earlier replay of this
- * batch gave up a bounded wait (see m2nufft_exec).
+ * as one CUDA graph launched on `stream`, cached per (plans, buffer pointers,
+ * batch mode) and replayed on later calls with the same arguments (the first
+ * call for a new set of arguments builds and instantiates it).  When every
+ * plan is a packed FP32 plan (path 2 or 3) the graph holds, in batch mode 0
+ * (default), one launch per stage over all nsig signals (spread, column DFTs
+ * per coset length, row FFTs, epilogue) with a workspace for every signal, or,
+ * in batch mode 1, a single launch of the persistent pipelined kernel with a
+ * workspace ring; the plans' own workspaces are not used.  Otherwise signals
+ * of different plans run concurrently on internal streams inside the graph
+ * (signals of one plan in order).  Results are bit-identical to m2nufft_exec
+ * on each signal's plan.  A plan in the batch must not be used by other work
+ * that overlaps the batch on the device.  M2_ERR_TIMEOUT: an earlier replay
+ * of this batch gave up a bounded wait (batch mode 1; see m2nufft_exec).
  */
 m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
                              void* const* Js, void* const* Es, void* const* Ps, void* stream);
+
+/* Select how m2nufft_exec_batch runs all-packed batches (process-wide):
+ * 0 = one launch per stage (default), 1 = one persistent pipelined kernel.
+ * Returns the previous mode, or -1 for an invalid mode. */
+int m2nufft_set_batch_mode(int mode);
 
 /* Copy the plan's tapers (host [K][N] FP64, order of t) and eigenvalues
  * (host [K], descending; NaN when the plan was made from caller tapers

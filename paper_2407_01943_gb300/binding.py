@@ -58,6 +58,7 @@ EXPORTS = [
     ("m2nufft_exec", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
     ("m2nufft_get_tapers", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_leakage", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_info", ctypes.c_int, [_VP, ctypes.POINTER(m2_info)]),
@@ -297,6 +298,15 @@ def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: 
     st = load().m2nufft_leakage_static(_tptr(t), N, float(fs), float(f_w), K, ctypes.byref(fg), _tptr(w),
                                        _tptr(lam), _tptr(Lhat), _tptr(Ehat), _stream_handle(stream))
     _check(st, "m2nufft_leakage_static")
+
+
+def set_batch_mode(mode: int) -> int:
+    """0 = all-packed exec_batch as one launch per stage (default), 1 = one persistent
+    pipelined kernel; returns the previous mode."""
+    prev = int(load().m2nufft_set_batch_mode(int(mode)))
+    if prev < 0:
+        raise ValueError(load().m2nufft_last_error().decode())
+    return prev
 
 
 def batch_pipe_profile():

@@ -93,6 +93,14 @@ m2_status init_device_kernels(int device);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P,
                           cudaStream_t st);
+// Stage-batched executor of uneven batches of packed plans (hbatch.cu).
+struct HBatch;
+m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                        void* const* Es, void* const* Ps, HBatch** out);
+m2_status hbatch_run(HBatch* H, cudaStream_t st);
+int hbatch_launches(const HBatch* H);
+void hbatch_free(HBatch* H);
+m2_status init_hbatch_kernels(int smem_optin);
 // Persistent pipelined kernel of the packed path (pipe.cu).
 struct PipeLaunch;
 void pipe_free(PipeLaunch* L);

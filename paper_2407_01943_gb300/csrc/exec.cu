@@ -15,6 +15,7 @@
 //             |J|^2 over the K tapers of the signal inside the CTA to form
 //             P-hat without atomics.
 #include <algorithm>
+#include <atomic>
 #include <list>
 #include <mutex>
 #include <type_traits>
@@ -516,13 +517,18 @@ struct GraphEntry {
     int device;
     std::vector<uintptr_t> key;
     cudaGraphExec_t exec;
-    PipeLaunch* pipe;  // persistent-kernel batch (owned), or NULL for a captured per-signal batch
+    PipeLaunch* pipe;  // persistent-kernel batch (owned), or NULL
+    HBatch* hb;        // stage-batched batch (owned), or NULL
 };
 
 void drop_entry(GraphEntry& e) {
     cudaGraphExecDestroy(e.exec);
     if (e.pipe) pipe_free(e.pipe);
+    if (e.hb) hbatch_free(e.hb);
 }
+
+// How all-packed batches run: 0 = stage-batched launches, 1 = one persistent-kernel launch.
+std::atomic<int> g_batch_mode{0};
 
 std::mutex g_batch_mu;
 BatchResources g_batch_res[64];
@@ -597,10 +603,11 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
     return st;
 }
 
-// All-packed batch: one persistent-kernel launch (counter reset + kernel) captured as a graph.
-m2_status capture_pipe_batch(PipeLaunch* L, BatchResources& r, cudaGraphExec_t* out) {
+// All-packed batch: the persistent-kernel launch (counter reset + kernel), or the stage-batched
+// launches, captured as a graph.
+m2_status capture_packed_batch(PipeLaunch* L, HBatch* H, BatchResources& r, cudaGraphExec_t* out) {
     M2_CUDA_TRY(cudaStreamBeginCapture(r.origin, cudaStreamCaptureModeThreadLocal));
-    m2_status st = pipe_batch_run(L, r.origin);
+    m2_status st = L ? pipe_batch_run(L, r.origin) : hbatch_run(H, r.origin);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(r.origin, &graph);
     if (st == M2_OK && e != cudaSuccess) {
@@ -624,10 +631,10 @@ m2_status capture_pipe_batch(PipeLaunch* L, BatchResources& r, cudaGraphExec_t* 
 void purge_batch_graphs(const m2nufft_plan_s* p) {
     std::lock_guard<std::mutex> lock(g_batch_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end();) {
-        const auto& k = it->key;
+        const auto& k = it->key;  // [nsig, mode, plans..., buffers...]
         const int64_t n = (int64_t)k[0];
         bool hit = false;
-        for (int64_t s = 0; s < n && !hit; ++s) hit = k[1 + s] == (uintptr_t)p;
+        for (int64_t s = 0; s < n && !hit; ++s) hit = k[2 + s] == (uintptr_t)p;
         if (hit) {
             drop_entry(*it);
             it = g_graphs.erase(it);
@@ -662,7 +669,9 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::vector<uintptr_t> key;
     key.reserve(1 + 5 * nsig);
+    const int mode = m2::g_batch_mode.load();
     key.push_back((uintptr_t)nsig);
+    key.push_back((uintptr_t)mode);
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)plans[s]);
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)xs[s]);
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Js ? Js[s] : nullptr));
@@ -685,19 +694,22 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     M2_TRY(m2::batch_resources(dev, &res));
     cudaGraphExec_t exec = nullptr;
     m2::PipeLaunch* pipe = nullptr;
+    m2::HBatch* hb = nullptr;
     bool all_packed = plans[0]->precision == 32;
     for (int64_t s = 0; s < nsig && all_packed; ++s) all_packed = plans[s]->g.path >= 2;
     if (all_packed) {
-        M2_TRY(m2::pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
-        const m2_status cs = m2::capture_pipe_batch(pipe, *res, &exec);
+        if (mode == 1) M2_TRY(m2::pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
+        else M2_TRY(m2::hbatch_create(plans, xs, nsig, Js, Es, Ps, &hb));
+        const m2_status cs = m2::capture_packed_batch(pipe, hb, *res, &exec);
         if (cs != M2_OK) {
-            m2::pipe_free(pipe);
+            if (pipe) m2::pipe_free(pipe);
+            if (hb) m2::hbatch_free(hb);
             return cs;
         }
     } else {
         M2_TRY(m2::capture_batch(plans, xs, nsig, Js, Es, Ps, *res, &exec));
     }
-    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec, pipe});
+    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec, pipe, hb});
     while (m2::g_graphs.size() > m2::kMaxGraphs) {
         m2::drop_entry(m2::g_graphs.back());
         m2::g_graphs.pop_back();
@@ -746,4 +758,13 @@ extern "C" m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* l
         p->timing_launches[k] = 0;
     }
     return M2_OK;
+}
+
+extern "C" int m2nufft_set_batch_mode(int mode) {
+    m2::clear_error();
+    if (mode != 0 && mode != 1) {
+        m2::set_error("m2nufft_set_batch_mode: mode must be 0 or 1");
+        return -1;
+    }
+    return m2::g_batch_mode.exchange(mode);
 }

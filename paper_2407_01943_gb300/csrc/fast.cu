@@ -90,13 +90,24 @@ using packed::Tw32;
 using packed::kColWarps;
 using packed::kRowLen;
 
-// grid (ntiles, nb): one 256-cell tile of one signal per CTA
+// grid (ntiles, ceil(nb / SB)): one 256-cell tile of up to SB signals per CTA (SB = 4, or 2 for
+// five or more taper pairs, which keeps the accumulators in registers)
+__host__ __device__ constexpr int spread_signals(int KP) { return KP <= 4 ? 4 : 2; }
 template <int KP>
-__global__ void __launch_bounds__(kSpreadTile) spread_packed_kernel(Ctx c, const float* __restrict__ x,
+__global__ void __launch_bounds__(kSpreadTile) spread_packed_kernel(Ctx c, const float* __restrict__ x, int nb,
                                                                     float2* __restrict__ g) {
-    __shared__ __align__(16) unsigned char smem[packed::spread_smem_bytes(KP)];
-    const int b = blockIdx.y;
-    packed::spread_tile<KP>(c, x + (int64_t)b * c.N, blockIdx.x, g + (int64_t)b * c.Kp * c.Lg, smem);
+    constexpr int SB = spread_signals(KP);
+    __shared__ __align__(16) unsigned char smem[packed::spread_multi_smem_bytes(KP, SB)];
+    const int b0 = blockIdx.y * SB;
+    packed::spread_tile_multi<KP, SB>(c, x + (int64_t)b0 * c.N, min(SB, nb - b0), blockIdx.x,
+                                      g + (int64_t)b0 * c.Kp * c.Lg, smem);
+}
+
+template <int KP>
+void launch_spread_packed(const Ctx& c, const float* x, int nb, float2* g, cudaStream_t st) {
+    constexpr int SB = spread_signals(KP);
+    dim3 grid((unsigned)((c.Lg + kSpreadTile - 1) / kSpreadTile), (unsigned)((nb + SB - 1) / SB));
+    spread_packed_kernel<KP><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
 }
 
 // grid (1024 / 32, Kp, nb): 32 columns of one taper pair per CTA of 4 warps
@@ -172,10 +183,9 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
 
     mark(p, 0, 0, st);
     {
-        dim3 grid((unsigned)g.ntiles, (unsigned)nb);
-        if (g.kp <= 2) spread_packed_kernel<2><<<grid, kSpreadTile, 0, st>>>(c, x, dg);
-        else if (g.kp <= 4) spread_packed_kernel<4><<<grid, kSpreadTile, 0, st>>>(c, x, dg);
-        else spread_packed_kernel<8><<<grid, kSpreadTile, 0, st>>>(c, x, dg);
+        if (g.kp <= 2) launch_spread_packed<2>(c, x, nb, dg, st);
+        else if (g.kp <= 4) launch_spread_packed<4>(c, x, nb, dg, st);
+        else launch_spread_packed<8>(c, x, nb, dg, st);
         M2_CUDA_TRY(cudaGetLastError());
     }
     mark(p, 0, 1, st);

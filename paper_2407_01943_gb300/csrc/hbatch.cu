@@ -1,0 +1,291 @@
+// Stage-batched executor for uneven batches of packed FP32 plans.
+//
+// An uneven batch (signal s with its own plan p_s: own sampling times, N, K,
+// I and FFT geometry) runs as one kernel launch per stage over all signals of
+// the batch -- spread, column DFTs (one launch per coset FFT length F), row
+// FFTs, epilogue -- each stage at the occupancy its own register and shared-
+// memory needs allow, captured as one CUDA graph by m2nufft_exec_batch.  The
+// stage bodies are those of packed_stages.cuh, so every signal's J, |J|^2 and
+// P-hat are bit-identical to m2nufft_exec on its own plan.
+//
+// Every CTA reads one entry of a per-stage work map built on the host (task,
+// and the stage's index within that task), then that task's record and its
+// plan context; the intermediates of all signals live in one workspace
+// (signal s at offsets g_off / z_off), so stages of different signals never
+// wait on each other and the whole batch is four to eight launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "packed_stages.cuh"
+
+namespace m2 {
+namespace {
+
+using packed::Ctx;
+using packed::Tw32;
+using packed::kRowLen;
+
+constexpr int kEpiThreads = 128;
+constexpr int kColThreads = 128;  // 4 warps: one group of 4 warps, or 4 one-warp groups
+constexpr int kRowWarps = 8;
+constexpr int kSpreadTiles = 1;  // spread tiles per CTA
+
+struct __align__(16) HTask {
+    const float* x;
+    float2* J;
+    float* E;
+    float* P;
+    int64_t g_off;  // spread grids [Kp][Lg] at ws + g_off
+    int64_t z_off;  // Z [Kp][n1][1024] at ws + z_off, Xt [Kp][1024][n1] right after
+    int ctx;
+    int pad0, pad1, pad2;
+};
+static_assert(sizeof(HTask) == 64, "HTask layout");
+
+// CTA prologue: stage the task record and the plan context in shared memory
+__device__ __forceinline__ void load_task(const HTask* tasks, const Ctx* ctxs, int task, HTask* s_task, Ctx* s_ctx) {
+    const int t = threadIdx.x;
+    if (t < 4) reinterpret_cast<int4*>(s_task)[t] = reinterpret_cast<const int4*>(tasks + task)[t];
+    __syncthreads();
+    if (t < (int)(sizeof(Ctx) / 16))
+        reinterpret_cast<int4*>(s_ctx)[t] = reinterpret_cast<const int4*>(ctxs + s_task->ctx)[t];
+    __syncthreads();
+}
+
+// map entry: (task, first tile, tiles); up to kSpreadTiles tiles per CTA amortise the
+// dependent loads (tile bounds, point records, samples) over more cells
+template <int KP>
+__global__ void __launch_bounds__(kSpreadTile) hb_spread_kernel(const int4* __restrict__ map, const HTask* tasks,
+                                                                const Ctx* ctxs, float2* ws) {
+    __shared__ __align__(16) unsigned char smem[packed::spread_smem_bytes(KP)];
+    __shared__ __align__(16) Ctx s_ctx;
+    __shared__ __align__(16) HTask s_task;
+    const int4 m = map[blockIdx.x];
+    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
+    packed::spread_tiles<KP, kSpreadTiles>(s_ctx, s_task.x, m.y, m.z, ws + s_task.g_off, smem);
+}
+
+// map entry: (task, pair, first column, warps per 32-column group); the CTA's 4 warps form
+// 4 / gw groups on consecutive 32-column blocks
+template <int F>
+__global__ void __launch_bounds__(kColThreads) hb_cols_kernel(const int4* __restrict__ map, const HTask* tasks,
+                                                              const Ctx* ctxs, Tw32 tw, float2* ws) {
+    extern __shared__ float2 smem_f2[];
+    __shared__ __align__(16) Ctx s_ctx;
+    __shared__ __align__(16) HTask s_task;
+    const int4 m = map[blockIdx.x];
+    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
+    const Ctx& c = s_ctx;
+    const int gw = m.w;
+    const int warp = threadIdx.x >> 5;
+    const int grp = warp / gw, gwarp = warp - grp * gw;
+    float2* s_tw = smem_f2;
+    for (int q = threadIdx.x; q < c.n1; q += kColThreads) s_tw[q] = __ldg(c.tw_n1 + q);
+    float2* ws_g = ws + s_task.g_off + (int64_t)m.y * c.Lg;
+    float2* ws_z = ws + s_task.z_off + (int64_t)m.y * c.n1 * kRowLen;
+    packed::cols_group<F>(c, tw, ws_g, ws_z, m.z + grp * 32, gwarp, gw, s_tw,
+                          s_tw + c.n1 + (size_t)grp * packed::cols_group_f2(c.rows, F));
+}
+
+// map entry: (task, pair, first row, rows)
+__global__ void __launch_bounds__(32 * kRowWarps, 2) hb_rows_kernel(const int4* __restrict__ map,
+                                                                     const HTask* tasks, const Ctx* ctxs, Tw32 tw,
+                                                                     float2* ws) {
+    extern __shared__ float2 smem_f2[];
+    __shared__ __align__(16) Ctx s_ctx;
+    __shared__ __align__(16) HTask s_task;
+    const int4 m = map[blockIdx.x];
+    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
+    const Ctx& c = s_ctx;
+    const int64_t plane = (int64_t)c.n1 * kRowLen;
+    float2* Z = ws + s_task.z_off + (int64_t)m.y * plane;
+    float2* Xt = ws + s_task.z_off + (int64_t)c.Kp * plane + (int64_t)m.y * plane;
+    packed::rowfft_rows<kRowWarps, true>(c, tw, Z, Xt, m.z, m.w, smem_f2);
+}
+
+// map entry: (task, first flattened position k2 * n1 + k1)
+__global__ void __launch_bounds__(kEpiThreads) hb_epi_kernel(const int2* __restrict__ map, const HTask* tasks,
+                                                             const Ctx* ctxs, const float2* ws) {
+    __shared__ __align__(16) Ctx s_ctx;
+    __shared__ __align__(16) HTask s_task;
+    const int2 m = map[blockIdx.x];
+    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
+    const Ctx& c = s_ctx;
+    const int pos = m.y + threadIdx.x;
+    if (pos >= c.n1 * (c.k2max + 1)) return;
+    const int k2 = pos / c.n1;
+    const float2* Xt = ws + s_task.z_off + (int64_t)c.Kp * c.n1 * kRowLen;
+    packed::epi_position<true>(c, Xt, pos - k2 * c.n1, k2, s_task.J, s_task.E, s_task.P);
+}
+
+template <typename T>
+m2_status upload_vec(std::vector<void*>& owned, T** dst, const std::vector<T>& v) {
+    *dst = nullptr;
+    if (v.empty()) return M2_OK;
+    M2_CUDA_TRY(cudaMalloc(dst, v.size() * sizeof(T)));
+    owned.push_back(*dst);
+    M2_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return M2_OK;
+}
+
+}  // namespace
+
+// Resources of one uneven batch (owned by the cached batch graph).
+struct HBatch {
+    int device = 0;
+    std::vector<void*> owned;
+    Ctx* d_ctxs = nullptr;
+    HTask* d_tasks = nullptr;
+    float2* ws = nullptr;
+    Tw32 tw;
+    int4* d_spread[3] = {};  // KP = 2, 4, 8
+    int n_spread[3] = {};
+    int4* d_cols[6] = {};  // F = 1 (unused), 2, 4, 8, 16, 32 by log2
+    int n_cols[6] = {};
+    size_t smem_cols[6] = {};
+    int4* d_rows = nullptr;
+    int n_rows = 0;
+    int2* d_epi = nullptr;
+    int n_epi = 0;
+    size_t ws_bytes = 0;
+
+    ~HBatch() {
+        for (void* q : owned) cudaFree(q);
+    }
+};
+
+void hbatch_free(HBatch* h) { delete h; }
+
+m2_status init_hbatch_kernels(int smem_optin) {
+    const void* funcs[] = {(const void*)hb_cols_kernel<2>,  (const void*)hb_cols_kernel<4>,
+                           (const void*)hb_cols_kernel<8>,  (const void*)hb_cols_kernel<16>,
+                           (const void*)hb_cols_kernel<32>, (const void*)hb_rows_kernel};
+    for (const void* f : funcs) {
+        cudaFuncAttributes fa;
+        M2_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_optin - (int)fa.sharedSizeBytes));
+    }
+    return M2_OK;
+}
+
+m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                        void* const* Es, void* const* Ps, HBatch** out) {
+    std::unique_ptr<HBatch> H(new HBatch());
+    H->device = plans[0]->device;
+    H->tw = packed::make_tw32();
+    std::vector<Ctx> ctxs;
+    std::map<const m2nufft_plan_s*, int> index;
+    std::vector<HTask> tasks((size_t)nsig);
+    std::vector<int4> sp[3];
+    std::vector<int4> co[6];
+    std::vector<int4> ro;
+    std::vector<int2> ep;
+    int64_t off = 0;
+    for (int64_t s = 0; s < nsig; ++s) {
+        const m2nufft_plan_s* p = plans[s];
+        auto f = index.find(p);
+        if (f == index.end()) {
+            f = index.emplace(p, (int)ctxs.size()).first;
+            ctxs.push_back(packed_ctx(p));
+        }
+        const Ctx& c = ctxs[(size_t)f->second];
+        const Geometry& g = p->g;
+        const int task = (int)s;
+        HTask& t = tasks[(size_t)s];
+        t.x = static_cast<const float*>(xs[s]);
+        t.J = Js ? static_cast<float2*>(Js[s]) : nullptr;
+        t.E = Es ? static_cast<float*>(Es[s]) : nullptr;
+        t.P = Ps ? static_cast<float*>(Ps[s]) : nullptr;
+        t.ctx = f->second;
+        t.pad0 = t.pad1 = t.pad2 = 0;
+        // workspace: 256-byte aligned sections
+        auto take = [&](int64_t n) {
+            const int64_t o = off;
+            off += (n + 31) / 32 * 32;
+            return o;
+        };
+        t.g_off = take((int64_t)c.Kp * c.Lg);
+        t.z_off = take(2 * (int64_t)c.Kp * c.n1 * kRowLen);
+        // spread: one CTA per tile
+        const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
+        for (int64_t tile = 0; tile < g.ntiles; tile += kSpreadTiles)
+            sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(kSpreadTiles, g.ntiles - tile), 0));
+        // column DFTs: one coset per warp where the C = n1 / F cosets allow it (C = 1: four one-warp
+        // groups per CTA, C = 2: two two-warp groups), else one four-warp group sharing the cosets
+        const int C = c.n1 / c.F;
+        const int gw = C == 1 ? 1 : (C == 2 ? 2 : 4);
+        const int lf = packed::ilog2c(c.F);
+        for (int j = 0; j < c.Kp; ++j)
+            for (int col = 0; col < kRowLen; col += 32 * (4 / gw)) co[lf].push_back(make_int4(task, j, col, gw));
+        H->smem_cols[lf] = std::max(H->smem_cols[lf], sizeof(float2) * ((size_t)c.n1 + (size_t)(4 / gw) *
+                                                                          packed::cols_group_f2(c.rows, c.F)));
+        // row FFTs: up to 8 rows per CTA
+        for (int j = 0; j < c.Kp; ++j)
+            for (int r0 = 0; r0 < c.n1; r0 += kRowWarps) ro.push_back(make_int4(task, j, r0, std::min(kRowWarps, c.n1 - r0)));
+        // epilogue: 128 positions per CTA
+        const int npos = c.n1 * (c.k2max + 1);
+        for (int p0 = 0; p0 < npos; p0 += kEpiThreads) ep.push_back(make_int2(task, p0));
+    }
+    H->ws_bytes = (size_t)off * sizeof(float2);
+    M2_CUDA_TRY(cudaMalloc(&H->ws, H->ws_bytes));
+    H->owned.push_back(H->ws);
+    M2_TRY(upload_vec(H->owned, &H->d_ctxs, ctxs));
+    M2_TRY(upload_vec(H->owned, &H->d_tasks, tasks));
+    for (int k = 0; k < 3; ++k) {
+        M2_TRY(upload_vec(H->owned, &H->d_spread[k], sp[k]));
+        H->n_spread[k] = (int)sp[k].size();
+    }
+    for (int k = 0; k < 6; ++k) {
+        M2_TRY(upload_vec(H->owned, &H->d_cols[k], co[k]));
+        H->n_cols[k] = (int)co[k].size();
+    }
+    M2_TRY(upload_vec(H->owned, &H->d_rows, ro));
+    H->n_rows = (int)ro.size();
+    M2_TRY(upload_vec(H->owned, &H->d_epi, ep));
+    H->n_epi = (int)ep.size();
+    *out = H.release();
+    return M2_OK;
+}
+
+// The batch's launches, in stage order, on one stream (captured into a graph by the caller).
+m2_status hbatch_run(HBatch* H, cudaStream_t st) {
+    if (H->n_spread[0]) hb_spread_kernel<2><<<H->n_spread[0], kSpreadTile, 0, st>>>(H->d_spread[0], H->d_tasks, H->d_ctxs, H->ws);
+    if (H->n_spread[1]) hb_spread_kernel<4><<<H->n_spread[1], kSpreadTile, 0, st>>>(H->d_spread[1], H->d_tasks, H->d_ctxs, H->ws);
+    if (H->n_spread[2]) hb_spread_kernel<8><<<H->n_spread[2], kSpreadTile, 0, st>>>(H->d_spread[2], H->d_tasks, H->d_ctxs, H->ws);
+    M2_CUDA_TRY(cudaGetLastError());
+    for (int k = 1; k < 6; ++k) {
+        if (!H->n_cols[k]) continue;
+        const size_t sm = H->smem_cols[k];
+        switch (k) {
+            case 1: hb_cols_kernel<2><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
+            case 2: hb_cols_kernel<4><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
+            case 3: hb_cols_kernel<8><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
+            case 4: hb_cols_kernel<16><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
+            default: hb_cols_kernel<32><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
+        }
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    if (H->n_rows) {
+        hb_rows_kernel<<<H->n_rows, 32 * kRowWarps, packed::rowfft_smem_bytes(kRowWarps), st>>>(H->d_rows, H->d_tasks, H->d_ctxs, H->tw, H->ws);
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    if (H->n_epi) {
+        hb_epi_kernel<<<H->n_epi, kEpiThreads, 0, st>>>(H->d_epi, H->d_tasks, H->d_ctxs, H->ws);
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    return M2_OK;
+}
+
+int hbatch_launches(const HBatch* H) {
+    int n = (H->n_rows ? 1 : 0) + (H->n_epi ? 1 : 0);
+    for (int k = 0; k < 3; ++k) n += H->n_spread[k] ? 1 : 0;
+    for (int k = 0; k < 6; ++k) n += H->n_cols[k] ? 1 : 0;
+    return n;
+}
+
+}  // namespace m2

@@ -103,21 +103,26 @@ __device__ __forceinline__ float2 ld_inter(const float2* p) {
 }
 
 // ---------------------------------------------------------------------------
-// spread one 256-cell tile of one signal:
+// spread tiles [tile0, tile0 + nt) (256 cells each, nt <= NT) of one signal:
 //   g[j][c] = sum_n (u_{2j}[n] + i u_{2j+1}[n]) x[n] phi(c - u_n)
-// blockDim = kSpreadTile; smem >= 2 * 4 * kSpreadChunk + KP * kSpreadChunk * 8 bytes.
+// Thread = cell tile0 * 256 + 256 u + threadIdx.x for u < nt.  The points whose
+// windows meet the tiles are staged in chunks; every cell adds its points in
+// ascending point order, so the result does not depend on NT.
+// blockDim = kSpreadTile; smem >= spread_smem_bytes(KP).
 // ---------------------------------------------------------------------------
-template <int KP>
-__device__ __forceinline__ void spread_tile(const Ctx& c, const float* __restrict__ xb, int tile,
-                                            float2* __restrict__ gb, unsigned char* smem) {
+template <int KP, int NT>
+__device__ __forceinline__ void spread_tiles(const Ctx& c, const float* __restrict__ xb, int tile0, int nt,
+                                             float2* __restrict__ gb, unsigned char* smem) {
     int32_t* s_cell = reinterpret_cast<int32_t*>(smem);
     float* s_off = reinterpret_cast<float*>(smem + 4 * kSpreadChunk);
     float2* s_val = reinterpret_cast<float2*>(smem + 8 * kSpreadChunk);  // [KP][chunk]
-    const int64_t cell = (int64_t)tile * kSpreadTile + threadIdx.x;
-    const int pb = c.tile_pb[tile], pe = c.tile_pe[tile];
-    float2 acc[KP];
+    const int64_t cell0 = (int64_t)tile0 * kSpreadTile + threadIdx.x;
+    const int pb = c.tile_pb[tile0], pe = c.tile_pe[tile0 + nt - 1];
+    float2 acc[NT][KP];
 #pragma unroll
-    for (int j = 0; j < KP; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int u = 0; u < NT; ++u)
+#pragma unroll
+        for (int j = 0; j < KP; ++j) acc[u][j] = make_float2(0.f, 0.f);
     for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
         const int n = min(kSpreadChunk, pe - q0);
         __syncthreads();
@@ -135,6 +140,93 @@ __device__ __forceinline__ void spread_tile(const Ctx& c, const float* __restric
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            const int64_t cell = cell0 + (int64_t)u * kSpreadTile;
+            if (u < nt && cell < c.Lg) {
+                const int ci = (int)cell;
+                int lo = 0, hi = n;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
+                }
+                for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
+                    const float z = s_off[t] + (float)(ci - s_cell[t]);
+                    const float a = z * c.two_over_w;
+                    const float phi = expf(c.beta * (sqrtf(fmaxf(0.f, 1.f - a * a)) - 1.f));
+#pragma unroll
+                    for (int j = 0; j < KP; ++j) {
+                        const float2 v = s_val[j * kSpreadChunk + t];
+                        acc[u][j].x += v.x * phi;
+                        acc[u][j].y += v.y * phi;
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        const int64_t cell = cell0 + (int64_t)u * kSpreadTile;
+        if (u < nt && cell < c.Lg) {
+#pragma unroll
+            for (int j = 0; j < KP; ++j)
+                if (j < c.Kp) gb[(int64_t)j * c.Lg + cell] = acc[u][j];
+        }
+    }
+    __syncthreads();  // smem reuse by the next stage of this CTA
+}
+
+template <int KP>
+__device__ __forceinline__ void spread_tile(const Ctx& c, const float* __restrict__ xb, int tile,
+                                            float2* __restrict__ gb, unsigned char* smem) {
+    spread_tiles<KP, 1>(c, xb, tile, 1, gb, smem);
+}
+
+// ---------------------------------------------------------------------------
+// spread one tile for SB signals of one plan at once (signals b0 .. b0 + nsb - 1,
+// x and g strided by N and Kp * Lg): the point records, tapers and window
+// searches are shared by all signals of a plan, so they are staged once per
+// tile; per signal the arithmetic and its order are those of spread_tiles, so
+// each signal's grid is bit-identical to spreading it alone.
+// smem >= spread_multi_smem_bytes(KP, SB).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t spread_multi_smem_bytes(int KP, int SB) {
+    return (size_t)8 * kSpreadChunk + (size_t)KP * kSpreadChunk * 8 + (size_t)SB * kSpreadChunk * 4;
+}
+
+template <int KP, int SB>
+__device__ __forceinline__ void spread_tile_multi(const Ctx& c, const float* __restrict__ x, int nsb, int tile,
+                                                  float2* __restrict__ g, unsigned char* smem) {
+    int32_t* s_cell = reinterpret_cast<int32_t*>(smem);
+    float* s_off = reinterpret_cast<float*>(smem + 4 * kSpreadChunk);
+    float2* s_tap = reinterpret_cast<float2*>(smem + 8 * kSpreadChunk);                      // [KP][chunk]
+    float* s_x = reinterpret_cast<float*>(smem + 8 * kSpreadChunk + KP * kSpreadChunk * 8);  // [SB][chunk]
+    const int64_t cell = (int64_t)tile * kSpreadTile + threadIdx.x;
+    const int pb = c.tile_pb[tile], pe = c.tile_pe[tile];
+    float2 acc[SB][KP];
+#pragma unroll
+    for (int b = 0; b < SB; ++b)
+#pragma unroll
+        for (int j = 0; j < KP; ++j) acc[b][j] = make_float2(0.f, 0.f);
+    for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
+        const int n = min(kSpreadChunk, pe - q0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            const int p = q0 + t;
+            s_cell[t] = c.pt_cell[p];
+            s_off[t] = c.pt_off[p];
+            const int src = c.pt_src[p];
+#pragma unroll
+            for (int b = 0; b < SB; ++b) s_x[b * kSpreadChunk + t] = b < nsb ? x[(int64_t)b * c.N + src] : 0.f;
+#pragma unroll
+            for (int j = 0; j < KP; ++j) {
+                float2 v = make_float2(0.f, 0.f);
+                if (2 * j < c.K) v.x = c.taper[(int64_t)(2 * j) * c.P + p];
+                if (2 * j + 1 < c.K) v.y = c.taper[(int64_t)(2 * j + 1) * c.P + p];
+                s_tap[j * kSpreadChunk + t] = v;
+            }
+        }
+        __syncthreads();
         if (cell < c.Lg) {
             const int ci = (int)cell;
             int lo = 0, hi = n;
@@ -147,20 +239,28 @@ __device__ __forceinline__ void spread_tile(const Ctx& c, const float* __restric
                 const float a = z * c.two_over_w;
                 const float phi = expf(c.beta * (sqrtf(fmaxf(0.f, 1.f - a * a)) - 1.f));
 #pragma unroll
-                for (int j = 0; j < KP; ++j) {
-                    const float2 v = s_val[j * kSpreadChunk + t];
-                    acc[j].x += v.x * phi;
-                    acc[j].y += v.y * phi;
+                for (int b = 0; b < SB; ++b) {
+                    const float xv = s_x[b * kSpreadChunk + t];
+#pragma unroll
+                    for (int j = 0; j < KP; ++j) {
+                        const float2 tp = s_tap[j * kSpreadChunk + t];
+                        const float vx = tp.x * xv, vy = tp.y * xv;  // the tapered sample, rounded as when spread alone
+                        acc[b][j].x += vx * phi;
+                        acc[b][j].y += vy * phi;
+                    }
                 }
             }
         }
     }
     if (cell < c.Lg) {
 #pragma unroll
-        for (int j = 0; j < KP; ++j)
-            if (j < c.Kp) gb[(int64_t)j * c.Lg + cell] = acc[j];
+        for (int b = 0; b < SB; ++b)
+            if (b < nsb) {
+#pragma unroll
+                for (int j = 0; j < KP; ++j)
+                    if (j < c.Kp) g[((int64_t)b * c.Kp + j) * c.Lg + cell] = acc[b][j];
+            }
     }
-    __syncthreads();  // smem reuse by the next stage of this CTA
 }
 
 __host__ __device__ constexpr size_t spread_smem_bytes(int KP) { return (size_t)8 * kSpreadChunk + (size_t)KP * kSpreadChunk * 8; }

@@ -57,6 +57,7 @@ m2_status init_device_kernels(int device) {
     M2_TRY(init_exec_kernels(optin));
     M2_TRY(init_fast_kernels(optin));
     M2_TRY(init_pipe_kernels(optin));
+    M2_TRY(init_hbatch_kernels(optin));
     g_init_done[device] = true;
     return M2_OK;
 }
@@ -795,8 +796,8 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                   "I <= 2^21 and a support of at most 64 rows of 1024 cells");
         return bail(M2_ERR_ARG);
     }
-    // packed plans run the persistent pipelined kernel (3) unless the four-kernel form (2) is asked for
-    g.path = packed_ok ? (opts.path == 2 ? 2 : 3) : 1;
+    // packed plans run the four-kernel form (2) unless the persistent pipelined kernel (3) is asked for
+    g.path = packed_ok ? (opts.path == 3 ? 3 : 2) : 1;
     if (g.path >= 2) {
         g.nf = nf_packed;
         g.width = w_packed;

@@ -332,7 +332,7 @@ def test_jitter16k_fp64_path(dev):
     assert rel_l2(out["P"][:, idx], Pr) <= TOL[64]
 
 
-def test_exec_batch_uneven_matches_single(dev):
+def test_exec_batch_uneven_matches_single(dev, batch_mode):
     """m2nufft_exec_batch over signals with different plans equals
     per-signal exec bit for bit."""
     ws = synth.batched_uneven(4, seed=3, n_min=256, n_max=1500)
@@ -438,11 +438,15 @@ def test_pipe_matches_four_kernels_full_size(dev, B):
     assert np.array_equal(o3b["P"], o2["P"])
 
 
-def test_pipe_default_path_is_pipelined(dev):
+def test_default_path_selection(dev):
+    """Automatic choice: packed four-kernel path for qualifying FP32 plans, the persistent
+    kernel on request, the generic path for FP64."""
     wl = synth.workload("jitter16k")
-    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
-                    tapers=seeded_tapers(wl.K, wl.N, 1))
-    assert plan.info["path"] == 3
+    w = seeded_tapers(wl.K, wl.N, 1)
+    args = (wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I)
+    assert pkg.Plan(*args, precision=32, tapers=w).info["path"] == 2
+    assert pkg.Plan(*args, precision=32, tapers=w, path=3).info["path"] == 3
+    assert pkg.Plan(*args, precision=64, tapers=w).info["path"] == 1
 
 
 def test_pipe_bounded_wait_reports_timeout(dev):
@@ -464,11 +468,18 @@ def test_pipe_bounded_wait_reports_timeout(dev):
     assert rel_l2(out["J"], Jr) <= TOL[32] and rel_l2(out["P"], Pr) <= TOL[32]
 
 
-def test_exec_batch_pipe_heterogeneous_matches_oracle(dev):
-    """All-packed uneven batch (one persistent launch): plans of different N, K
-    (odd K included), I and n1 (coset FFT lengths F = 2..32), more signals than
-    ring slots; equals the four-kernel per-signal exec bit for bit and the
-    oracle within the FP32 tolerance."""
+@pytest.fixture(params=[0, 1], ids=["stage_batched", "persistent"])
+def batch_mode(request):
+    prev = pkg.binding.set_batch_mode(request.param)
+    yield request.param
+    pkg.binding.set_batch_mode(prev)
+
+
+def test_exec_batch_pipe_heterogeneous_matches_oracle(dev, batch_mode):
+    """All-packed uneven batch (one launch per stage, or one persistent launch):
+    plans of different N, K (odd K included), I and n1 (coset FFT lengths
+    F = 2..32), more signals than ring slots; equals the four-kernel
+    per-signal exec bit for bit and the oracle within the FP32 tolerance."""
     ws = synth.batched_uneven(11, seed=12, n_min=300, n_max=8000)
     Ks = [1, 3, 5, 8, 6, 4, 7, 2, 8, 5, 3]
     plans2, plans3, xs, Js, Es, Ps, ws2 = [], [], [], [], [], [], []
