@@ -59,7 +59,7 @@ def parse_args():
                     help="exec path: 0 automatic, 1 generic, 2 packed four-kernel, 3 packed persistent kernel")
     ap.add_argument("--outputs", default="JEPL",
                     help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat), "
-                         "L (leakage estimates L-hat, E-hat)")
+                         "L (leakage estimates L-hat, E-hat), F (Thomson F-statistic)")
     ap.add_argument("--skip-gep", action="store_true",
                     help="plan from taper-shaped inputs instead of the FP64 GEP (profiling runs; "
                          "the exec kernels and their shapes are identical)")
@@ -181,6 +181,7 @@ def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: s
         return nb * per + I * csz
     if kernel == "epi":
         per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
+        per += I * rsz if "F" in outputs else 0
         return nb * per + I * csz
     if kernel == "pipe":
         # the whole path in one launch over nb signals: read x, write J, |J|^2, P-hat; the plan's
@@ -455,6 +456,16 @@ def run_ours(args):
     # leakage estimates (plan constants, App. B) are handed out with every exec
     Lh = torch.empty((wl.K, wl.I), dtype=torch.float64, device=dev) if "L" in args.outputs else None
     Eh = torch.empty((wl.I,), dtype=torch.float64, device=dev) if "L" in args.outputs else None
+    # Thomson F-statistic per band (Sec. 3, Eq. f_stat), optional output
+    Fb = torch.empty((B, wl.I), dtype=rdt, device=dev) if "F" in args.outputs else None
+
+    def step(xin):
+        if Fb is None:
+            plan.exec(xin, J, E, P, Lh, Eh, stream=stream)
+        else:
+            plan.exec(xin, J, E, P, stream=stream, F=Fb)
+            if Lh is not None:
+                plan.exec(xin[:0], None, None, None, Lh, Eh, stream=stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def flush_l2():
@@ -470,7 +481,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         flush_l2()
-        plan.exec(x, J, E, P, Lh, Eh, stream=stream)
+        step(x)
     torch.cuda.synchronize()
 
     # ---- timed region: K device-timed steps, L2 flushed between them ----
@@ -486,7 +497,7 @@ def run_ours(args):
     for s in range(args.steps):
         flush_l2()
         evs[s][0].record(stream)
-        plan.exec(x, J, E, P, Lh, Eh, stream=stream)
+        step(x)
         evs[s][1].record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -543,7 +554,7 @@ def run_ours(args):
         xd = torch.empty_like(x)
         for _ in range(2):
             xd.copy_(xh, non_blocking=True)
-            plan.exec(xd, J, E, P, Lh, Eh, stream=stream)
+            step(xd)
             ph.copy_(P, non_blocking=True)
         torch.cuda.synchronize()
         ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -553,7 +564,7 @@ def run_ours(args):
             flush_l2()
             ev_e[s][0].record(stream)
             xd.copy_(xh, non_blocking=True)
-            plan.exec(xd, J, E, P, Lh, Eh, stream=stream)
+            step(xd)
             ph.copy_(P, non_blocking=True)
             ev_e[s][1].record(stream)
         torch.cuda.synchronize()

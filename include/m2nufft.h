@@ -169,6 +169,24 @@ m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, void* J, void
                        double* Lhat, double* Ehat, void* stream);
 
 /*
+ * As m2nufft_exec, plus Thomson's F-statistic for a spectral line at every
+ * band centre (Sec. 3, Eq. f_stat and the amplitude estimate after it):
+ *   C_i = sum_k J_k(A_i) W_k / sum_k W_k^2,   W_k = W_k^0(0) = sum_n w_k(t_n),
+ *   F_i = |C_i|^2 (K - 1) sum_k W_k^2 / sum_k |J_k(A_i) - C_i W_k|^2,
+ * distributed F(2, 2K - 2) under the no-line hypothesis (bands with
+ * 2 f_i > f_w).  W_k is formed in FP64 at plan time.
+ *   F      device [B][I] real (plan precision), required
+ *   J,E,P  as for m2nufft_exec, each may be NULL
+ * The packed path (2 or 3) forms F in its epilogue from the eigencoefficients
+ * it already holds (a path-3 plan runs its four-kernel form for this call);
+ * the generic path runs one more kernel over J (an internal J buffer of one
+ * chunk is allocated on first use when J is NULL).
+ * Errors: as m2nufft_exec; M2_ERR_ARG for K < 2 or F == NULL.
+ */
+m2_status m2nufft_exec_ftest(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P, void* F,
+                             void* stream);
+
+/*
  * Uneven batch: nsig signals, each with its own plan (plans may repeat).
  *   plans  host [nsig] plan handles
  *   xs     host [nsig] device pointers, xs[s] -> [N_s] real

@@ -56,6 +56,7 @@ EXPORTS = [
      [_DP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(m2_fgrid), _DP, _DP,
       ctypes.POINTER(m2_opts), ctypes.POINTER(_VP)]),
     ("m2nufft_exec", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("m2nufft_exec_ftest", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP]),
     ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
@@ -203,8 +204,9 @@ class Plan:
         return Lh, Eh
 
     # -- execution ------------------------------------------------------
-    def exec(self, x, J=None, E=None, P=None, Lhat=None, Ehat=None, stream=None):
-        """Enqueue the path for x [B, N] (torch CUDA tensor of the plan's real dtype)."""
+    def exec(self, x, J=None, E=None, P=None, Lhat=None, Ehat=None, stream=None, F=None):
+        """Enqueue the path for x [B, N] (torch CUDA tensor of the plan's real dtype); with F
+        [B, I], also the F-statistic (m2nufft_exec_ftest; L-hat/E-hat then not copied)."""
         if x.dim() != 2 or x.shape[1] != self.N:
             raise ValueError(f"x must have shape [B, {self.N}]")
         if x.dtype != self.real_dtype:
@@ -212,9 +214,17 @@ class Plan:
         B = int(x.shape[0])
         for name, a, shape, dt in (("J", J, (B, self.K, self.I), self.complex_dtype),
                                    ("E", E, (B, self.K, self.I), self.real_dtype),
-                                   ("P", P, (B, self.I), self.real_dtype)):
+                                   ("P", P, (B, self.I), self.real_dtype),
+                                   ("F", F, (B, self.I), self.real_dtype)):
             if a is not None and (tuple(a.shape) != shape or a.dtype != dt):
                 raise ValueError(f"{name} must be {dt} with shape {shape}")
+        if F is not None:
+            if Lhat is not None or Ehat is not None:
+                raise ValueError("exec with F does not copy L-hat/E-hat; call leakage() or a second exec")
+            st = load().m2nufft_exec_ftest(self._h, _tptr(x), B, _tptr(J), _tptr(E), _tptr(P), _tptr(F),
+                                           _stream_handle(stream))
+            _check(st, "m2nufft_exec_ftest")
+            return
         st = load().m2nufft_exec(self._h, _tptr(x), B, _tptr(J), _tptr(E), _tptr(P), _tptr(Lhat),
                                  _tptr(Ehat), _stream_handle(stream))
         _check(st, "m2nufft_exec")
@@ -235,6 +245,12 @@ class Plan:
             out["Lhat"] = torch.empty((self.K, self.I), dtype=torch.float64, device=dev)
         if "Ehat" in want:
             out["Ehat"] = torch.empty((self.I,), dtype=torch.float64, device=dev)
+        if "F" in want:
+            out["F"] = torch.empty((B, self.I), dtype=self.real_dtype, device=dev)
+            self.exec(x, out.get("J"), out.get("E"), out.get("P"), stream=stream, F=out["F"])
+            if "Lhat" in out or "Ehat" in out:
+                self.exec(x[:0], None, None, None, out.get("Lhat"), out.get("Ehat"), stream)
+            return out
         self.exec(x, out.get("J"), out.get("E"), out.get("P"), out.get("Lhat"), out.get("Ehat"), stream)
         return out
 

@@ -91,7 +91,7 @@ m2_status init_fast_kernels(int smem_optin);
 m2_status init_pipe_kernels(int smem_optin);
 m2_status init_device_kernels(int device);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
-m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P,
+m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
                           cudaStream_t st);
 // Stage-batched executor of uneven batches of packed plans (hbatch.cu).
 struct HBatch;
@@ -151,6 +151,9 @@ struct m2nufft_plan_s {
     void* d_tw1024 = nullptr;      // packed path: [1024] C, exp(-i 2 pi q / 1024) full circle
     void* d_colT = nullptr;        // packed path: [F][1024] C, exp(-i 2 pi l2 C q / nf) (column-FFT output twiddle)
     void* d_colB = nullptr;        // packed path: [C][1024] C, exp(-i 2 pi l2 r / nf) (per-coset factor)
+    void* d_wsum = nullptr;        // [K] R: W_k^0(0) = sum_n w_k(t_n) (F-statistic)
+    double wq = 0.0;               // sum_k W_k^0(0)^2
+    void* d_Jscratch = nullptr;    // generic path: J of one chunk when F is wanted without J
     double* d_Lhat = nullptr;      // [K][I]
     double* d_Ehat = nullptr;      // [I]
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C

@@ -375,8 +375,34 @@ m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J
     return M2_OK;
 }
 
+// Thomson's F-statistic (Sec. 3, Eq. f_stat) from the eigencoefficients of nb signals, generic
+// path: thread = band i of signal b;  C = sum_k J_k W_k / sum_k W_k^2,
+// F = |C|^2 (K - 1) sum_k W_k^2 / sum_k |J_k - C W_k|^2.
 template <typename R>
-m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, void* Ev, void* Pv,
+__global__ void __launch_bounds__(128) ftest_kernel(const typename CT<R>::C* __restrict__ J, int K, int64_t I,
+                                                    const R* __restrict__ wsum, R wq, R* __restrict__ F) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= I) return;
+    const auto* Jb = J + (int64_t)b * K * I + i;
+    R sx = 0, sy = 0;
+    for (int k = 0; k < K; ++k) {
+        const auto v = Jb[(int64_t)k * I];
+        sx += v.x * wsum[k];
+        sy += v.y * wsum[k];
+    }
+    const R cx = sx / wq, cy = sy / wq;
+    R res = 0;
+    for (int k = 0; k < K; ++k) {
+        const auto v = Jb[(int64_t)k * I];
+        const R rx = v.x - cx * wsum[k], ry = v.y - cy * wsum[k];
+        res += rx * rx + ry * ry;
+    }
+    F[(int64_t)b * I + i] = (cx * cx + cy * cy) * (R)(K - 1) * wq / res;
+}
+
+template <typename R>
+m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, void* Ev, void* Pv, void* Fv,
                      cudaStream_t st) {
     using C = typename CT<R>::C;
     const Geometry& g = p->g;
@@ -384,21 +410,36 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     C* J = reinterpret_cast<C*>(Jv);
     R* E = reinterpret_cast<R*>(Ev);
     R* P = reinterpret_cast<R*>(Pv);
+    R* F = reinterpret_cast<R*>(Fv);
     if constexpr (std::is_same<R, float>::value) {
-        if (g.path == 3) return exec_pipe(p, x, B, J, E, P, st);  // all B signals in one launch
+        // all B signals in one launch; the F-statistic runs the four-kernel form (same stages)
+        if (g.path == 3 && !F) return exec_pipe(p, x, B, J, E, P, st);
+    }
+    if (F && g.path == 1 && !J && !p->d_Jscratch) {
+        // the generic path forms F from J: a chunk-sized J buffer when the caller wants none
+        M2_CUDA_TRY(cudaMalloc(&p->d_Jscratch, sizeof(C) * (size_t)g.chunk * g.K * g.I));
+        p->allocations.push_back(p->d_Jscratch);
+        p->device_bytes += sizeof(C) * (size_t)g.chunk * g.K * g.I;
     }
     for (int64_t b0 = 0; b0 < B; b0 += g.chunk) {
         const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
         C* Jc = J ? J + b0 * g.K * g.I : nullptr;
         R* Ec = E ? E + b0 * g.K * g.I : nullptr;
         R* Pc = P ? P + b0 * g.I : nullptr;
+        R* Fc = F ? F + b0 * g.I : nullptr;
         if constexpr (std::is_same<R, float>::value) {
-            if (g.path == 2) {
-                M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, Jc, Ec, Pc, st));
+            if (g.path >= 2) {
+                M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, Jc, Ec, Pc, Fc, st));
                 continue;
             }
         }
+        if (Fc && !Jc) Jc = reinterpret_cast<C*>(p->d_Jscratch);
         M2_TRY(exec_chunk<R>(p, x + b0 * g.N, nb, Jc, Ec, Pc, st));
+        if (Fc) {
+            dim3 grid((unsigned)((g.I + 127) / 128), (unsigned)nb);
+            ftest_kernel<R><<<grid, 128, 0, st>>>(Jc, g.K, g.I, reinterpret_cast<const R*>(p->d_wsum), (R)p->wq, Fc);
+            M2_CUDA_TRY(cudaGetLastError());
+        }
     }
     return M2_OK;
 }
@@ -416,7 +457,7 @@ struct DeviceGuard {
     }
 };
 
-m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E, void* P,
+m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E, void* P, void* F,
                    double* Lhat, double* Ehat, cudaStream_t st) {
     if (B < 0) {
         set_error("m2nufft_exec: B must be >= 0");
@@ -431,9 +472,13 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
         set_error("m2nufft_exec: x is NULL");
         return M2_ERR_ARG;
     }
+    if (F && p->g.K < 2) {
+        set_error("m2nufft_exec_ftest: the F-statistic needs K >= 2 tapers (F(2, 2K - 2))");
+        return M2_ERR_ARG;
+    }
     if (B > 0) {
-        if (p->precision == 32) M2_TRY(exec_typed<float>(p, x, B, J, E, P, st));
-        else M2_TRY(exec_typed<double>(p, x, B, J, E, P, st));
+        if (p->precision == 32) M2_TRY(exec_typed<float>(p, x, B, J, E, P, F, st));
+        else M2_TRY(exec_typed<double>(p, x, B, J, E, P, F, st));
     }
     const Geometry& g = p->g;
     if (Lhat)
@@ -492,7 +537,18 @@ extern "C" m2_status m2nufft_exec(m2nufft_plan_t p, const void* x, int64_t B, vo
         return M2_ERR_ARG;
     }
     m2::DeviceGuard guard(p->device);
-    return m2::exec_one(p, x, B, J, E, P, Lhat, Ehat, reinterpret_cast<cudaStream_t>(stream));
+    return m2::exec_one(p, x, B, J, E, P, nullptr, Lhat, Ehat, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" m2_status m2nufft_exec_ftest(m2nufft_plan_t p, const void* x, int64_t B, void* J, void* E, void* P,
+                                        void* F, void* stream) {
+    m2::clear_error();
+    if (!p || !F) {
+        m2::set_error("m2nufft_exec_ftest: plan or F is NULL");
+        return M2_ERR_ARG;
+    }
+    m2::DeviceGuard guard(p->device);
+    return m2::exec_one(p, x, B, J, E, P, F, nullptr, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
 namespace m2 {
@@ -575,7 +631,7 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
         const int saved = p->timing;
         p->timing = 0;
         st = exec_one(p, xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr, Ps ? Ps[s] : nullptr, nullptr,
-                      nullptr, r.ws[lane[p]]);
+                      nullptr, nullptr, r.ws[lane[p]]);
         p->timing = saved;
     }
     for (int w = 0; w < kBatchStreams && st == M2_OK; ++w) {

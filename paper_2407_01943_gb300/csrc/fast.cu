@@ -80,6 +80,8 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     c.colB = reinterpret_cast<const float2*>(p->d_colB);
     c.tw1024 = reinterpret_cast<const float2*>(p->d_tw1024);
     c.deconv = reinterpret_cast<const float2*>(p->d_deconv);
+    c.wsum = reinterpret_cast<const float*>(p->d_wsum);
+    c.wq = (float)p->wq;
     return c;
 }
 
@@ -132,15 +134,18 @@ rowfft_kernel(Ctx c, Tw32 tw, const float2* __restrict__ Z, float2* __restrict__
     packed::rowfft_rows<R, true>(c, tw, Z + base, Xt + base, blockIdx.x * R, R, smem_f2);
 }
 
-// grid (ceil(n1 / 128), k2max + 1, nb): thread = position (k1, k2) and its mirror
+// grid (ceil(n1 / 128), k2max + 1, nb): thread = position (k1, k2) and its mirror; kF adds the
+// F-statistic output
+template <bool kF>
 __global__ void __launch_bounds__(128) epi_kernel(Ctx c, const float2* __restrict__ Xt, float2* __restrict__ J,
-                                                  float* __restrict__ E, float* __restrict__ P) {
+                                                  float* __restrict__ E, float* __restrict__ P, float* __restrict__ F) {
     const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.z;
     if (k1 >= c.n1) return;
     const int64_t KI = (int64_t)c.K * c.I;
-    packed::epi_position<true>(c, Xt + (int64_t)b * c.Kp * c.n1 * kRowLen, k1, blockIdx.y, J ? J + b * KI : nullptr,
-                               E ? E + b * KI : nullptr, P ? P + (int64_t)b * c.I : nullptr);
+    packed::epi_position<true, kF>(c, Xt + (int64_t)b * c.Kp * c.n1 * kRowLen, k1, blockIdx.y,
+                                   J ? J + b * KI : nullptr, E ? E + b * KI : nullptr,
+                                   P ? P + (int64_t)b * c.I : nullptr, F ? F + (int64_t)b * c.I : nullptr);
 }
 
 template <int F>
@@ -173,7 +178,8 @@ m2_status init_fast_kernels(int smem_optin) {
     return M2_OK;
 }
 
-m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, cudaStream_t st) {
+m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
+                          cudaStream_t st) {
     const Geometry& g = p->g;
     static const Tw32 tw = packed::make_tw32();
     const Ctx c = packed_ctx(p);
@@ -213,7 +219,8 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     mark(p, 3, 0, st);
     {
         dim3 grid((unsigned)((g.n1 + 127) / 128), (unsigned)(c.k2max + 1), (unsigned)nb);
-        epi_kernel<<<grid, 128, 0, st>>>(c, dX, J, E, P);
+        if (F) epi_kernel<true><<<grid, 128, 0, st>>>(c, dX, J, E, P, F);
+        else epi_kernel<false><<<grid, 128, 0, st>>>(c, dX, J, E, P, nullptr);
         M2_CUDA_TRY(cudaGetLastError());
     }
     mark(p, 3, 1, st);

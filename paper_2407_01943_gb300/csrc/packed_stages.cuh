@@ -91,6 +91,8 @@ struct __align__(16) Ctx {
     const float2* colB;    // [C][1024]
     const float2* tw1024;  // [1024]
     const float2* deconv;  // [I]
+    const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
+    float wq;              // sum_k W_k^0(0)^2
 };
 
 // Load of an intermediate written earlier: kStream = streaming (evict-first) for the
@@ -393,10 +395,13 @@ inline size_t rowfft_smem_bytes(int R) { return sizeof(float2) * ((size_t)kRowLe
 // deconvolve, write J and |J|^2 at m and -m, and the taper average P-hat.
 // Xtb: [Kp][1024][n1]; J, E: [K][I]; P: [I] (this signal; NULL = not wanted).
 // ---------------------------------------------------------------------------
-template <bool kStream>
+// With kF, also Thomson's F-statistic (Sec. 3, Eq. f_stat) at m and -m (equal, since
+// J_k(-m) = conj J_k(m) and W_k^0(0) is real):
+//   C = sum_k J_k W_k / sum_k W_k^2,  F = |C|^2 (K - 1) sum_k W_k^2 / sum_k |J_k - C W_k|^2.
+template <bool kStream, bool kF = false>
 __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restrict__ Xtb, int k1, int k2,
                                              float2* __restrict__ J, float* __restrict__ E,
-                                             float* __restrict__ Pout) {
+                                             float* __restrict__ Pout, float* __restrict__ Fout = nullptr) {
     const int n1 = c.n1, nf = c.nf, I = c.I, K = c.K;
     const int half = nf >> 1;
     int pk1, pk2;
@@ -426,7 +431,10 @@ __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restr
     const float2* X2 = Xtb + (int64_t)pk2 * n1 + pk1;
     const int Kp = c.Kp;
     float pacc = 0.f;
-    for (int j = 0; j < Kp; ++j) {
+    constexpr int kMaxPairs = kF ? (kMaxK + 1) / 2 : 1;
+    float2 jk[kMaxPairs][2];  // kF: J of every taper at m, for the residual of the line fit
+    float2 csum = make_float2(0.f, 0.f);
+    auto pair = [&](int j) {
         const float2 A = ld_inter<kStream>(X1 + (int64_t)j * plane);
         const float2 Bc = ld_inter<kStream>(X2 + (int64_t)j * plane);
         // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
@@ -442,8 +450,20 @@ __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restr
             if (v2) __stcs(E + o0 + i2, p0);
         }
         pacc += p0;
+        if (kF) {
+            const float w0 = c.wsum[2 * j];
+            jk[kF ? j : 0][0] = j0;
+            csum.x += j0.x * w0;
+            csum.y += j0.y * w0;
+        }
         if (2 * j + 1 < K) {
             const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd);
+            if (kF) {
+                const float w1 = c.wsum[2 * j + 1];
+                jk[kF ? j : 0][1] = j1;
+                csum.x += j1.x * w1;
+                csum.y += j1.y * w1;
+            }
             const float p1 = j1.x * j1.x + j1.y * j1.y;
             const int64_t o1 = o0 + I;
             if (J) {
@@ -456,11 +476,37 @@ __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restr
             }
             pacc += p1;
         }
+    };
+    if constexpr (kF) {
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j)
+            if (j < Kp) pair(j);  // fully unrolled: jk stays in registers
+    } else {
+        for (int j = 0; j < Kp; ++j) pair(j);
     }
     if (Pout) {
         const float pv = pacc * (1.0f / (float)K);
         if (v1) __stcs(Pout + i1, pv);
         if (v2) __stcs(Pout + i2, pv);
+    }
+    if (kF && Fout) {
+        const float2 ch = make_float2(csum.x / c.wq, csum.y / c.wq);  // line amplitude C at m
+        float res = 0.f;
+#pragma unroll
+        for (int j = 0; j < kMaxPairs; ++j) {
+            if (j >= Kp) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (2 * j + h < K) {
+                    const float wk = c.wsum[2 * j + h];
+                    const float rx = jk[j][h].x - ch.x * wk, ry = jk[j][h].y - ch.y * wk;
+                    res += rx * rx + ry * ry;
+                }
+            }
+        }
+        const float fv = (ch.x * ch.x + ch.y * ch.y) * (float)(K - 1) * c.wq / res;
+        if (v1) __stcs(Fout + i1, fv);
+        if (v2) __stcs(Fout + i2, fv);
     }
 }
 

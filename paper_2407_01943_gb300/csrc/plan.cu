@@ -1027,6 +1027,19 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         }
     }
 
+    // ---- taper sums W_k^0(0) = sum_n w_k(t_n) for the F-statistic (Sec. 3, Eq. f_stat) ----
+    {
+        std::vector<double> ws(K, 0.0);
+        double q = 0.0;
+        for (int k = 0; k < K; ++k) {
+            for (int64_t j = 0; j < N; ++j) ws[k] += w_sorted[(size_t)k * N + j];
+            q += ws[k] * ws[k];
+        }
+        p->wq = q;
+        if (opts.precision == 32) M2_TRY_OR(upload_typed<float>(pb, &p->d_wsum, ws));
+        else M2_TRY_OR(upload_typed<double>(pb, &p->d_wsum, ws));
+    }
+
     // ---- leakage estimate (App. B) ----
     M2_TRY_OR(pb.alloc(&p->d_Lhat, (size_t)K * g.I));
     M2_TRY_OR(pb.alloc(&p->d_Ehat, (size_t)g.I));

@@ -525,3 +525,80 @@ def test_exec_batch_mixed_generic_and_pipelined(dev):
         single = p.run(x[None, :], want=("P",))
         torch.cuda.synchronize()
         assert torch.equal(single["P"][0], P)
+
+
+# ---------------------------------------------------------------------------
+# Thomson F-statistic (Sec. 3, Eq. f_stat)
+# ---------------------------------------------------------------------------
+def _f_bound(Jg, Jr, Fr, K, prec):
+    """Per-band bound on |F_gpu - F_ref| / F_ref propagated from the eigencoefficient error at
+    that band: with eps = ||J_gpu - J_ref|| / ||J_ref|| over the K tapers, the projections of J on
+    W and on its complement move by at most eps ||J||, so the relative error of F is at most
+    2 eps (sqrt(1 + (K-1)/F) + sqrt(1 + F/(K-1))) to first order; 3x that, plus the rounding of
+    the statistic's own arithmetic (eps floor)."""
+    eps = np.linalg.norm(Jg - Jr, axis=0) / np.linalg.norm(Jr, axis=0)
+    eps = eps + (4e-7 * np.sqrt(K) if prec == 32 else 1e-14)
+    return 3 * eps * (np.sqrt(1 + (K - 1) / Fr) + np.sqrt(1 + Fr / (K - 1)))
+
+
+@pytest.mark.parametrize("prec,path", PATHS)
+def test_ftest_parity(dev, prec, path):
+    """F at every band against the oracle's F from its FP64 eigencoefficients (same tapers), within
+    the bound propagated from the eigencoefficient error; the injected lines are detected."""
+    from oracle import ftest as oft
+    scipy_stats = pytest.importorskip("scipy.stats")
+    N, K, I = 3000, 6, 8192
+    fw = 4.0 / N
+    t = synth.jittered(N, 0.4, 31)
+    X = np.stack([synth.tones(t, np.array([0.1 + 0.01 * b, -0.3]), np.array([1.5, 0.8]), 1.0, 90 + b)
+                  for b in range(2)])
+    w, lam = ogpss.nominal_tapers(t, 1.0, fw, K)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=prec, tapers=w, lam=lam, path=path)
+    out = run_plan(plan, X, dev, want=("J", "P", "F"))
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
+    crit = scipy_stats.f(2, 2 * K - 2).ppf(1 - 1.0 / N)
+    for b in range(X.shape[0]):
+        Fr = oft.f_statistic(Jr[b], w)
+        bound = _f_bound(out["J"][b], Jr[b], Fr, K, prec)
+        rel = np.abs(out["F"][b] - Fr) / Fr
+        assert np.all(rel <= bound), (np.max(rel / bound), int(np.argmax(rel / bound)))
+        line = int(round((0.1 + 0.01 * b + 0.5) * I))
+        assert out["F"][b][line] > crit
+    assert rel_l2(out["P"], Pr) <= TOL[prec]
+
+
+def test_ftest_generic_without_J(dev):
+    """Generic path, F requested without J: the internal J buffer gives the same F."""
+    N, K, I = 1200, 5, 4096
+    t = synth.jittered(N, 0.4, 8)
+    X = np.stack([synth.white(t, 1.0, 60 + b) for b in range(3)])
+    w = seeded_tapers(K, N, 3)
+    plan = pkg.Plan(t, 1.0, 3.0 / N, K, -0.5, 1.0 / I, I, precision=64, tapers=w, path=1, max_batch=2)
+    a = run_plan(plan, X, dev, want=("J", "F"))
+    b = run_plan(plan, X, dev, want=("P", "F"))
+    assert np.array_equal(a["F"], b["F"])
+
+
+def test_ftest_full_size_sampled(dev):
+    """jitter16k (N = 16384, K = 8, I = 2^18), FP32 packed path: F on sampled bands against the
+    oracle's F from its FP64 eigencoefficients at those bands."""
+    from oracle import ftest as oft
+    wl = synth.workload("jitter16k", batch=1)
+    w = seeded_tapers(wl.K, wl.N, 7)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w)
+    out = run_plan(plan, wl.x, dev, want=("J", "F"))
+    idx = sample_bands(wl.I, 256, 4)
+    Jr, _ = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    Fr = oft.f_statistic(Jr[0], w)
+    bound = _f_bound(out["J"][0][:, idx], Jr[0], Fr, wl.K, 32)
+    assert np.all(np.abs(out["F"][0][idx] - Fr) / Fr <= bound)
+
+
+def test_ftest_rejects_single_taper(dev):
+    t = synth.jittered(300, 0.4, 1)
+    plan = pkg.Plan(t, 1.0, 0.01, 1, -0.5, 1 / 1024, 1024, precision=32, tapers=seeded_tapers(1, 300, 0))
+    x = torch.zeros((1, 300), dtype=torch.float32, device=dev)
+    F = torch.empty((1, 1024), dtype=torch.float32, device=dev)
+    with pytest.raises(pkg.M2Error) as e:
+        plan.exec(x, F=F)
+    assert e.value.status == 1
