@@ -459,11 +459,12 @@ def run_ours(args):
     # Thomson F-statistic per band (Sec. 3, Eq. f_stat), optional output
     Fb = torch.empty((B, wl.I), dtype=rdt, device=dev) if "F" in args.outputs else None
 
-    def step(xin):
+    def step(xin, Pout=None):
+        Pout = P if Pout is None else Pout
         if Fb is None:
-            plan.exec(xin, J, E, P, Lh, Eh, stream=stream)
+            plan.exec(xin, J, E, Pout, Lh, Eh, stream=stream)
         else:
-            plan.exec(xin, J, E, P, stream=stream, F=Fb)
+            plan.exec(xin, J, E, Pout, stream=stream, F=Fb)
             if Lh is not None:
                 plan.exec(xin[:0], None, None, None, Lh, Eh, stream=stream)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -547,36 +548,58 @@ def run_ours(args):
                     "traffic": profiled_traffic(args.workload, dom, per_launch)}
 
     # ---- end to end through the public API with host buffers ----
+    # Every step copies its x from pinned host memory and reads its P-hat back to pinned host
+    # memory.  Steps are double-buffered the way a streaming caller would run them: the
+    # device-to-host read of step s runs on a copy stream while step s+1 computes (the execs
+    # themselves stay ordered on one stream, as a plan requires).
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(wl.x.astype(np.float32 if args.precision == 32 else np.float64)).pin_memory()
-        ph = torch.empty((B, wl.I), dtype=rdt).pin_memory()
-        xd = torch.empty_like(x)
-        for _ in range(2):
-            xd.copy_(xh, non_blocking=True)
-            step(xd)
-            ph.copy_(P, non_blocking=True)
+        ph = [torch.empty((B, wl.I), dtype=rdt).pin_memory() for _ in range(2)]
+        xd = [torch.empty_like(x) for _ in range(2)]
+        Pd = [P, torch.empty_like(P)]
+        cstream = torch.cuda.Stream(device=dev)
+        out_bytes = B * wl.I * rsz + (B * wl.K * wl.I * csz if J is not None else 0) + \
+            (B * wl.K * wl.I * rsz if E is not None else 0)
+        d2h_done = [torch.cuda.Event() for _ in range(2)]
+
+        def e2e_steps(n):
+            for s_ in range(n):
+                b = s_ % 2
+                stream.wait_event(d2h_done[b])  # P-hat buffer b was read back two steps ago
+                xd[b].copy_(xh, non_blocking=True)
+                step(xd[b], Pd[b])
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                cstream.wait_event(ev)
+                with torch.cuda.stream(cstream):
+                    ph[b].copy_(Pd[b], non_blocking=True)
+                    d2h_done[b].record(cstream)
+            stream.wait_stream(cstream)
+
+        for ev in d2h_done:
+            ev.record(stream)
+        e2e_steps(2)
         torch.cuda.synchronize()
-        ev_e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         torch.cuda.synchronize()
-        for s in range(args.steps):
-            flush_l2()
-            ev_e[s][0].record(stream)
-            xd.copy_(xh, non_blocking=True)
-            step(xd)
-            ph.copy_(P, non_blocking=True)
-            ev_e[s][1].record(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_steps(args.steps)
+        e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = float(sum(a.elapsed_time(b) for a, b in ev_e))
+        e2e_ms = float(e0.elapsed_time(e1))
         if world > 1:
             tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_ms = float(tt.item())
         e2e = {"value": world * args.steps * B * units_per_signal / (e2e_ms * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
-               "d2h_bytes_per_step": int(ph.numel() * ph.element_size()),
-               "ms_per_step": e2e_ms / args.steps}
+               "d2h_bytes_per_step": int(ph[0].numel() * ph[0].element_size()),
+               "ms_per_step": e2e_ms / args.steps,
+               "overlap": "double-buffered: the P-hat read-back of step s overlaps the execs of step s+1",
+               "l2": f"not flushed between steps: each step writes {out_bytes / 1e9:.2f} GB of outputs "
+                     f"({out_bytes / 129e6:.1f}x the 129 MB L2)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
