@@ -73,6 +73,28 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own signals (replicas: the units are partitioned, nothing is exchanged)."""
+    return 1000 * rank
+
+
+def job_time_ms(local_ms: float, world: int, device=None) -> float:
+    """The job's time: the slowest rank's (max over ranks; one all-reduce of a scalar, outside the
+    timed region)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job aggregate: the units all ranks processed over the slowest rank's time."""
+    return world * steps * units_per_rank_step / (job_ms * 1e-3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -432,7 +454,7 @@ def run_ours(args):
     pkg.build()
 
     B = args.batch
-    wl = synth.workload(args.workload, batch=B, seed=1000 * rank)
+    wl = synth.workload(args.workload, batch=B, seed=rank_seed(rank))
     rdt = torch.float32 if args.precision == 32 else torch.float64
     cdt = torch.complex64 if args.precision == 32 else torch.complex128
     csz, rsz = (8, 4) if args.precision == 32 else (16, 8)
@@ -514,13 +536,9 @@ def run_ours(args):
                        for i, n in enumerate(["spread", "cols", "rows", "epi"])}
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = job_time_ms(float(sum(step_ms)), world, dev)
     units_per_signal = wl.K * wl.N * wl.I
-    value = world * args.steps * B * units_per_signal / (total_ms * 1e-3)
+    value = job_throughput(B * units_per_signal, args.steps, world, total_ms)
     chunks = -(-B // info["chunk"])
     pipelined = info["path"] == 3
     launches = args.steps * (1 if pipelined else chunks * (4 if info["path"] == 2 else 3))
@@ -588,12 +606,8 @@ def run_ours(args):
         e2e_steps(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = float(e0.elapsed_time(e1))
-        if world > 1:
-            tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
-        e2e = {"value": world * args.steps * B * units_per_signal / (e2e_ms * 1e-3), "unit": UNIT,
+        e2e_ms = job_time_ms(float(e0.elapsed_time(e1)), world, dev)
+        e2e = {"value": job_throughput(B * units_per_signal, args.steps, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                "d2h_bytes_per_step": int(ph[0].numel() * ph[0].element_size()),
                "ms_per_step": e2e_ms / args.steps,
