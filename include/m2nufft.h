@@ -94,6 +94,11 @@ typedef struct {
                            3 = packed FP32 path as one persistent pipelined kernel per exec;
                            2 and 3 need real tapers, nf >= 2048 and a support of <= 64 rows
                            of 1024 cells (M2_ERR_ARG if the plan does not qualify) */
+    int tapers;         /* m2nufft_plan only: 0 = GEP (Eq. gep_at_A0, dense FP64, O(N^3)),
+                           1 = interpolated DPSS (Table 1 step 3 a-c: DPSS on N uniform nodes
+                           from t_1 to t_N, not-a-knot cubic spline to t, scaled to
+                           w^T R(B) w = 2 f_w; O(N) host work plus an O(N^2) FP64 pair sum on
+                           the GPU; eigenvalues = the concentrations w^T R(A0) w / w^T R(B) w) */
 } m2_opts;
 
 /* Geometry of a plan, for callers that size buffers or compute rooflines. */

@@ -34,7 +34,8 @@ class m2_fgrid(ctypes.Structure):
 
 class m2_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
-                ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("path", ctypes.c_int)]
+                ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("path", ctypes.c_int),
+                ("tapers", ctypes.c_int)]
 
 
 class m2_info(ctypes.Structure):
@@ -145,7 +146,7 @@ class Plan:
 
     def __init__(self, t, fs: float, f_w: float, K: int, f_lo: float, df: float, I: int,
                  precision: int = 32, tol: float = 0.0, mem_budget: int = 0, device: int = -1,
-                 max_batch: int = 0, tapers=None, lam=None, path: int = 0):
+                 max_batch: int = 0, tapers=None, lam=None, path: int = 0, taper_design: str = "gep"):
         L = load()
         self._t = np.ascontiguousarray(t, dtype=np.float64)
         self.N = int(self._t.shape[0])
@@ -154,7 +155,8 @@ class Plan:
         self.precision = int(precision)
         self.fs, self.f_w, self.f_lo, self.df = float(fs), float(f_w), float(f_lo), float(df)
         fg = m2_fgrid(self.f_lo, self.df, self.I)
-        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path))
+        design = {"gep": 0, "spline": 1}[taper_design]
+        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path), design)
         h = _VP()
         if tapers is None:
             st = L.m2nufft_plan(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(fg),

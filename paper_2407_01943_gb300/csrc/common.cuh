@@ -90,6 +90,9 @@ m2_status init_exec_kernels(int smem_optin);
 m2_status init_fast_kernels(int smem_optin);
 m2_status init_pipe_kernels(int smem_optin);
 m2_status init_device_kernels(int device);
+// Interpolated-DPSS nominal tapers (spline_tapers.cu): ts sorted; w_sorted [K][N], lam [K].
+m2_status spline_tapers(const std::vector<double>& ts, double fmax, double fw, int K,
+                        std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
                           cudaStream_t st);

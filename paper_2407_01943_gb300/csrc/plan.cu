@@ -722,13 +722,23 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                 set_error("repeated sampling time %.17g: R(B) is singular", ts[j]);
                 return bail(M2_ERR_GEP);
             }
-        if (N > 46340) {
-            set_error("GEP size N = %lld is above the dense solver limit (46340)", (long long)N);
+        if (opts.tapers != 0 && opts.tapers != 1) {
+            set_error("opts.tapers must be 0 (GEP) or 1 (interpolated DPSS)");
             return bail(M2_ERR_ARG);
         }
         std::vector<double> lam;
-        m2_status s = solve_gep(ts, fmax, f_w, K, opts.mem_budget, w_sorted, lam, p->gep_seconds);
-        if (s != M2_OK) return bail(s);
+        if (opts.tapers == 1) {
+            // Table 1 step 3 (a)-(c): DPSS on a uniform grid, cubic spline to t, R(B) normalisation
+            m2_status s = spline_tapers(ts, fmax, f_w, K, w_sorted, lam, p->gep_seconds);
+            if (s != M2_OK) return bail(s);
+        } else {
+            if (N > 46340) {
+                set_error("GEP size N = %lld is above the dense solver limit (46340)", (long long)N);
+                return bail(M2_ERR_ARG);
+            }
+            m2_status s = solve_gep(ts, fmax, f_w, K, opts.mem_budget, w_sorted, lam, p->gep_seconds);
+            if (s != M2_OK) return bail(s);
+        }
         // sign: sum_n w_k(t_n) (t_n - tbar)^(k mod 2) > 0
         double tbar = 0;
         for (double v : ts) tbar += v;

@@ -602,3 +602,47 @@ def test_ftest_rejects_single_taper(dev):
     with pytest.raises(pkg.M2Error) as e:
         plan.exec(x, F=F)
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# interpolated-DPSS tapers (Table 1 step 3 a-c), no GEP
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["jitter", "bernoulli"])
+def test_spline_tapers_match_oracle(dev, kind):
+    """Plan-time tapers from DPSS + not-a-knot spline + R(B) normalisation against the oracle's
+    (independent tridiagonal solver, scipy spline, dense quadratic forms); then J and P-hat with
+    them against the oracle's direct sum."""
+    from oracle import spline_tapers as ost
+    N, K, I = 1500, 6, 4096
+    fw = 4.0 / N
+    t = synth.jittered(N, 0.4, 17) if kind == "jitter" else synth.grid_bernoulli(1800, 0.17, 17)
+    N = t.size
+    wr, lr = ost.spline_tapers(t, 1.0, fw, K)
+    plan = pkg.Plan(t, 1.0, fw, K, -0.5, 1.0 / I, I, precision=64, taper_design="spline")
+    w, lam = plan.tapers()
+    np.testing.assert_allclose(w, wr, rtol=0, atol=1e-10 * np.abs(wr).max())
+    np.testing.assert_allclose(lam, lr, rtol=1e-10)
+    X = np.stack([synth.white(t, 1.0, 33 + b) for b in range(2)])
+    out = run_plan(plan, X, dev, want=("J", "P"))
+    Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
+    assert rel_l2(out["J"], Jr) <= TOL[64]
+    assert rel_l2(out["P"], Pr) <= TOL[64]
+
+
+def test_spline_tapers_full_size(dev):
+    """N = 16384 jittered, K = 8: the interpolated tapers are R(B)-normalised (checked block by
+    block against the oracle's R(B) rows), their concentrations lie in (0, 1) and do not exceed
+    the first GEP eigenvalue bound 1, and planning takes well under the GEP's time."""
+    import time
+    wl = synth.workload("jitter16k")
+    t0 = time.perf_counter()
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, taper_design="spline")
+    dt = time.perf_counter() - t0
+    w, lam = plan.tapers()
+    assert np.all((lam > 0) & (lam < 1))
+    RBw = np.zeros((wl.N, wl.K))
+    for r0 in range(0, wl.N, 1024):
+        blk = np.arange(r0, min(r0 + 1024, wl.N))
+        RBw[blk] = ogpss.gpss_rows(wl.t, blk, 0.5) @ w.T
+    np.testing.assert_allclose(np.einsum("kn,nk->k", w, RBw), 2 * wl.f_w, rtol=1e-10)
+    assert plan.info["gep_seconds"] < 5.0 and dt < 30.0
