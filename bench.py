@@ -171,9 +171,9 @@ def profiled_traffic(workload: str, kernel: str, nb: int):
     try:
         with open(path) as f:
             d = json.load(f)
-        src = open(os.path.join(ROOT, d["source"]), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
-            return None
+        for rel, h in d["sources"].items():
+            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16] != h:
+                return None
         return float(d["traffic_bytes_per_launch"]) * nb / float(d["signals_per_launch"])
     except Exception:
         return None
