@@ -71,6 +71,16 @@ typedef struct {
     int64_t I;
 } m2_fgrid;
 
+/* Sub-band of the multiband partition (Sec. 2.3 and Sec. 3): the signal band
+ * restricted to f_min <= |f| <= f_max, with the nominal analysis band
+ * |f - f_c0| <= f_w inside it.  f_min = 0, f_max = fs/2, f_c0 = 0 is the full
+ * band of m2nufft_plan. */
+typedef struct {
+    double f_c0;   /* nominal band centre */
+    double f_min;  /* 0 <= f_min < f_max */
+    double f_max;  /* <= fs/2 */
+} m2_subband;
+
 /* Output selection bits (informational; exec writes whatever pointers are non-NULL). */
 enum {
     M2_OUT_J = 1,
@@ -152,6 +162,35 @@ m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double
                                    const m2_opts* opts, m2nufft_plan_t* out);
 
 /*
+ * Plan for one sub-band of a multiband partition (Q > 1; Sec. 2.3, Sec. 3,
+ * Table 1 steps 2-4 per sub-band q).  The nominal tapers solve Eq. gep_at_A0
+ * with R(A0) centred at f_c0 (complex Hermitian, Eq. gpss_matrix_a) against the
+ * sub-band matrix R(B^q) (Eq. gpss_matrix_b_q), normalised to
+ * w^H R(B^q) w = 2 f_w; the eigencoefficients of the band centred at f_ci are
+ *   J_k(A_i) = sum_n conj(w_k(t_n)) x(t_n) e^{-i 2 pi (f_ci - f_c0) t_n}
+ * (Eq. eigencoefficients with Delta f_i = f_ci - f_c0), and P-hat as usual.
+ *   sb      host, the sub-band and nominal centre
+ *   fc      host, the absolute band centres f_ci = f_lo + i df of this sub-band
+ *   w       host [K][N] complex (re, im interleaved) tapers in the order of t, or
+ *           NULL to solve the GEP (FP64, cuSOLVER).  R(B^q) is numerically
+ *           singular once N exceeds 2 (f_max - f_min) T, so the GEP is solved on
+ *           its numerical range (eigenvalues above 1e-9 of the largest): a
+ *           standard Hermitian eigenproblem of the reduced matrix
+ *   lambda  host [K] eigenvalues when w is given, or NULL
+ * The tapers are complex, so exec runs the generic path (either precision);
+ * leakage estimates and the F-statistic are not formed for sub-band plans.
+ * The phase of each taper is fixed by making
+ * sum_n w_k(t_n) e^{-i 2 pi f_c0 t_n} (t_n - tbar)^(k mod 2) real and positive.
+ * A multiband analysis is Q such plans (one per sub-band) run on the same x,
+ * e.g. with one m2nufft_exec_batch call.
+ * Errors: as m2nufft_plan; M2_ERR_ARG when the nominal band is not inside the
+ * sub-band; M2_ERR_GEP when K exceeds the numerical rank of R(B^q).
+ */
+m2_status m2nufft_plan_subband(const double* t, int64_t N, double fs, double f_w, int K, const m2_subband* sb,
+                               const m2_fgrid* fc, const double* w, const double* lambda, const m2_opts* opts,
+                               m2nufft_plan_t* out);
+
+/*
  * Run the per-signal path for B signals that share the plan's sampling times.
  *   x      device [B][N] real (plan precision), each row in the order of t
  *   B      number of signals, >= 0 (0 is a no-op)
@@ -225,6 +264,10 @@ int m2nufft_set_batch_mode(int mode);
  * (host [K], descending; NaN when the plan was made from caller tapers
  * without eigenvalues).  Either pointer may be NULL. */
 m2_status m2nufft_get_tapers(m2nufft_plan_t p, double* w, double* lambda);
+
+/* Complex tapers (host [K][N], re and im interleaved, order of t) and eigenvalues (host [K]); for a
+ * full-band plan the imaginary parts are 0.  m2nufft_get_tapers rejects sub-band plans. */
+m2_status m2nufft_get_tapers_complex(m2nufft_plan_t p, double* w, double* lambda);
 
 /* Copy L-hat (host [K][I]) and E-hat (host [I]); either may be NULL. */
 m2_status m2nufft_get_leakage(m2nufft_plan_t p, double* Lhat, double* Ehat);

@@ -32,6 +32,10 @@ class m2_fgrid(ctypes.Structure):
     _fields_ = [("f_lo", ctypes.c_double), ("df", ctypes.c_double), ("I", ctypes.c_int64)]
 
 
+class m2_subband(ctypes.Structure):
+    _fields_ = [("f_c0", ctypes.c_double), ("f_min", ctypes.c_double), ("f_max", ctypes.c_double)]
+
+
 class m2_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("path", ctypes.c_int),
@@ -62,6 +66,10 @@ EXPORTS = [
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
     ("m2nufft_get_tapers", ctypes.c_int, [_VP, _DP, _DP]),
+    ("m2nufft_get_tapers_complex", ctypes.c_int, [_VP, _DP, _DP]),
+    ("m2nufft_plan_subband", ctypes.c_int, [_DP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(m2_subband), ctypes.POINTER(m2_fgrid), _DP, _DP,
+                                            ctypes.POINTER(m2_opts), ctypes.POINTER(_VP)]),
     ("m2nufft_get_leakage", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_info", ctypes.c_int, [_VP, ctypes.POINTER(m2_info)]),
     ("m2nufft_set_timing", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -146,7 +154,10 @@ class Plan:
 
     def __init__(self, t, fs: float, f_w: float, K: int, f_lo: float, df: float, I: int,
                  precision: int = 32, tol: float = 0.0, mem_budget: int = 0, device: int = -1,
-                 max_batch: int = 0, tapers=None, lam=None, path: int = 0, taper_design: str = "gep"):
+                 max_batch: int = 0, tapers=None, lam=None, path: int = 0, taper_design: str = "gep",
+                 subband=None):
+        """subband = (f_c0, f_min, f_max) makes a sub-band plan (m2nufft_plan_subband): band centres
+        f_lo + i df are absolute, tapers (if given) complex [K, N]."""
         L = load()
         self._t = np.ascontiguousarray(t, dtype=np.float64)
         self.N = int(self._t.shape[0])
@@ -158,7 +169,23 @@ class Plan:
         design = {"gep": 0, "spline": 1}[taper_design]
         op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path), design)
         h = _VP()
-        if tapers is None:
+        self.subband = subband
+        if subband is not None:
+            sb = m2_subband(*[float(v) for v in subband])
+            wp = lp = None
+            if tapers is not None:
+                wc = np.ascontiguousarray(np.asarray(tapers, dtype=np.complex128))
+                if wc.shape != (self.K, self.N):
+                    raise ValueError(f"tapers must have shape ({self.K}, {self.N})")
+                self._wc_in = wc.view(np.float64)
+                wp = _dptr(self._wc_in)
+            if lam is not None:
+                self._lam_in = np.ascontiguousarray(lam, dtype=np.float64)
+                lp = _dptr(self._lam_in)
+            st = L.m2nufft_plan_subband(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(sb),
+                                        ctypes.byref(fg), wp, lp, ctypes.byref(op), ctypes.byref(h))
+            _check(st, "m2nufft_plan_subband")
+        elif tapers is None:
             st = L.m2nufft_plan(_dptr(self._t), self.N, self.fs, self.f_w, self.K, ctypes.byref(fg),
                                 ctypes.byref(op), ctypes.byref(h))
             _check(st, "m2nufft_plan")
@@ -194,8 +221,14 @@ class Plan:
         return torch.complex64 if self.precision == 32 else torch.complex128
 
     def tapers(self):
-        w = np.empty((self.K, self.N))
+        """(w [K, N], lambda [K]); w is complex for a sub-band plan."""
         lam = np.empty(self.K)
+        if self.subband is not None:
+            wc = np.empty((self.K, self.N), dtype=np.complex128)
+            _check(load().m2nufft_get_tapers_complex(self._h, _dptr(wc.view(np.float64)), _dptr(lam)),
+                   "m2nufft_get_tapers_complex")
+            return wc, lam
+        w = np.empty((self.K, self.N))
         _check(load().m2nufft_get_tapers(self._h, _dptr(w), _dptr(lam)), "m2nufft_get_tapers")
         return w, lam
 

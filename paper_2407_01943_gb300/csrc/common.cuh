@@ -90,6 +90,10 @@ m2_status init_exec_kernels(int smem_optin);
 m2_status init_fast_kernels(int smem_optin);
 m2_status init_pipe_kernels(int smem_optin);
 m2_status init_device_kernels(int device);
+// Sub-band nominal tapers (subband.cu): ts sorted; w_re, w_im [K][N], lam [K] descending.
+m2_status solve_gep_subband(const std::vector<double>& ts, double f_w, int K, double f_c0, double f_min,
+                            double f_max, size_t budget, std::vector<double>& w_re, std::vector<double>& w_im,
+                            std::vector<double>& lam, double& seconds);
 // Interpolated-DPSS nominal tapers (spline_tapers.cu): ts sorted; w_sorted [K][N], lam [K].
 m2_status spline_tapers(const std::vector<double>& ts, double fmax, double fw, int K,
                         std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds);
@@ -135,7 +139,10 @@ struct m2nufft_plan_s {
     double gep_seconds = 0.0;
     size_t device_bytes = 0;
     std::vector<double> t;       // caller order
-    std::vector<double> w;       // [K][N] caller order
+    std::vector<double> w;       // [K][N] caller order (real part for sub-band plans)
+    std::vector<double> w_im;    // [K][N] caller order, imaginary part (sub-band plans)
+    int complex_taper = 0;       // sub-band plan: complex tapers, band grid relative to f_c0
+    double f_c0 = 0.0;           // nominal band centre
     std::vector<double> lambda;  // [K] descending
 
     // device caches (precision-typed buffers are void*)

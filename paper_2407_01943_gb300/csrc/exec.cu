@@ -476,6 +476,10 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
         set_error("m2nufft_exec_ftest: the F-statistic needs K >= 2 tapers (F(2, 2K - 2))");
         return M2_ERR_ARG;
     }
+    if (F && p->complex_taper) {
+        set_error("m2nufft_exec_ftest: the F-statistic is formed for full-band plans (real tapers, f_c0 = 0)");
+        return M2_ERR_ARG;
+    }
     if (B > 0) {
         if (p->precision == 32) M2_TRY(exec_typed<float>(p, x, B, J, E, P, F, st));
         else M2_TRY(exec_typed<double>(p, x, B, J, E, P, F, st));

@@ -624,7 +624,7 @@ std::vector<double> unit_roots(int64_t count, int64_t n, int64_t step) {
 
 m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
                      const double* w_given, const double* lam_given, const m2_opts* opts_in,
-                     m2nufft_plan_t* out) {
+                     m2nufft_plan_t* out, const m2_subband* sb = nullptr, const double* wc_given = nullptr) {
     if (!out) {
         set_error("out is NULL");
         return M2_ERR_ARG;
@@ -665,6 +665,30 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
             return M2_ERR_ARG;
         }
     }
+    // sub-band B^q = {f_min <= |f| <= f_max} and nominal centre f_c0 (Sec. 2.3, Sec. 3 multiband partition)
+    const bool cplx = sb != nullptr;
+    const double f_c0 = cplx ? sb->f_c0 : 0.0;
+    if (cplx) {
+        const double a = std::fabs(sb->f_c0);
+        const bool inside = sb->f_min == 0.0 ? (a + f_w <= sb->f_max) : (sb->f_min <= a - f_w && a + f_w <= sb->f_max);
+        if (!(sb->f_min >= 0) || !(sb->f_max > sb->f_min) || !(sb->f_max <= fmax) || !std::isfinite(sb->f_c0) ||
+            !inside) {
+            set_error("sub-band needs 0 <= f_min < f_max <= fs/2 and the nominal band |f - f_c0| <= f_w inside "
+                      "f_min <= |f| <= f_max");
+            return M2_ERR_ARG;
+        }
+    }
+    if (wc_given) {
+        for (int64_t q = 0; q < 2 * (int64_t)K * N; ++q)
+            if (!std::isfinite(wc_given[q])) {
+                set_error("taper value %lld is not finite", (long long)q);
+                return M2_ERR_ARG;
+            }
+    }
+    // band centres relative to the nominal centre: Delta f_i = f_ci - f_c0 (Eq. freq_shift_op)
+    m2_fgrid fcs = *fc;
+    fcs.f_lo = fc->f_lo - f_c0;
+    fc = &fcs;
     if (w_given) {
         for (int64_t q = 0; q < (int64_t)K * N; ++q)
             if (!std::isfinite(w_given[q])) {
@@ -708,8 +732,61 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     p->integer_grid = integer_grid ? 1 : 0;
 
     // ---- tapers ----
-    std::vector<double> w_sorted((size_t)K * N);
-    if (w_given) {
+    std::vector<double> w_sorted((size_t)K * N), w_sorted_im;  // imaginary parts: sub-band plans only
+    if (cplx) {
+        w_sorted_im.assign((size_t)K * N, 0.0);
+        if (wc_given) {
+            for (int k = 0; k < K; ++k)
+                for (int64_t j = 0; j < N; ++j) {
+                    w_sorted[(size_t)k * N + j] = wc_given[2 * ((size_t)k * N + ord[j])];
+                    w_sorted_im[(size_t)k * N + j] = wc_given[2 * ((size_t)k * N + ord[j]) + 1];
+                }
+            if (lam_given) {
+                p->lambda.assign(lam_given, lam_given + K);
+                p->have_lambda = 1;
+            }
+        } else {
+            for (int64_t j = 0; j + 1 < N; ++j)
+                if (ts[j] == ts[j + 1]) {
+                    set_error("repeated sampling time %.17g: R(B^q) is singular", ts[j]);
+                    return bail(M2_ERR_GEP);
+                }
+            if (N > 46340) {
+                set_error("GEP size N = %lld is above the dense solver limit (46340)", (long long)N);
+                return bail(M2_ERR_ARG);
+            }
+            std::vector<double> lam;
+            m2_status s = solve_gep_subband(ts, f_w, K, f_c0, sb->f_min, sb->f_max, opts.mem_budget, w_sorted,
+                                            w_sorted_im, lam, p->gep_seconds);
+            if (s != M2_OK) return bail(s);
+            // phase: sum_n w_k(t_n) e^{-i 2 pi f_c0 t_n} (t_n - tbar)^(k mod 2) real and positive
+            double tbar = 0;
+            for (double v : ts) tbar += v;
+            tbar /= (double)N;
+            for (int k = 0; k < K; ++k) {
+                double sr = 0, si = 0;
+                for (int64_t j = 0; j < N; ++j) {
+                    const double cyc = frac_cycles(-f_c0, 0.0, ts[j]);
+                    const double c = std::cos(2.0 * kPi * cyc), sn = std::sin(2.0 * kPi * cyc);
+                    const double fac = (k & 1) ? (ts[j] - tbar) : 1.0;
+                    const double wr = w_sorted[(size_t)k * N + j], wi = w_sorted_im[(size_t)k * N + j];
+                    sr += fac * (wr * c - wi * sn);
+                    si += fac * (wr * sn + wi * c);
+                }
+                const double a = std::hypot(sr, si);
+                if (a > 0) {
+                    const double cr = sr / a, ci = -si / a;  // multiply by conj(S) / |S|
+                    for (int64_t j = 0; j < N; ++j) {
+                        const double wr = w_sorted[(size_t)k * N + j], wi = w_sorted_im[(size_t)k * N + j];
+                        w_sorted[(size_t)k * N + j] = wr * cr - wi * ci;
+                        w_sorted_im[(size_t)k * N + j] = wr * ci + wi * cr;
+                    }
+                }
+            }
+            p->lambda = lam;
+            p->have_lambda = 1;
+        }
+    } else if (w_given) {
         for (int k = 0; k < K; ++k)
             for (int64_t j = 0; j < N; ++j) w_sorted[(size_t)k * N + j] = w_given[(size_t)k * N + ord[j]];
         if (lam_given) {
@@ -755,6 +832,13 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     p->w.assign((size_t)K * N, 0.0);
     for (int k = 0; k < K; ++k)
         for (int64_t j = 0; j < N; ++j) p->w[(size_t)k * N + ord[j]] = w_sorted[(size_t)k * N + j];
+    p->complex_taper = cplx ? 1 : 0;
+    p->f_c0 = f_c0;
+    if (cplx) {
+        p->w_im.assign((size_t)K * N, 0.0);
+        for (int k = 0; k < K; ++k)
+            for (int64_t j = 0; j < N; ++j) p->w_im[(size_t)k * N + ord[j]] = w_sorted_im[(size_t)k * N + j];
+    }
 
     // ---- geometry ----
     Geometry& g = p->g;
@@ -777,7 +861,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     // whole span: 1e-9 cycles for FP32 plans (relative effect <= 6.3e-9, far below their tolerance; a
     // grid like f_lo = -1/2, df = 1/I leaves f_mid = O(1e-16) from the rounding of df), 1e-12 for FP64
     const double real_thresh = opts.precision == 32 ? 1e-9 : 1e-12;
-    g.real_taper = (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < real_thresh ? 1 : 0;
+    g.real_taper = !cplx && (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < real_thresh ? 1 : 0;
     // ---- exec path, fine-grid length and spreading kernel ----
     // generic path: nf = power of two >= 2 I (sigma in [2, 4)), w = ceil(log10(1/tol)) + 1, beta = 2.30 w.
     // packed FP32 path: nf = smallest 2^a or 3 * 2^a >= 1.5 I (sigma in [1.5, 2)), w = ceil(1.25 log10(1/tol)) + 1,
@@ -940,9 +1024,11 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
                 const double cyc = frac_cycles(g.fmid_hi, g.fmid_lo, ts[pts[q].sidx]);
                 const double c = std::cos(2.0 * kPi * cyc), s = std::sin(2.0 * kPi * cyc);
                 for (int k = 0; k < K; ++k) {
+                    // conj(w_k) e^{-i 2 pi f_mid t} (Eq. eigencoefficients: the conjugated taper)
                     const double wv = w_sorted[(size_t)k * N + pts[q].sidx];
-                    tap[2 * ((size_t)k * g.P + q)] = wv * c;
-                    tap[2 * ((size_t)k * g.P + q) + 1] = -wv * s;
+                    const double wi = cplx ? w_sorted_im[(size_t)k * N + pts[q].sidx] : 0.0;
+                    tap[2 * ((size_t)k * g.P + q)] = wv * c - wi * s;
+                    tap[2 * ((size_t)k * g.P + q) + 1] = -wv * s - wi * c;
                 }
             }
         }
@@ -1053,7 +1139,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     // ---- leakage estimate (App. B) ----
     M2_TRY_OR(pb.alloc(&p->d_Lhat, (size_t)K * g.I));
     M2_TRY_OR(pb.alloc(&p->d_Ehat, (size_t)g.I));
-    if (p->have_lambda) {
+    if (p->have_lambda && !cplx) {
         const unsigned blocks = (unsigned)((g.I + 127) / 128);
         if (integer_grid) {
             std::vector<double> Lk(K);
@@ -1150,10 +1236,45 @@ extern "C" m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double
     return m2::build_plan(t, N, fs, f_w, K, fc, w, lambda, opts, out);
 }
 
+extern "C" m2_status m2nufft_plan_subband(const double* t, int64_t N, double fs, double f_w, int K,
+                                          const m2_subband* sb, const m2_fgrid* fc, const double* w,
+                                          const double* lambda, const m2_opts* opts, m2nufft_plan_t* out) {
+    m2::clear_error();
+    if (!sb) {
+        m2::set_error("sub-band is NULL");
+        return M2_ERR_ARG;
+    }
+    return m2::build_plan(t, N, fs, f_w, K, fc, nullptr, lambda, opts, out, sb, w);
+}
+
+extern "C" m2_status m2nufft_get_tapers_complex(m2nufft_plan_t p, double* w, double* lambda) {
+    m2::clear_error();
+    if (!p) {
+        m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    if (w) {
+        for (size_t q = 0; q < p->w.size(); ++q) {
+            w[2 * q] = p->w[q];
+            w[2 * q + 1] = p->complex_taper ? p->w_im[q] : 0.0;
+        }
+    }
+    if (lambda) {
+        if (p->have_lambda) std::memcpy(lambda, p->lambda.data(), sizeof(double) * p->lambda.size());
+        else
+            for (int k = 0; k < p->g.K; ++k) lambda[k] = std::nan("");
+    }
+    return M2_OK;
+}
+
 extern "C" m2_status m2nufft_get_tapers(m2nufft_plan_t p, double* w, double* lambda) {
     m2::clear_error();
     if (!p) {
         m2::set_error("plan is NULL");
+        return M2_ERR_ARG;
+    }
+    if (w && p->complex_taper) {
+        m2::set_error("m2nufft_get_tapers: the plan's tapers are complex; use m2nufft_get_tapers_complex");
         return M2_ERR_ARG;
     }
     if (w) std::memcpy(w, p->w.data(), sizeof(double) * p->w.size());

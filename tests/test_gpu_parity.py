@@ -646,3 +646,95 @@ def test_spline_tapers_full_size(dev):
         RBw[blk] = ogpss.gpss_rows(wl.t, blk, 0.5) @ w.T
     np.testing.assert_allclose(np.einsum("kn,nk->k", w, RBw), 2 * wl.f_w, rtol=1e-10)
     assert plan.info["gep_seconds"] < 5.0 and dt < 30.0
+
+
+# ---------------------------------------------------------------------------
+# multiband: sub-band plans (Sec. 2.3, Sec. 3, Eq. gpss_matrix_b_q, f_c0 != 0)
+# ---------------------------------------------------------------------------
+def _subband_oracle(t, X, w, f_c0, f_lo, df, I):
+    Js, Ps = [], []
+    for b in range(X.shape[0]):
+        J, _, P = oest.m2nufft(t, X[b], w, f_lo - f_c0, df, I)
+        Js.append(J)
+        Ps.append(P)
+    return np.stack(Js), np.stack(Ps)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_subband_parity(dev, prec):
+    """Sub-band [0.1, 0.3] with nominal centre 0.2 on a jittered pattern: complex tapers from the
+    oracle's Hermitian GEP; J and P-hat at absolute band centres inside the sub-band against the
+    direct sum with Delta f_i = f_ci - f_c0."""
+    N, K, I = 1200, 4, 2048
+    fw, f_c0, f_min, f_max = 4.0 / N, 0.2, 0.1, 0.3
+    t = synth.jittered(N, 0.4, 23)
+    w, lam = ogpss.subband_tapers(t, fw, K, f_c0, f_min, f_max)
+    f_lo, df = 0.105, 0.19 / I
+    X = np.stack([synth.tones(t, np.array([0.17, 0.26]), np.array([1.0, 0.5]), 1.0, 70 + b) for b in range(2)])
+    plan = pkg.Plan(t, 1.0, fw, K, f_lo, df, I, precision=prec, tapers=w, lam=lam, subband=(f_c0, f_min, f_max))
+    assert plan.info["path"] == 1 and plan.info["real_taper"] == 0
+    out = run_plan(plan, X, dev, want=("J", "P"))
+    Jr, Pr = _subband_oracle(t, X, w, f_c0, f_lo, df, I)
+    assert rel_l2(out["J"], Jr) <= TOL[prec]
+    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    wg, lg = plan.tapers()
+    np.testing.assert_array_equal(wg, w)
+
+
+def test_subband_gep_matches_oracle(dev):
+    """The GPU's range-restricted Hermitian GEP against the oracle's: eigenvalues, the K-dimensional
+    taper subspace (R(B^q) inner products of the two bases are 2 f_w times a unitary matrix), the
+    normalisation and the phase rule."""
+    N, K = 900, 5
+    fw, f_c0, f_min, f_max = 4.0 / N, 0.31, 0.22, 0.45
+    t = synth.grid_bernoulli(1100, 0.18, 4)
+    N = t.size
+    w, lam = ogpss.subband_tapers(t, fw, K, f_c0, f_min, f_max)
+    plan = pkg.Plan(t, 1.0, fw, K, 0.25, 0.1 / 512, 512, precision=64, subband=(f_c0, f_min, f_max))
+    wg, lg = plan.tapers()
+    np.testing.assert_allclose(lg, lam, atol=1e-10)
+    RB = ogpss.gpss_matrix_b_sub(t, f_min, f_max)
+    G = np.conj(wg) @ RB @ w.T / (2 * fw)
+    sv = np.linalg.svd(G, compute_uv=False)
+    np.testing.assert_allclose(sv, 1.0, atol=1e-8)
+    np.testing.assert_allclose(np.real(np.einsum("kn,nm,km->k", np.conj(wg), RB, wg)), 2 * fw, rtol=1e-10)
+    dem = np.exp(-2j * np.pi * f_c0 * t)
+    tc = t - t.mean()
+    for k in range(K):
+        s = np.sum(wg[k] * dem * (tc if k % 2 else 1.0))
+        assert s.real > 0 and abs(s.imag) < 1e-9 * abs(s)
+
+
+def test_multiband_partition_batch(dev):
+    """Q = 3 sub-bands partitioning [0, 1/2] run as one exec_batch on the same signal: each equals
+    its own exec bit for bit and the oracle within the FP64 tolerance."""
+    N, K = 700, 3
+    fw = 3.0 / N
+    t = synth.jittered(N, 0.4, 29)
+    x = synth.white(t, 1.0, 5)
+    bands = [(0.06, 0.0, 0.12), (0.2, 0.12, 0.3), (0.4, 0.3, 0.5)]
+    I = 512
+    plans, Ps, ws = [], [], []
+    for f_c0, a, b in bands:
+        w, lam = ogpss.subband_tapers(t, fw, K, f_c0, a, b)
+        lo = max(a, f_c0 - 0.05)
+        plans.append(pkg.Plan(t, 1.0, fw, K, lo, 0.1 / I, I, precision=64, tapers=w, lam=lam,
+                              subband=(f_c0, a, b)))
+        ws.append((w, f_c0, lo))
+        Ps.append(torch.empty((I,), dtype=torch.float64, device=dev))
+    xs = [torch.from_numpy(x).to(dev) for _ in bands]
+    pkg.exec_batch(plans, xs, None, None, Ps)
+    torch.cuda.synchronize()
+    for p, P, (w, f_c0, lo) in zip(plans, Ps, ws):
+        single = p.run(xs[0][None, :], want=("P",))
+        torch.cuda.synchronize()
+        assert torch.equal(single["P"][0], P)
+        _, Pr = _subband_oracle(t, x[None, :], w, f_c0, lo, 0.1 / I, I)
+        assert rel_l2(P.cpu().numpy(), Pr[0]) <= TOL[64]
+
+
+def test_subband_rejects_band_outside(dev):
+    t = synth.jittered(300, 0.4, 1)
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.Plan(t, 1.0, 0.02, 2, 0.1, 1e-4, 64, precision=64, subband=(0.11, 0.1, 0.3))
+    assert e.value.status == 1
