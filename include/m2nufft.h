@@ -353,6 +353,22 @@ m2_status m2nufft_leakage_static(const double* t, int64_t N, double fs, double f
  */
 m2_status m2nufft_pipe_selftest(int timeout_ms, void* stream);
 
+/*
+ * The suboptimality measure with the optimal per-band eigenvalues (Sec. 3,
+ * Eq. subopt_measure):  E_i = (1/K) sum_k |lambda_k^i - lambda_k^0|, where
+ * lambda_k^i are the K largest eigenvalues of the GEP at band A_i itself,
+ * R(A_i) w = lambda R(B) w (R(A_i) = Eq. gpss_matrix_a centred at f_i), and
+ * lambda_k^0 the plan's nominal eigenvalues.  It is what L-hat / E-hat estimate
+ * without per-band GEPs; this entry point computes it exactly for small
+ * problems (FP64 on the GPU: one Cholesky of R(B), batched reductions, one
+ * Hermitian eigenvalue solve per band).  Synchronous.
+ *   E         host [I] output
+ *   lam_band  host [I][K] output (per-band eigenvalues, descending) or NULL
+ * Errors: M2_ERR_ARG for sub-band plans, plans without eigenvalues, or
+ * N > 512 or I N^3 > 4e12; M2_ERR_GEP when R(B) is not positive definite.
+ */
+m2_status m2nufft_true_suboptimality(m2nufft_plan_t p, double* E, double* lam_band);
+
 /* Release every resource of the plan (synchronises its device first).  NULL is a no-op. */
 m2_status m2nufft_destroy(m2nufft_plan_t p);
 

@@ -77,6 +77,7 @@ EXPORTS = [
     ("m2nufft_leakage_static", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               ctypes.POINTER(m2_fgrid), _VP, _VP, _VP, _VP, _VP]),
     ("m2nufft_pipe_selftest", ctypes.c_int, [ctypes.c_int, _VP]),
+    ("m2nufft_true_suboptimality", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_pipe_profile", ctypes.c_int, [_VP, _DP, _DP, ctypes.POINTER(ctypes.c_int64)]),
     ("m2nufft_destroy", ctypes.c_int, [_VP]),
     ("m2nufft_last_error", ctypes.c_char_p, []),
@@ -299,6 +300,13 @@ class Plan:
         _check(load().m2nufft_get_timing(self._h, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                "m2nufft_get_timing")
         return ms, n
+
+    def true_suboptimality(self):
+        """(E [I], per-band eigenvalues [I, K]) from per-band GEPs (small N only)."""
+        E = np.empty(self.I)
+        lb = np.empty((self.I, self.K))
+        _check(load().m2nufft_true_suboptimality(self._h, _dptr(E), _dptr(lb)), "m2nufft_true_suboptimality")
+        return E, lb
 
     def get_pipe_profile(self):
         """Persistent kernel (path 3): per-stage (spread, columns, rows, epilogue) summed item

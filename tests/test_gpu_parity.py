@@ -738,3 +738,31 @@ def test_subband_rejects_band_outside(dev):
     with pytest.raises(pkg.M2Error) as e:
         pkg.Plan(t, 1.0, 0.02, 2, 0.1, 1e-4, 64, precision=64, subband=(0.11, 0.1, 0.3))
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# true suboptimality from per-band GEPs (Sec. 3, Eq. subopt_measure)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["jitter", "integer"])
+def test_true_suboptimality_matches_oracle(dev, kind):
+    """E_i from the GPU's per-band Hermitian GEPs against the oracle's (LAPACK per band); on an
+    integer grid E = 0; the plan's own L-hat for the leading taper is consistent with the per-band
+    optimum (lambda_hat_0^i <= lambda_0^i, Courant-Fischer)."""
+    from oracle import true_subopt as ots
+    t = synth.jittered(40, 0.4, 5) if kind == "jitter" else synth.grid_bernoulli(52, 0.2, 3)
+    N, K, fw, I = t.size, 3, 3.0 / 40, 96
+    w, lam0 = ogpss.nominal_tapers(t, 1.0, fw, K)
+    f_lo, df = -0.42, 0.84 / I  # analysis bands inside |f| <= 1/2
+    plan = pkg.Plan(t, 1.0, fw, K, f_lo, df, I, precision=64, tapers=w, lam=lam0)
+    E, lb = plan.true_suboptimality()
+    freqs = f_lo + df * np.arange(I)
+    lbr = ots.band_eigenvalues(t, 1.0, fw, K, freqs)
+    np.testing.assert_allclose(lb, lbr, atol=1e-10)
+    np.testing.assert_allclose(E, ots.true_suboptimality(lam0, lbr), atol=1e-10)
+    if kind == "integer":
+        assert np.max(np.abs(E)) < 1e-10
+    else:
+        L, Eh = plan.leakage()
+        lam_hat0 = lam0[0] * 2 * fw / oleak.leakage_denominator(t, w, 1.0, freqs)[0]
+        np.testing.assert_allclose(np.abs(lam0[0] - lam_hat0), L[0], atol=1e-9)
+        assert np.all(lb[:, 0] >= lam_hat0 - 1e-10)
