@@ -116,9 +116,9 @@ extern "C" m2_status m2nufft_true_suboptimality(m2nufft_plan_t p, double* E, dou
     M2_CUDA_TRY(alloc((void**)&G, sizeof(double2) * (size_t)group * N * N));
     M2_CUDA_TRY(alloc((void**)&T, sizeof(double2) * (size_t)group * N * N));
     M2_CUDA_TRY(alloc((void**)&C, sizeof(double2) * (size_t)group * N * N));
-    M2_CUDA_TRY(alloc((void**)&dW, sizeof(double) * N));
+    M2_CUDA_TRY(alloc((void**)&dW, sizeof(double) * (size_t)group * N));
     M2_CUDA_TRY(alloc((void**)&df, sizeof(double) * group));
-    M2_CUDA_TRY(alloc((void**)&dinfo, sizeof(int)));
+    M2_CUDA_TRY(alloc((void**)&dinfo, sizeof(int) * (size_t)group));
     M2_CUDA_TRY(cudaMemcpy(dt, tc.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     ts_matrices_kernel<<<dim3((N + 127) / 128, N), 128>>>(dt, N, 0.5 * p->fs, p->f_w, RB, RA);
     M2_CUDA_TRY(cudaGetLastError());
@@ -171,7 +171,8 @@ extern "C" m2_status m2nufft_true_suboptimality(m2nufft_plan_t p, double* E, dou
         return M2_ERR_GEP;
     }
     M2_CUDA_TRY(alloc((void**)&zwork, sizeof(double2) * std::max(lwz, 1)));
-    std::vector<double> w(N), lb((size_t)I * K);
+    std::vector<double> w((size_t)group * N), lb((size_t)I * K);
+    std::vector<int> infos(group);
     const cuDoubleComplex one = {1.0, 0.0}, zero = {0.0, 0.0};
     for (int64_t i0 = 0; i0 < I; i0 += group) {
         const int nb = (int)std::min<int64_t>(group, I - i0);
@@ -192,21 +193,24 @@ extern "C" m2_status m2nufft_true_suboptimality(m2nufft_plan_t p, double* E, dou
             set_error("m2nufft_true_suboptimality: batched GEMM failed");
             return M2_ERR_CUDA;
         }
+        // one eigenvalue solve per band, results gathered once per group
         for (int b = 0; b < nb; ++b) {
             if (cusolverDnZheevd(hs, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, N,
-                                 reinterpret_cast<cuDoubleComplex*>(C) + (size_t)b * N * N, N, dW,
-                                 reinterpret_cast<cuDoubleComplex*>(zwork), lwz, dinfo) != CUSOLVER_STATUS_SUCCESS) {
+                                 reinterpret_cast<cuDoubleComplex*>(C) + (size_t)b * N * N, N, dW + (size_t)b * N,
+                                 reinterpret_cast<cuDoubleComplex*>(zwork), lwz, dinfo + b) != CUSOLVER_STATUS_SUCCESS) {
                 set_error("m2nufft_true_suboptimality: heevd failed");
                 return M2_ERR_GEP;
             }
-            M2_CUDA_TRY(cudaMemcpy(w.data(), dW, sizeof(double) * N, cudaMemcpyDeviceToHost));
-            M2_CUDA_TRY(cudaMemcpy(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost));
-            if (info != 0) {
+        }
+        M2_CUDA_TRY(cudaMemcpy(w.data(), dW, sizeof(double) * (size_t)nb * N, cudaMemcpyDeviceToHost));
+        M2_CUDA_TRY(cudaMemcpy(infos.data(), dinfo, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+        for (int b = 0; b < nb; ++b) {
+            if (infos[b] != 0) {
                 set_error("m2nufft_true_suboptimality: band %lld eigenvalues did not converge (info %d)",
-                          (long long)(i0 + b), info);
+                          (long long)(i0 + b), infos[b]);
                 return M2_ERR_GEP;
             }
-            for (int k = 0; k < K; ++k) lb[(size_t)(i0 + b) * K + k] = w[N - 1 - k];
+            for (int k = 0; k < K; ++k) lb[(size_t)(i0 + b) * K + k] = w[(size_t)b * N + N - 1 - k];
         }
     }
     for (int64_t i = 0; i < I; ++i) {
