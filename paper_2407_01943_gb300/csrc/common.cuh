@@ -99,7 +99,7 @@ m2_status spline_tapers(const std::vector<double>& ts, double fmax, double fw, i
                         std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
-                          cudaStream_t st);
+                          cudaStream_t st, int lane = 0);
 // Stage-batched executor of uneven batches of packed plans (hbatch.cu).
 struct HBatch;
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
@@ -169,6 +169,14 @@ struct m2nufft_plan_s {
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C
     void* d_Z = nullptr;           // workspace [chunk][K][nf] C
     void* d_X = nullptr;           // packed path workspace [chunk][K/2][1024][n1] C: row transforms, transposed
+    // packed path, execs of more than one chunk: a second workspace and two internal streams, so
+    // that chunk c's epilogue (HBM-bound) overlaps chunk c+1's spread and FFTs (issue-bound)
+    void* d_g2 = nullptr;
+    void* d_Z2 = nullptr;
+    void* d_X2 = nullptr;
+    cudaStream_t lane_st[2] = {nullptr, nullptr};
+    cudaEvent_t lane_ev[2] = {nullptr, nullptr};
+    cudaEvent_t fork_ev = nullptr;
     std::vector<void*> allocations;
     // persistent pipelined path: launch configurations by batch size, and a mapped pinned
     // status word [abort, status, item] that a launch writes if a wait gives up

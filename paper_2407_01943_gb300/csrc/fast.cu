@@ -179,13 +179,14 @@ m2_status init_fast_kernels(int smem_optin) {
 }
 
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
-                          cudaStream_t st) {
+                          cudaStream_t st, int lane) {
     const Geometry& g = p->g;
     static const Tw32 tw = packed::make_tw32();
     const Ctx c = packed_ctx(p);
-    float2* dg = reinterpret_cast<float2*>(p->d_g);
-    float2* dZ = reinterpret_cast<float2*>(p->d_Z);
-    float2* dX = reinterpret_cast<float2*>(p->d_X);
+    // workspace of lane 0 (the plan's) or lane 1 (the second half, for overlapped chunks)
+    float2* dg = reinterpret_cast<float2*>(lane ? p->d_g2 : p->d_g);
+    float2* dZ = reinterpret_cast<float2*>(lane ? p->d_Z2 : p->d_Z);
+    float2* dX = reinterpret_cast<float2*>(lane ? p->d_X2 : p->d_X);
 
     mark(p, 0, 0, st);
     {

@@ -331,6 +331,11 @@ void free_plan(m2nufft_plan_s* p) {
         DeviceGuard guard(p->device);
         cudaDeviceSynchronize();
         for (auto& kv : p->pipe_cache) pipe_free(kv.second);
+        for (int L = 0; L < 2; ++L) {
+            if (p->lane_st[L]) cudaStreamDestroy(p->lane_st[L]);
+            if (p->lane_ev[L]) cudaEventDestroy(p->lane_ev[L]);
+        }
+        if (p->fork_ev) cudaEventDestroy(p->fork_ev);
         if (p->pipe_status) cudaFreeHost(p->pipe_status);
         if (p->d_pipe_prof) cudaFree(p->d_pipe_prof);
         for (void* d : p->allocations) cudaFree(d);
