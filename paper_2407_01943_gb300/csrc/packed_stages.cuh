@@ -329,17 +329,15 @@ __host__ __device__ inline size_t cols_group_f2(int rows, int F) { return (size_
 // warps only take part in the barriers), written transposed for the in-band
 // columns k2 <= k2max and k2 >= 1023 - k2max only:
 //   Xt[k2][k1] = sum_{l2} Z[k1][l2] W_1024^{l2 k2}
-// Called by all 32 R threads of the CTA.  smem (float2): 1024 + R * kRowPad.
+// Called by all 32 R threads of the CTA.  smem (float2): R * kRowPad.
 // ---------------------------------------------------------------------------
 template <int R, bool kStream>
 __device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, const float2* __restrict__ Zj,
                                             float2* __restrict__ Xtj, int r0, int nr, float2* smem) {
     constexpr int NT = 32 * R;
-    float2* s_tw = smem;             // [32 c][32 lane]: W_1024^{lane c}
-    float2* s_row = s_tw + kRowLen;  // [R][kRowPad]
+    float2* s_row = smem;  // [R][kRowPad]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < kRowLen; q += NT) s_tw[q] = __ldg(c.tw1024 + (q >> 5) * (q & 31));
     float2* S = s_row + warp * kRowPad;
     const bool active = warp < nr;
     float2 v[32];
@@ -347,14 +345,13 @@ __device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, const 
         const float2* Zr = Zj + (int64_t)(r0 + warp) * kRowLen + lane;
 #pragma unroll
         for (int a = 0; a < 32; ++a) v[a] = ld_inter<kStream>(Zr + 32 * a);
-    }
-    __syncthreads();  // s_tw ready
-    if (active) {
         fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
+        // twiddle W_1024^{lane cc} straight from the (L1-resident) table: lane cc <= 961
+        const float2* twl = c.tw1024;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
             const int cc = brev(q, 5);
-            S[cc * 33 + lane] = cmulf(v[q], s_tw[cc * 32 + lane]);
+            S[cc * 33 + lane] = cmulf(v[q], __ldg(twl + cc * lane));
         }
         __syncwarp();
 #pragma unroll
@@ -387,7 +384,7 @@ __device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, const 
     __syncthreads();  // smem reuse
 }
 
-inline size_t rowfft_smem_bytes(int R) { return sizeof(float2) * ((size_t)kRowLen + (size_t)R * kRowPad); }
+inline size_t rowfft_smem_bytes(int R) { return sizeof(float2) * (size_t)R * kRowPad; }
 
 // ---------------------------------------------------------------------------
 // epilogue for position k = k1 + n1 k2 (k2 <= k2max) and its partner nf - k:
