@@ -2,18 +2,27 @@
  * m2serve.h -- native continuous-batching PSD server over cached M2NuFFT plans.
  *
  * The paper has no counterpart to this interface: it is the serving runtime
- * around the per-signal path of include/m2nufft.h (m2nufft_exec).  Requests
- * (pattern index, host samples, arrival time) are admitted whenever a launch
- * slot is free and the request's device buffers fit that slot's share of the
- * memory budget; admitted requests are grouped by pattern so each group is
- * one m2nufft_exec over B signals; slots run on separate CUDA streams, so a
- * new batch starts while earlier batches are still on the GPU.  A pattern is
- * in at most one slot at a time (a plan's workspace serves one launch at a
- * time).  Latency = completion time (P-hat back in host memory) minus arrival.
+ * around the per-signal path of include/m2nufft.h.  Requests (pattern index,
+ * host samples, arrival time) are admitted whenever a launch slot is free and
+ * the request's device buffers fit that slot's share of the memory budget;
+ * slots run on separate CUDA streams, so a new batch starts while earlier
+ * batches are still on the GPU.  Latency = completion time (P-hat back in host
+ * memory) minus arrival.
+ *
+ * Launches: when every plan is a packed FP32 plan (m2_info.path 2 or 3), a
+ * launch takes up to max_batch queued requests of any patterns and runs them
+ * through one set of stage launches (spread, column DFTs, row FFTs, epilogue
+ * over all its requests, the work maps built per launch and copied with one
+ * transfer, the workspace in the slot's arena): one H2D copy of the samples,
+ * one D2H copy of the P-hats.  Otherwise requests are grouped by pattern, each
+ * group is one m2nufft_exec, and a pattern is in at most one slot at a time (a
+ * plan's workspace serves one launch at a time).  Results do not depend on the
+ * launch a request lands in.
  *
  * Memory: at create, each slot receives a device arena of
- * (mem_budget - sum of plan device bytes) / slots bytes and a pinned host
- * staging arena of the same layout; nothing is allocated while serving.
+ * min((mem_budget - sum of plan device bytes) / slots, max_batch requests of the
+ * largest pattern) bytes and a pinned host staging arena; nothing is allocated
+ * while serving.
  */
 #ifndef M2SERVE_H
 #define M2SERVE_H

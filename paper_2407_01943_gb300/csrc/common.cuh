@@ -108,6 +108,15 @@ m2_status hbatch_run(HBatch* H, cudaStream_t st);
 int hbatch_launches(const HBatch* H);
 void hbatch_free(HBatch* H);
 m2_status init_hbatch_kernels(int smem_optin);
+// Serving with the stage-batched kernels (hbatch.cu): plan contexts on the device, per-launch maps.
+struct HServe;
+m2_status hserve_create(m2nufft_plan_s* const* plans, int nplans, HServe** out);
+void hserve_free(HServe* H);
+size_t hserve_ws_bytes(const HServe* H, int plan);   // workspace of one request of that plan
+size_t hserve_map_bytes(const HServe* H, int plan);  // staged task record and work maps of one request
+m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x, float2* const* J,
+                        float* const* E, float* const* P, float2* ws, char* hstage, char* dstage, size_t stage_cap,
+                        cudaStream_t st);
 // Persistent pipelined kernel of the packed path (pipe.cu).
 struct PipeLaunch;
 void pipe_free(PipeLaunch* L);

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <vector>
@@ -173,6 +174,92 @@ m2_status init_hbatch_kernels(int smem_optin) {
     return M2_OK;
 }
 
+namespace {
+
+// Work maps of a list of tasks (stage order per kernel class) and the workspace they need.
+struct Maps {
+    std::vector<int4> sp[3];
+    std::vector<int4> co[6];
+    size_t smem_cols[6] = {};
+    std::vector<int4> ro;
+    std::vector<int2> ep;
+    int64_t ws_f2 = 0;  // workspace, float2 units
+};
+
+// Append task `task` of context c (geometry g) to the maps; its workspace goes at the end.
+void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
+    auto take = [&](int64_t n) {  // 256-byte aligned sections
+        const int64_t o = m.ws_f2;
+        m.ws_f2 += (n + 31) / 32 * 32;
+        return o;
+    };
+    t.g_off = take((int64_t)c.Kp * c.Lg);
+    t.z_off = take(2 * (int64_t)c.Kp * c.n1 * kRowLen);
+    // spread: kSpreadTiles tiles per CTA
+    const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
+    for (int64_t tile = 0; tile < ntiles; tile += kSpreadTiles)
+        m.sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(kSpreadTiles, ntiles - tile), 0));
+    // column DFTs: one coset per warp where the C = n1 / F cosets allow it (C = 1: four one-warp
+    // groups per CTA, C = 2: two two-warp groups), else one four-warp group sharing the cosets
+    const int C = c.n1 / c.F;
+    const int gw = C == 1 ? 1 : (C == 2 ? 2 : 4);
+    const int lf = packed::ilog2c(c.F);
+    for (int j = 0; j < c.Kp; ++j)
+        for (int col = 0; col < kRowLen; col += 32 * (4 / gw)) m.co[lf].push_back(make_int4(task, j, col, gw));
+    m.smem_cols[lf] = std::max(m.smem_cols[lf], sizeof(float2) * ((size_t)c.n1 + (size_t)(4 / gw) *
+                                                                   packed::cols_group_f2(c.rows, c.F)));
+    // row FFTs: up to 8 rows per CTA
+    for (int j = 0; j < c.Kp; ++j)
+        for (int r0 = 0; r0 < c.n1; r0 += kRowWarps) m.ro.push_back(make_int4(task, j, r0, std::min(kRowWarps, c.n1 - r0)));
+    // epilogue: 128 positions per CTA
+    const int npos = c.n1 * (c.k2max + 1);
+    for (int p0 = 0; p0 < npos; p0 += kEpiThreads) m.ep.push_back(make_int2(task, p0));
+}
+
+// Device work-map pointers and counts of one launch.
+struct MapView {
+    const int4* sp[3] = {};
+    int n_sp[3] = {};
+    const int4* co[6] = {};
+    int n_co[6] = {};
+    size_t smem_cols[6] = {};
+    const int4* ro = nullptr;
+    int n_ro = 0;
+    const int2* ep = nullptr;
+    int n_ep = 0;
+};
+
+m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, const Tw32& tw, float2* ws,
+                      cudaStream_t st) {
+    if (v.n_sp[0]) hb_spread_kernel<2><<<v.n_sp[0], kSpreadTile, 0, st>>>(v.sp[0], tasks, ctxs, ws);
+    if (v.n_sp[1]) hb_spread_kernel<4><<<v.n_sp[1], kSpreadTile, 0, st>>>(v.sp[1], tasks, ctxs, ws);
+    if (v.n_sp[2]) hb_spread_kernel<8><<<v.n_sp[2], kSpreadTile, 0, st>>>(v.sp[2], tasks, ctxs, ws);
+    M2_CUDA_TRY(cudaGetLastError());
+    for (int k = 1; k < 6; ++k) {
+        if (!v.n_co[k]) continue;
+        const size_t sm = v.smem_cols[k];
+        switch (k) {
+            case 1: hb_cols_kernel<2><<<v.n_co[k], kColThreads, sm, st>>>(v.co[k], tasks, ctxs, tw, ws); break;
+            case 2: hb_cols_kernel<4><<<v.n_co[k], kColThreads, sm, st>>>(v.co[k], tasks, ctxs, tw, ws); break;
+            case 3: hb_cols_kernel<8><<<v.n_co[k], kColThreads, sm, st>>>(v.co[k], tasks, ctxs, tw, ws); break;
+            case 4: hb_cols_kernel<16><<<v.n_co[k], kColThreads, sm, st>>>(v.co[k], tasks, ctxs, tw, ws); break;
+            default: hb_cols_kernel<32><<<v.n_co[k], kColThreads, sm, st>>>(v.co[k], tasks, ctxs, tw, ws); break;
+        }
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    if (v.n_ro) {
+        hb_rows_kernel<<<v.n_ro, 32 * kRowWarps, packed::rowfft_smem_bytes(kRowWarps), st>>>(v.ro, tasks, ctxs, tw, ws);
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    if (v.n_ep) {
+        hb_epi_kernel<<<v.n_ep, kEpiThreads, 0, st>>>(v.ep, tasks, ctxs, ws);
+        M2_CUDA_TRY(cudaGetLastError());
+    }
+    return M2_OK;
+}
+
+}  // namespace
+
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
                         void* const* Es, void* const* Ps, HBatch** out) {
     std::unique_ptr<HBatch> H(new HBatch());
@@ -181,11 +268,7 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
     std::vector<Ctx> ctxs;
     std::map<const m2nufft_plan_s*, int> index;
     std::vector<HTask> tasks((size_t)nsig);
-    std::vector<int4> sp[3];
-    std::vector<int4> co[6];
-    std::vector<int4> ro;
-    std::vector<int2> ep;
-    int64_t off = 0;
+    Maps m;
     for (int64_t s = 0; s < nsig; ++s) {
         const m2nufft_plan_s* p = plans[s];
         auto f = index.find(p);
@@ -193,9 +276,6 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
             f = index.emplace(p, (int)ctxs.size()).first;
             ctxs.push_back(packed_ctx(p));
         }
-        const Ctx& c = ctxs[(size_t)f->second];
-        const Geometry& g = p->g;
-        const int task = (int)s;
         HTask& t = tasks[(size_t)s];
         t.x = static_cast<const float*>(xs[s]);
         t.J = Js ? static_cast<float2*>(Js[s]) : nullptr;
@@ -203,34 +283,14 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
         t.P = Ps ? static_cast<float*>(Ps[s]) : nullptr;
         t.ctx = f->second;
         t.pad0 = t.pad1 = t.pad2 = 0;
-        // workspace: 256-byte aligned sections
-        auto take = [&](int64_t n) {
-            const int64_t o = off;
-            off += (n + 31) / 32 * 32;
-            return o;
-        };
-        t.g_off = take((int64_t)c.Kp * c.Lg);
-        t.z_off = take(2 * (int64_t)c.Kp * c.n1 * kRowLen);
-        // spread: one CTA per tile
-        const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
-        for (int64_t tile = 0; tile < g.ntiles; tile += kSpreadTiles)
-            sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(kSpreadTiles, g.ntiles - tile), 0));
-        // column DFTs: one coset per warp where the C = n1 / F cosets allow it (C = 1: four one-warp
-        // groups per CTA, C = 2: two two-warp groups), else one four-warp group sharing the cosets
-        const int C = c.n1 / c.F;
-        const int gw = C == 1 ? 1 : (C == 2 ? 2 : 4);
-        const int lf = packed::ilog2c(c.F);
-        for (int j = 0; j < c.Kp; ++j)
-            for (int col = 0; col < kRowLen; col += 32 * (4 / gw)) co[lf].push_back(make_int4(task, j, col, gw));
-        H->smem_cols[lf] = std::max(H->smem_cols[lf], sizeof(float2) * ((size_t)c.n1 + (size_t)(4 / gw) *
-                                                                          packed::cols_group_f2(c.rows, c.F)));
-        // row FFTs: up to 8 rows per CTA
-        for (int j = 0; j < c.Kp; ++j)
-            for (int r0 = 0; r0 < c.n1; r0 += kRowWarps) ro.push_back(make_int4(task, j, r0, std::min(kRowWarps, c.n1 - r0)));
-        // epilogue: 128 positions per CTA
-        const int npos = c.n1 * (c.k2max + 1);
-        for (int p0 = 0; p0 < npos; p0 += kEpiThreads) ep.push_back(make_int2(task, p0));
+        add_task(m, (int)s, ctxs[(size_t)f->second], p->g.ntiles, t);
     }
+    const int64_t off = m.ws_f2;
+    std::vector<int4>* sp = m.sp;
+    std::vector<int4>* co = m.co;
+    std::vector<int4>& ro = m.ro;
+    std::vector<int2>& ep = m.ep;
+    for (int k = 0; k < 6; ++k) H->smem_cols[k] = m.smem_cols[k];
     H->ws_bytes = (size_t)off * sizeof(float2);
     M2_CUDA_TRY(cudaMalloc(&H->ws, H->ws_bytes));
     H->owned.push_back(H->ws);
@@ -254,31 +314,21 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
 
 // The batch's launches, in stage order, on one stream (captured into a graph by the caller).
 m2_status hbatch_run(HBatch* H, cudaStream_t st) {
-    if (H->n_spread[0]) hb_spread_kernel<2><<<H->n_spread[0], kSpreadTile, 0, st>>>(H->d_spread[0], H->d_tasks, H->d_ctxs, H->ws);
-    if (H->n_spread[1]) hb_spread_kernel<4><<<H->n_spread[1], kSpreadTile, 0, st>>>(H->d_spread[1], H->d_tasks, H->d_ctxs, H->ws);
-    if (H->n_spread[2]) hb_spread_kernel<8><<<H->n_spread[2], kSpreadTile, 0, st>>>(H->d_spread[2], H->d_tasks, H->d_ctxs, H->ws);
-    M2_CUDA_TRY(cudaGetLastError());
-    for (int k = 1; k < 6; ++k) {
-        if (!H->n_cols[k]) continue;
-        const size_t sm = H->smem_cols[k];
-        switch (k) {
-            case 1: hb_cols_kernel<2><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
-            case 2: hb_cols_kernel<4><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
-            case 3: hb_cols_kernel<8><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
-            case 4: hb_cols_kernel<16><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
-            default: hb_cols_kernel<32><<<H->n_cols[k], kColThreads, sm, st>>>(H->d_cols[k], H->d_tasks, H->d_ctxs, H->tw, H->ws); break;
-        }
-        M2_CUDA_TRY(cudaGetLastError());
+    MapView v;
+    for (int k = 0; k < 3; ++k) {
+        v.sp[k] = H->d_spread[k];
+        v.n_sp[k] = H->n_spread[k];
     }
-    if (H->n_rows) {
-        hb_rows_kernel<<<H->n_rows, 32 * kRowWarps, packed::rowfft_smem_bytes(kRowWarps), st>>>(H->d_rows, H->d_tasks, H->d_ctxs, H->tw, H->ws);
-        M2_CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k < 6; ++k) {
+        v.co[k] = H->d_cols[k];
+        v.n_co[k] = H->n_cols[k];
+        v.smem_cols[k] = H->smem_cols[k];
     }
-    if (H->n_epi) {
-        hb_epi_kernel<<<H->n_epi, kEpiThreads, 0, st>>>(H->d_epi, H->d_tasks, H->d_ctxs, H->ws);
-        M2_CUDA_TRY(cudaGetLastError());
-    }
-    return M2_OK;
+    v.ro = H->d_rows;
+    v.n_ro = H->n_rows;
+    v.ep = H->d_epi;
+    v.n_ep = H->n_epi;
+    return launch_maps(v, H->d_tasks, H->d_ctxs, H->tw, H->ws, st);
 }
 
 int hbatch_launches(const HBatch* H) {
@@ -286,6 +336,107 @@ int hbatch_launches(const HBatch* H) {
     for (int k = 0; k < 3; ++k) n += H->n_spread[k] ? 1 : 0;
     for (int k = 0; k < 6; ++k) n += H->n_cols[k] ? 1 : 0;
     return n;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: the same stage kernels over the requests of one launch, whatever
+// their sampling patterns.  The plan contexts stay on the device; each launch
+// builds its task records and work maps on the host into a pinned staging
+// buffer, copies them with one transfer and runs the stage launches.
+// ---------------------------------------------------------------------------
+struct HServe {
+    std::vector<Ctx> ctxs;
+    std::vector<int64_t> ntiles;
+    Ctx* d_ctxs = nullptr;
+    Tw32 tw;
+    ~HServe() {
+        if (d_ctxs) cudaFree(d_ctxs);
+    }
+};
+
+m2_status hserve_create(m2nufft_plan_s* const* plans, int nplans, HServe** out) {
+    std::unique_ptr<HServe> H(new HServe());
+    H->tw = packed::make_tw32();
+    for (int i = 0; i < nplans; ++i) {
+        H->ctxs.push_back(packed_ctx(plans[i]));
+        H->ntiles.push_back(plans[i]->g.ntiles);
+    }
+    M2_CUDA_TRY(cudaMalloc(&H->d_ctxs, sizeof(Ctx) * H->ctxs.size()));
+    M2_CUDA_TRY(cudaMemcpy(H->d_ctxs, H->ctxs.data(), sizeof(Ctx) * H->ctxs.size(), cudaMemcpyHostToDevice));
+    *out = H.release();
+    return M2_OK;
+}
+
+void hserve_free(HServe* H) { delete H; }
+
+size_t hserve_ws_bytes(const HServe* H, int plan) {
+    Maps m;
+    HTask t{};
+    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t);
+    return sizeof(float2) * (size_t)m.ws_f2;
+}
+
+size_t hserve_map_bytes(const HServe* H, int plan) {
+    Maps m;
+    HTask t{};
+    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t);
+    size_t b = sizeof(HTask);
+    for (auto& v : m.sp) b += sizeof(int4) * v.size();
+    for (auto& v : m.co) b += sizeof(int4) * v.size();
+    b += sizeof(int4) * m.ro.size() + sizeof(int2) * m.ep.size();
+    return b + 16 * 12;  // per-section alignment
+}
+
+m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x, float2* const* J,
+                        float* const* E, float* const* P, float2* ws, char* hstage, char* dstage, size_t stage_cap,
+                        cudaStream_t st) {
+    Maps m;
+    std::vector<HTask> tasks((size_t)n);
+    for (int r = 0; r < n; ++r) {
+        HTask& t = tasks[(size_t)r];
+        t.x = x[r];
+        t.J = J ? J[r] : nullptr;
+        t.E = E ? E[r] : nullptr;
+        t.P = P[r];
+        t.ctx = plan[r];
+        t.pad0 = t.pad1 = t.pad2 = 0;
+        add_task(m, r, H->ctxs[plan[r]], H->ntiles[plan[r]], t);
+    }
+    // staging layout: tasks, then the maps, each section 16-byte aligned
+    size_t off = 0;
+    auto put = [&](const void* src, size_t bytes) -> size_t {
+        off = (off + 15) & ~size_t(15);
+        const size_t o = off;
+        if (bytes) std::memcpy(hstage + o, src, bytes);
+        off += bytes;
+        return o;
+    };
+    MapView v;
+    const size_t ot = put(tasks.data(), sizeof(HTask) * tasks.size());
+    size_t osp[3], oco[6];
+    for (int k = 0; k < 3; ++k) osp[k] = put(m.sp[k].data(), sizeof(int4) * m.sp[k].size());
+    for (int k = 0; k < 6; ++k) oco[k] = put(m.co[k].data(), sizeof(int4) * m.co[k].size());
+    const size_t oro = put(m.ro.data(), sizeof(int4) * m.ro.size());
+    const size_t oep = put(m.ep.data(), sizeof(int2) * m.ep.size());
+    if (off > stage_cap) {
+        set_error("internal: serving work maps (%zu bytes) exceed the staging buffer (%zu)", off, stage_cap);
+        return M2_ERR_ARG;
+    }
+    M2_CUDA_TRY(cudaMemcpyAsync(dstage, hstage, off, cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < 3; ++k) {
+        v.sp[k] = reinterpret_cast<const int4*>(dstage + osp[k]);
+        v.n_sp[k] = (int)m.sp[k].size();
+    }
+    for (int k = 0; k < 6; ++k) {
+        v.co[k] = reinterpret_cast<const int4*>(dstage + oco[k]);
+        v.n_co[k] = (int)m.co[k].size();
+        v.smem_cols[k] = m.smem_cols[k];
+    }
+    v.ro = reinterpret_cast<const int4*>(dstage + oro);
+    v.n_ro = (int)m.ro.size();
+    v.ep = reinterpret_cast<const int2*>(dstage + oep);
+    v.n_ep = (int)m.ep.size();
+    return launch_maps(v, reinterpret_cast<const HTask*>(dstage + ot), H->d_ctxs, H->tw, ws, st);
 }
 
 }  // namespace m2

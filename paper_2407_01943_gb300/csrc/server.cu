@@ -1,8 +1,12 @@
 // Native continuous-batching PSD server (include/m2serve.h).
 //
-// Host-side runtime around m2nufft_exec: real-time trace replay, admission
-// into launch slots (CUDA streams) with per-slot device and pinned-host arenas
-// carved at create time, grouping by pattern, and completion by event polling.
+// Host-side runtime: real-time trace replay, admission into launch slots (CUDA
+// streams) with per-slot device and pinned-host arenas carved at create time,
+// and completion by event polling.  When every plan is a packed FP32 plan, a
+// launch runs all its requests, whatever their sampling patterns, through the
+// stage-batched kernels (one set of stage launches over the launch's requests,
+// work maps built per launch, workspace in the slot's arena); otherwise the
+// requests are grouped by pattern and each group is one m2nufft_exec.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -34,6 +38,8 @@ struct Slot {
     size_t host_cap = 0;
     bool busy = false;
     std::vector<Group> groups;
+    // cross-pattern launches: the requests and the pinned offsets of their P-hat
+    std::vector<std::pair<int64_t, size_t>> cross;
 };
 
 struct PlanGeo {
@@ -51,6 +57,8 @@ struct m2serve_s {
     int max_batch = 1;
     std::vector<Slot> slots;
     int64_t last_launches = 0, last_requests = 0;
+    m2::HServe* hs = nullptr;                // cross-pattern launches (all plans packed), else NULL
+    std::vector<size_t> ws_bytes, map_bytes;  // per request of each plan (cross-pattern launches)
 };
 
 namespace {
@@ -77,11 +85,17 @@ size_t host_bytes(const m2serve_s* s, int pat, int64_t B) {
     const PlanGeo& g = s->geo[pat];
     return align_up(sizeof(float) * B * g.N) + align_up(sizeof(float) * B * g.I);
 }
+// one request in a cross-pattern launch: its buffers, workspace and staged work maps
+size_t cross_dev_bytes(const m2serve_s* s, int pat) {
+    return dev_bytes(s, pat, 1) + align_up(s->ws_bytes[pat]) + align_up(s->map_bytes[pat]);
+}
+size_t cross_host_bytes(const m2serve_s* s, int pat) { return host_bytes(s, pat, 1) + align_up(s->map_bytes[pat]); }
 
 void destroy_server(m2serve_s* s) {
     if (!s) return;
     {
         DevGuard guard(s->device);
+        if (s->hs) m2::hserve_free(s->hs);
         for (Slot& sl : s->slots) {
             if (sl.stream) cudaStreamSynchronize(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
@@ -163,9 +177,72 @@ struct Run {
         return M2_OK;
     }
 
+    // all requests of the launch through the stage-batched kernels, whatever their patterns
+    m2_status launch_cross(int si, const std::vector<int64_t>& reqs) {
+        Slot& sl = s->slots[si];
+        const int n = (int)reqs.size();
+        sl.cross.clear();
+        std::vector<int> plan(n);
+        std::vector<const float*> xd(n);
+        std::vector<float2*> Jd(n, nullptr);
+        std::vector<float*> Ed(n, nullptr), Pd(n);
+        // device arena: x | P | J | E | workspace | staged maps;  pinned arena: x | P | staged maps
+        size_t dx = 0, hx = 0, xb = 0, pb = 0, jb = 0, eb = 0, wb = 0, mb = 0;
+        for (int64_t r : reqs) {
+            const PlanGeo& g = s->geo[pattern[r]];
+            xb += align_up(sizeof(float) * g.N);
+            pb += align_up(sizeof(float) * g.I);
+            if (s->outputs & M2_OUT_J) jb += align_up(sizeof(float2) * g.K * g.I);
+            if (s->outputs & M2_OUT_E) eb += align_up(sizeof(float) * g.K * g.I);
+            wb += align_up(s->ws_bytes[pattern[r]]);
+            mb += align_up(s->map_bytes[pattern[r]]);
+        }
+        const size_t dP0 = xb, dJ0 = dP0 + pb, dE0 = dJ0 + jb, dW0 = dE0 + eb, dM0 = dW0 + wb;
+        const size_t hP0 = xb, hM0 = hP0 + pb;
+        size_t oP = 0, oJ = 0, oE = 0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t r = reqs[i];
+            const PlanGeo& g = s->geo[pattern[r]];
+            plan[i] = pattern[r];
+            std::memcpy(sl.host + hx, x[r], sizeof(float) * g.N);
+            xd[i] = reinterpret_cast<const float*>(sl.dev + dx);
+            dx += align_up(sizeof(float) * g.N);
+            hx += align_up(sizeof(float) * g.N);
+            Pd[i] = reinterpret_cast<float*>(sl.dev + dP0 + oP);
+            sl.cross.emplace_back(r, hP0 + oP);
+            oP += align_up(sizeof(float) * g.I);
+            if (s->outputs & M2_OUT_J) {
+                Jd[i] = reinterpret_cast<float2*>(sl.dev + dJ0 + oJ);
+                oJ += align_up(sizeof(float2) * g.K * g.I);
+            }
+            if (s->outputs & M2_OUT_E) {
+                Ed[i] = reinterpret_cast<float*>(sl.dev + dE0 + oE);
+                oE += align_up(sizeof(float) * g.K * g.I);
+            }
+        }
+        M2_CUDA_TRY(cudaMemcpyAsync(sl.dev, sl.host, xb, cudaMemcpyHostToDevice, sl.stream));
+        M2_TRY(m2::hserve_launch(s->hs, n, plan.data(), xd.data(), (s->outputs & M2_OUT_J) ? Jd.data() : nullptr,
+                                 (s->outputs & M2_OUT_E) ? Ed.data() : nullptr, Pd.data(),
+                                 reinterpret_cast<float2*>(sl.dev + dW0), sl.host + hM0, sl.dev + dM0, mb,
+                                 sl.stream));
+        M2_CUDA_TRY(cudaMemcpyAsync(sl.host + hP0, sl.dev + dP0, pb, cudaMemcpyDeviceToHost, sl.stream));
+        M2_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
+        sl.busy = true;
+        ++launches;
+        return M2_OK;
+    }
+
     void retire(int si) {
         Slot& sl = s->slots[si];
         const double t = now();
+        for (const auto& q : sl.cross) {
+            const int64_t r = q.first;
+            if (p_out && p_out[r])
+                std::memcpy(p_out[r], sl.host + q.second, sizeof(float) * s->geo[pattern[r]].I);
+            latency[r] = t - arrival[r];
+            ++completed;
+        }
+        sl.cross.clear();
         for (const Group& g : sl.groups) {
             const PlanGeo& geo = s->geo[g.pattern];
             const float* hP = reinterpret_cast<const float*>(sl.host + g.hP);
@@ -228,12 +305,27 @@ extern "C" m2_status m2serve_create(const m2nufft_plan_t* plans, int nplans, siz
             return M2_ERR_ARG;
         }
     }
+    DevGuard guard0(s->device);
+    bool all_packed = true;
+    for (int i = 0; i < nplans; ++i) all_packed = all_packed && plans[i]->g.path >= 2;
+    if (all_packed) {
+        m2_status st = m2::hserve_create(const_cast<m2nufft_plan_s* const*>(plans), nplans, &s->hs);
+        if (st != M2_OK) {
+            delete s;
+            return st;
+        }
+        for (int i = 0; i < nplans; ++i) {
+            s->ws_bytes.push_back(m2::hserve_ws_bytes(s->hs, i));
+            s->map_bytes.push_back(m2::hserve_map_bytes(s->hs, i));
+        }
+    }
     size_t max_req_dev = 0, max_req_host = 0;
     for (int i = 0; i < nplans; ++i) {
-        max_req_dev = std::max(max_req_dev, dev_bytes(s, i, 1));
-        max_req_host = std::max(max_req_host, host_bytes(s, i, 1));
+        max_req_dev = std::max(max_req_dev, s->hs ? cross_dev_bytes(s, i) : dev_bytes(s, i, 1));
+        max_req_host = std::max(max_req_host, s->hs ? cross_host_bytes(s, i) : host_bytes(s, i, 1));
     }
     if (mem_budget <= plan_bytes || (mem_budget - plan_bytes) / slots < max_req_dev) {
+        if (s->hs) m2::hserve_free(s->hs);
         delete s;
         m2::set_error("m2serve_create: budget %zu does not cover the plans (%zu bytes) plus one request of the "
                       "largest pattern (%zu bytes) per slot",
@@ -298,10 +390,23 @@ extern "C" m2_status m2serve_run_trace(m2serve_t s, int64_t nreq, const int32_t*
             size_t used_dev = 0, used_host = 0;
             // patterns of this launch so far, with their request counts
             std::vector<std::pair<int, int64_t>> pats;
+            const bool cross = s->hs != nullptr && !plain;
             while (!queue.empty() && (int)take.size() < batch) {
                 const int64_t r = queue.front();
                 queue.pop_front();
                 const int pat = pattern[r];
+                if (cross) {  // any pattern; the slot's arena bounds the launch
+                    const size_t dnew = used_dev + cross_dev_bytes(s, pat);
+                    const size_t hnew = used_host + cross_host_bytes(s, pat);
+                    if (dnew > s->slots[free_slot].dev_cap || hnew > s->slots[free_slot].host_cap) {
+                        keep.push_back(r);
+                        break;
+                    }
+                    used_dev = dnew;
+                    used_host = hnew;
+                    take.push_back(r);
+                    continue;
+                }
                 if (run.pattern_slot[pat] >= 0) {  // pattern busy in another slot
                     keep.push_back(r);
                     continue;
@@ -325,7 +430,8 @@ extern "C" m2_status m2serve_run_trace(m2serve_t s, int64_t nreq, const int32_t*
                 keep.pop_back();
             }
             if (!take.empty()) {
-                M2_TRY(run.launch(free_slot, take));
+                if (cross) M2_TRY(run.launch_cross(free_slot, take));
+                else M2_TRY(run.launch(free_slot, take));
                 continue;
             }
         }

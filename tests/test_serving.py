@@ -14,18 +14,21 @@ from paper_2407_01943_gb300 import serve  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def _patterns(n=6):
+def _patterns(n=6, path=0):
     pats = synth.serving_patterns(n, seed=5, n_min=300, n_max=1500)
     plans = {}
     for i, pt in enumerate(pats):
         plans[i] = pkg.Plan(pt["t"], 1.0, pt["f_w"], 4, pt["f_lo"], pt["df"], pt["I"], precision=32,
-                            tapers=synth.taper_like(4, pt["t"].shape[0], i), max_batch=8)
+                            tapers=synth.taper_like(4, pt["t"].shape[0], i), max_batch=8, path=path)
     return pats, plans
 
 
-def test_server_results_equal_alone():
+@pytest.mark.parametrize("path", [0, 1], ids=["cross_pattern", "per_pattern"])
+def test_server_results_equal_alone(path):
+    """path 0: packed plans, so each launch runs all its requests (any patterns) through the
+    stage-batched kernels; path 1: generic plans, grouped by pattern into m2nufft_exec calls."""
     torch.cuda.set_device(0)
-    pats, plans = _patterns()
+    pats, plans = _patterns(path=path)
     arr = synth.poisson_arrivals(20000.0, 80, seed=3)   # bursty: batches of several requests form
     rng = np.random.default_rng(4)
     reqs = []
@@ -73,4 +76,8 @@ def test_server_respects_memory_budget():
 
 
 def srv_bytes(plans):
-    return max(p.N * 4 + p.I * 4 + p.K * p.I * 12 for p in plans.values())
+    """Upper bound of one request's device bytes: samples, outputs, and for the cross-pattern
+    launches of packed plans its workspace (spread grids, column and row transforms) and work maps."""
+    return max(p.N * 4 + p.I * 4 + p.K * p.I * 12
+               + ((p.K + 1) // 2) * (p.info["rows"] * 1024 + 2 * p.info["nf"]) * 8 + (1 << 20)
+               for p in plans.values())
