@@ -109,6 +109,14 @@ typedef struct {
                            from t_1 to t_N, not-a-knot cubic spline to t, scaled to
                            w^T R(B) w = 2 f_w; O(N) host work plus an O(N^2) FP64 pair sum on
                            the GPU; eigenvalues = the concentrations w^T R(A0) w / w^T R(B) w) */
+    double sigma;       /* minimum oversampling nf / I: 0 = automatic (1.5 on the packed path with
+                           the width ceil(1.25 log10(1/tol)) + 1; 2 on the generic path); at 2 or
+                           more the width is ceil(log10(1/tol)) + 1; accepted range [1.5, 8] */
+    int tune;           /* 1 = autotune at plan time (m2nufft_plan / _with_tapers, packed FP32 plans):
+                           candidate configurations -- sigma 1.5 or 2, signals per chunk (the
+                           default or half of it), the four-kernel or the persistent path -- are
+                           built from the same tapers and timed on a synthetic batch of two chunks
+                           on the device; the fastest is kept (m2nufft_get_tuning reports them) */
 } m2_opts;
 
 /* Geometry of a plan, for callers that size buffers or compute rooflines. */
@@ -259,6 +267,12 @@ m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs,
  * 0 = one launch per stage (default), 1 = one persistent pipelined kernel.
  * Returns the previous mode, or -1 for an invalid mode. */
 int m2nufft_set_batch_mode(int mode);
+
+/* Autotuning report of a plan made with m2_opts.tune = 1: *n candidate configurations (0 for
+ * an untuned plan), their options (host [*n] or NULL; path 2/3, sigma, max_batch as tried) and the
+ * measured ms per exec of a synthetic batch of two default chunks (host [*n] or NULL; 1e300 for
+ * a candidate the plan does not admit).  Call with NULL arrays first to get *n (at most 8). */
+m2_status m2nufft_get_tuning(m2nufft_plan_t p, int* n, m2_opts* opts, double* ms);
 
 /* Copy the plan's tapers (host [K][N] FP64, order of t) and eigenvalues
  * (host [K], descending; NaN when the plan was made from caller tapers

@@ -39,7 +39,7 @@ class m2_subband(ctypes.Structure):
 class m2_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("mem_budget", ctypes.c_size_t),
                 ("device", ctypes.c_int), ("max_batch", ctypes.c_int), ("path", ctypes.c_int),
-                ("tapers", ctypes.c_int)]
+                ("tapers", ctypes.c_int), ("sigma", ctypes.c_double), ("tune", ctypes.c_int)]
 
 
 class m2_info(ctypes.Structure):
@@ -65,6 +65,7 @@ EXPORTS = [
     ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
+    ("m2nufft_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), _VP, _DP]),
     ("m2nufft_get_tapers", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_tapers_complex", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_plan_subband", ctypes.c_int, [_DP, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -156,9 +157,11 @@ class Plan:
     def __init__(self, t, fs: float, f_w: float, K: int, f_lo: float, df: float, I: int,
                  precision: int = 32, tol: float = 0.0, mem_budget: int = 0, device: int = -1,
                  max_batch: int = 0, tapers=None, lam=None, path: int = 0, taper_design: str = "gep",
-                 subband=None):
+                 subband=None, sigma: float = 0.0, tune: bool = False):
         """subband = (f_c0, f_min, f_max) makes a sub-band plan (m2nufft_plan_subband): band centres
-        f_lo + i df are absolute, tapers (if given) complex [K, N]."""
+        f_lo + i df are absolute, tapers (if given) complex [K, N].  sigma > 0 asks for an
+        oversampling factor of at least sigma; tune = True times the packed configurations at plan
+        time and keeps the fastest (report: tuning())."""
         L = load()
         self._t = np.ascontiguousarray(t, dtype=np.float64)
         self.N = int(self._t.shape[0])
@@ -168,7 +171,8 @@ class Plan:
         self.fs, self.f_w, self.f_lo, self.df = float(fs), float(f_w), float(f_lo), float(df)
         fg = m2_fgrid(self.f_lo, self.df, self.I)
         design = {"gep": 0, "spline": 1}[taper_design]
-        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path), design)
+        op = m2_opts(self.precision, float(tol), int(mem_budget), int(device), int(max_batch), int(path), design,
+                     float(sigma), 1 if tune else 0)
         h = _VP()
         self.subband = subband
         if subband is not None:
@@ -300,6 +304,19 @@ class Plan:
         _check(load().m2nufft_get_timing(self._h, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
                "m2nufft_get_timing")
         return ms, n
+
+    def tuning(self):
+        """Autotuning report: [(path, sigma, max_batch, ms per exec)] for the candidates tried."""
+        L = load()
+        n = ctypes.c_int(0)
+        _check(L.m2nufft_get_tuning(self._h, ctypes.byref(n), None, None), "m2nufft_get_tuning")
+        if n.value == 0:
+            return []
+        ops = (m2_opts * n.value)()
+        ms = np.zeros(n.value)
+        _check(L.m2nufft_get_tuning(self._h, ctypes.byref(n), ctypes.cast(ops, _VP), _dptr(ms)),
+               "m2nufft_get_tuning")
+        return [(int(o.path), float(o.sigma), int(o.max_batch), float(m)) for o, m in zip(ops, ms)]
 
     def true_suboptimality(self):
         """(E [I], per-band eigenvalues [I, K]) from per-band GEPs (small N only)."""

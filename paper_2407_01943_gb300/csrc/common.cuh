@@ -191,6 +191,9 @@ struct m2nufft_plan_s {
     // status word [abort, status, item] that a launch writes if a wait gives up
     std::map<int64_t, m2::PipeLaunch*> pipe_cache;
     int* pipe_status = nullptr;
+    // autotuning at plan time: the candidate configurations and their measured ms per exec
+    std::vector<m2_opts> tune_opts;
+    std::vector<double> tune_ms;
     unsigned long long* d_pipe_prof = nullptr;  // per-stage busy/wait accounting while timing is enabled
 
     // per-kernel timing (instrumentation): event pairs recorded by exec

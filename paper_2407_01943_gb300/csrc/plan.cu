@@ -878,13 +878,21 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const double span_t = ts.back() - ts.front();
     bool packed_ok = false;
     int64_t nf_packed = 0;
-    const int w_packed = std::min(16, std::max(2, (int)std::ceil(1.25 * std::log10(1.0 / p->tol)) + 1));
+    if (!(opts.sigma == 0.0 || (opts.sigma >= 1.5 && opts.sigma <= 8.0))) {
+        set_error("opts.sigma must be 0 (automatic) or in [1.5, 8]");
+        return bail(M2_ERR_ARG);
+    }
+    int w_packed = std::min(16, std::max(2, (int)std::ceil(1.25 * std::log10(1.0 / p->tol)) + 1));
     if (opts.precision == 32 && g.real_taper && opts.path != 1) {
-        const double target = std::max(1.5 * (double)g.I, 2048.0);
+        // nf >= sigma I with sigma = 1.5 unless asked for more; at sigma >= 2 the kernel needs the
+        // narrower width of the generic rule
+        const double target = std::max((opts.sigma > 0 ? opts.sigma : 1.5) * (double)g.I, 2048.0);
         int64_t a2 = 2048, a3 = 3 * 2048;  // nf = 1024 * n1 with n1 even
         while ((double)a2 < target) a2 <<= 1;
         while ((double)a3 < target) a3 <<= 1;
         nf_packed = std::min(a2, a3);
+        if ((double)nf_packed >= 2.0 * (double)g.I)
+            w_packed = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
         const double span = span_t * (double)nf_packed * g.df;
         const bool wrap_p = span + w_packed + 2.0 >= (double)nf_packed;
         const int64_t rows_p = wrap_p ? nf_packed / 1024 : (int64_t)std::ceil((span + w_packed + 2.0) / 1024.0);
@@ -903,7 +911,7 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         const double sigma = (double)g.nf / (double)g.I;
         g.beta = 0.97 * kPi * (1.0 - 0.5 / sigma) * g.width;
     } else {
-        g.nf = std::max<int64_t>(64, next_pow2(2 * g.I));
+        g.nf = std::max<int64_t>(64, next_pow2((int64_t)std::ceil(std::max(2.0, opts.sigma) * (double)g.I)));
         g.width = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
         g.beta = 2.30 * g.width;
     }
@@ -1218,6 +1226,125 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     return M2_OK;
 }
 
+// Time `reps` execs of B synthetic signals on plan p (ms per exec, the fastest repetition).
+m2_status time_exec(m2nufft_plan_t p, int64_t B, int reps, double* ms) {
+    const Geometry& g = p->g;
+    const size_t nx = (size_t)B * g.N, nj = (size_t)B * g.K * g.I, np = (size_t)B * g.I;
+    float *x = nullptr, *E = nullptr, *P = nullptr;
+    float2* J = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    m2_status rs = M2_OK;
+    cudaError_t e = cudaMalloc(&x, sizeof(float) * nx);
+    if (e == cudaSuccess) e = cudaMalloc(&J, sizeof(float2) * nj);
+    if (e == cudaSuccess) e = cudaMalloc(&E, sizeof(float) * nj);
+    if (e == cudaSuccess) e = cudaMalloc(&P, sizeof(float) * np);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        std::vector<float> hx(nx);
+        uint64_t z = 0x9e3779b97f4a7c15ull;  // any signal does: the work does not depend on x
+        for (size_t i = 0; i < nx; ++i) {
+            z ^= z << 13;
+            z ^= z >> 7;
+            z ^= z << 17;
+            hx[i] = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        }
+        e = cudaMemcpy(x, hx.data(), sizeof(float) * nx, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        set_error("autotune: %s", cudaGetErrorString(e));
+        rs = e == cudaErrorMemoryAllocation ? M2_ERR_NOMEM : M2_ERR_CUDA;
+    }
+    double best = 1e300;
+    for (int r = -2; r < reps && rs == M2_OK; ++r) {  // two untimed warm-up execs
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) rs = m2nufft_exec(p, x, B, J, E, P, nullptr, nullptr, st);
+        if (rs == M2_OK && (e = cudaEventRecord(e1, st)) == cudaSuccess) e = cudaEventSynchronize(e1);
+        float tm = 0.f;
+        if (rs == M2_OK && e == cudaSuccess) e = cudaEventElapsedTime(&tm, e0, e1);
+        if (rs == M2_OK && e != cudaSuccess) {
+            set_error("autotune: %s", cudaGetErrorString(e));
+            rs = M2_ERR_CUDA;
+        }
+        if (r >= 0) best = std::min(best, (double)tm);
+    }
+    if (st) cudaStreamSynchronize(st);
+    cudaFree(x);
+    cudaFree(J);
+    cudaFree(E);
+    cudaFree(P);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    *ms = best;
+    return rs;
+}
+
+// Autotuning (m2_opts.tune = 1): the default plan, then candidates built from its tapers --
+// sigma 2, half the chunk, the persistent path -- each timed on a synthetic batch of two default
+// chunks; the fastest configuration is rebuilt with the plan's eigenvalues (for the leakage
+// estimate) and returned.  Plans that take the generic path are returned untuned.
+m2_status tuned_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
+                     const double* w_given, const double* lam_given, const m2_opts* opts_in, m2nufft_plan_t* out) {
+    m2_opts base = *opts_in;
+    base.tune = 0;
+    m2nufft_plan_t p0 = nullptr;
+    M2_TRY(build_plan(t, N, fs, f_w, K, fc, w_given, lam_given, &base, &p0));
+    if (p0->g.path < 2) {
+        *out = p0;
+        return M2_OK;
+    }
+    DeviceGuard guard(p0->device);
+    const std::vector<double> w = p0->w;
+    const std::vector<double> lam = p0->lambda;
+    const bool have_lam = p0->have_lambda != 0;
+    const int64_t B = std::min<int64_t>(2 * p0->g.chunk, 64);
+    std::vector<m2_opts> cand;
+    m2_opts c = base;
+    c.path = 2;
+    cand.push_back(c);  // the default configuration (p0)
+    c.sigma = 2.0;
+    cand.push_back(c);
+    c = base;
+    c.path = 2;
+    c.max_batch = std::max(1, p0->g.chunk / 2);
+    cand.push_back(c);
+    c = base;
+    c.path = 3;
+    cand.push_back(c);
+    std::vector<double> ms(cand.size(), 1e300);
+    m2_status st = time_exec(p0, B, 3, &ms[0]);
+    for (size_t i = 1; i < cand.size() && st == M2_OK; ++i) {
+        m2nufft_plan_t pc = nullptr;
+        m2_status s2 = build_plan(t, N, fs, f_w, K, fc, w.data(), nullptr, &cand[i], &pc);
+        if (s2 != M2_OK) {  // a candidate the pattern does not admit (e.g. sigma 2 beyond the packed limits)
+            clear_error();
+            continue;
+        }
+        st = time_exec(pc, B, 3, &ms[i]);
+        free_plan(pc);
+    }
+    if (st != M2_OK) {
+        free_plan(p0);
+        return st;
+    }
+    size_t best = 0;
+    for (size_t i = 1; i < cand.size(); ++i)
+        if (ms[i] < ms[best]) best = i;
+    m2nufft_plan_t pf = p0;
+    if (best != 0) {
+        free_plan(p0);
+        st = build_plan(t, N, fs, f_w, K, fc, w.data(), have_lam ? lam.data() : nullptr, &cand[best], &pf);
+        if (st != M2_OK) return st;
+    }
+    pf->tune_opts = cand;
+    pf->tune_ms = ms;
+    *out = pf;
+    return M2_OK;
+}
+
 }  // namespace
 }  // namespace m2
 
@@ -1227,7 +1354,22 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
 extern "C" m2_status m2nufft_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
                                   const m2_opts* opts, m2nufft_plan_t* out) {
     m2::clear_error();
+    if (opts && opts->tune) return m2::tuned_plan(t, N, fs, f_w, K, fc, nullptr, nullptr, opts, out);
     return m2::build_plan(t, N, fs, f_w, K, fc, nullptr, nullptr, opts, out);
+}
+
+extern "C" m2_status m2nufft_get_tuning(m2nufft_plan_t p, int* n, m2_opts* opts, double* ms) {
+    m2::clear_error();
+    if (!p || !n) {
+        m2::set_error("plan or n is NULL");
+        return M2_ERR_ARG;
+    }
+    *n = (int)p->tune_ms.size();
+    for (size_t i = 0; i < p->tune_ms.size(); ++i) {
+        if (opts) opts[i] = p->tune_opts[i];
+        if (ms) ms[i] = p->tune_ms[i];
+    }
+    return M2_OK;
 }
 
 extern "C" m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double f_w, int K,
@@ -1238,6 +1380,7 @@ extern "C" m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double
         m2::set_error("w is NULL");
         return M2_ERR_ARG;
     }
+    if (opts && opts->tune) return m2::tuned_plan(t, N, fs, f_w, K, fc, w, lambda, opts, out);
     return m2::build_plan(t, N, fs, f_w, K, fc, w, lambda, opts, out);
 }
 

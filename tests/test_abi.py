@@ -46,7 +46,8 @@ def test_version_string_without_gpu():
 def test_struct_layouts_match_header():
     # m2_fgrid: 2 doubles + int64; m2_opts: int, double, size_t, int, int, int (natural alignment)
     assert ctypes.sizeof(binding.m2_fgrid) == 24
-    assert ctypes.sizeof(binding.m2_opts) == 40
+    assert ctypes.sizeof(binding.m2_opts) == 56
+    assert binding.m2_opts.sigma.offset == 40 and binding.m2_opts.tune.offset == 48
     assert binding.m2_opts.path.offset == 32 and binding.m2_opts.tapers.offset == 36
     assert binding.m2_opts.tol.offset == 8 and binding.m2_opts.mem_budget.offset == 16
 

@@ -766,3 +766,72 @@ def test_true_suboptimality_matches_oracle(dev, kind):
         lam_hat0 = lam0[0] * 2 * fw / oleak.leakage_denominator(t, w, 1.0, freqs)[0]
         np.testing.assert_allclose(np.abs(lam0[0] - lam_hat0), L[0], atol=1e-9)
         assert np.all(lb[:, 0] >= lam_hat0 - 1e-10)
+
+
+# ---------------------------------------------------------------------------
+# oversampling option and plan-time autotuning
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,path,sigma", [(32, 2, 2.0), (32, 3, 2.0), (32, 2, 3.0), (64, 1, 3.0)])
+def test_sigma_option_parity(dev, prec, path, sigma):
+    """A requested oversampling factor sigma: nf >= sigma I, the packed path takes the narrower
+    width of the sigma >= 2 rule, and the result still meets the parity bar."""
+    wl = synth.workload("jitter16k", batch=2)
+    w = seeded_tapers(wl.K, wl.N, 5)
+    args = (wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I)
+    base = pkg.Plan(*args, precision=prec, tapers=w, path=path)
+    plan = pkg.Plan(*args, precision=prec, tapers=w, path=path, sigma=sigma)
+    assert plan.info["path"] == path
+    assert plan.info["nf"] >= sigma * wl.I
+    if path >= 2:
+        assert plan.info["width"] < base.info["width"]
+    out = run_plan(plan, wl.x, dev)
+    idx = sample_bands(wl.I, 256, 2)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[prec]
+    assert rel_l2(out["P"][:, idx], Pr) <= TOL[prec]
+
+
+def test_sigma_option_rejects_out_of_range(dev):
+    wl = synth.workload("jitter16k")
+    w = seeded_tapers(wl.K, wl.N, 5)
+    for s in (1.2, 9.0, -1.0):
+        with pytest.raises(pkg.M2Error):
+            pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, sigma=s)
+
+
+def test_autotuned_plan(dev):
+    """tune = True: the report lists the four packed configurations (default, sigma 2, half chunk,
+    persistent), the plan kept is the fastest of them, its output meets the parity bar, and the
+    eigenvalues handed in survive the rebuild (the leakage estimate is the untuned plan's)."""
+    wl = synth.workload("jitter16k", batch=3)
+    w = seeded_tapers(wl.K, wl.N, 8)
+    lam = np.linspace(0.999, 0.95, wl.K)
+    args = (wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I)
+    ref = pkg.Plan(*args, precision=32, tapers=w, lam=lam)
+    plan = pkg.Plan(*args, precision=32, tapers=w, lam=lam, tune=True)
+    rep = plan.tuning()
+    assert [r[0] for r in rep] == [2, 2, 2, 3]
+    assert rep[1][1] == 2.0 and rep[2][2] == ref.info["chunk"] // 2
+    ms = [r[3] for r in rep]
+    assert all(0 < m < 1e3 for m in ms)
+    best = int(np.argmin(ms))
+    assert plan.info["path"] == rep[best][0]
+    if best == 1:
+        assert plan.info["nf"] >= 2 * wl.I
+    if best == 2:
+        assert plan.info["chunk"] == rep[2][2]
+    assert ref.tuning() == []
+    out = run_plan(plan, wl.x, dev)
+    idx = sample_bands(wl.I, 256, 3)
+    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
+    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+    for a, b in zip(plan.leakage(), ref.leakage()):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
+
+
+def test_autotune_leaves_generic_plans_untuned(dev):
+    wl = synth.workload("jitter16k")
+    w = seeded_tapers(wl.K, wl.N, 8)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=64, tapers=w, tune=True)
+    assert plan.info["path"] == 1 and plan.tuning() == []
