@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--chunk", type=int, default=0, help="signals per internal chunk (0 = the plan's choice)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="exec path: 0 automatic, 1 generic, 2 packed four-kernel, 3 packed persistent kernel")
+    ap.add_argument("--sigma", type=float, default=0.0, help="oversampling factor (0 = the plan's choice)")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the plan (oversampling, chunk, path) before the timed steps")
     ap.add_argument("--outputs", default="JEPL",
                     help="outputs written each step: any of J (eigencoefficients), E (eigenspectra), P (P-hat), "
                          "L (leakage estimates L-hat, E-hat), F (Thomson F-statistic)")
@@ -577,10 +580,11 @@ def run_ours(args):
         # taper-shaped rows and placeholder eigenvalues: the exec kernels and their shapes are the same
         plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local,
                         tapers=synth.taper_like(wl.K, wl.N, 0), lam=np.linspace(0.999, 0.99, wl.K),
-                        max_batch=args.chunk, path=args.path)
+                        max_batch=args.chunk, path=args.path, sigma=args.sigma, tune=args.tune)
     else:
         plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=args.precision, device=local,
-                        max_batch=args.chunk, path=args.path, taper_design=args.taper_design)
+                        max_batch=args.chunk, path=args.path, taper_design=args.taper_design, sigma=args.sigma,
+                        tune=args.tune)
     t_plan = time.perf_counter() - t_plan
     info = plan.info
 
@@ -755,6 +759,8 @@ def run_ours(args):
                        "signals_per_gpu_per_step": B, "N": wl.N, "K": wl.K, "I": wl.I, "nf": info["nf"],
                        "outputs": args.outputs,
                        "kernel_width": info["width"], "chunk": info["chunk"], "exec_path": info["path"],
+                       "autotune": ([{"path": r[0], "sigma": r[1], "max_batch": r[2], "ms": r[3]}
+                                     for r in plan.tuning()] if args.tune else None),
                        "kernel_timing": ("separate instrumented pass (chunks one after the other); the timed "
                                          "steps overlap consecutive chunks on two streams"
                                          if separate_kernel_pass else "instrumented timed steps"),

@@ -97,7 +97,8 @@ typedef struct {
     size_t mem_budget;  /* maximum bytes of device memory the plan may hold
                            (including GEP scratch); 0 = unlimited */
     int device;         /* CUDA device ordinal; < 0 = the caller's current device */
-    int max_batch;      /* signals processed per internal chunk; <= 0 = automatic */
+    int max_batch;      /* signals per internal chunk; <= 0 = automatic.  Packed paths: the chunk
+                           (at most 64); generic path: an upper bound on the automatic chunk */
     int path;           /* exec kernels: 0 = automatic (2 where the plan qualifies, else 1),
                            1 = generic (any precision/grid),
                            2 = packed FP32 path as four kernels per chunk of signals,
@@ -113,10 +114,9 @@ typedef struct {
                            the width ceil(1.25 log10(1/tol)) + 1; 2 on the generic path); at 2 or
                            more the width is ceil(log10(1/tol)) + 1; accepted range [1.5, 8] */
     int tune;           /* 1 = autotune at plan time (m2nufft_plan / _with_tapers, packed FP32 plans):
-                           candidate configurations -- sigma 1.5 or 2, signals per chunk (the
-                           default or half of it), the four-kernel or the persistent path -- are
-                           built from the same tapers and timed on a synthetic batch of two chunks
-                           on the device; the fastest is kept (m2nufft_get_tuning reports them) */
+                           candidate configurations -- sigma 1.5 or 2, 4, 8 or 16 signals per
+                           chunk, the four-kernel or the persistent path -- are built from the
+                           same tapers and timed on a synthetic batch of 32 signals on the device; the fastest is kept (m2nufft_get_tuning reports them) */
 } m2_opts;
 
 /* Geometry of a plan, for callers that size buffers or compute rooflines. */
@@ -270,7 +270,7 @@ int m2nufft_set_batch_mode(int mode);
 
 /* Autotuning report of a plan made with m2_opts.tune = 1: *n candidate configurations (0 for
  * an untuned plan), their options (host [*n] or NULL; path 2/3, sigma, max_batch as tried) and the
- * measured ms per exec of a synthetic batch of two default chunks (host [*n] or NULL; 1e300 for
+ * measured ms per exec of a synthetic batch of 32 signals (host [*n] or NULL; 1e300 for
  * a candidate the plan does not admit).  Call with NULL arrays first to get *n (at most 8). */
 m2_status m2nufft_get_tuning(m2nufft_plan_t p, int* n, m2_opts* opts, double* ms);
 

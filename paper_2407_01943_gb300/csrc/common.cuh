@@ -167,7 +167,7 @@ struct m2nufft_plan_s {
     void* d_twa = nullptr;         // [nf >> twb_bits] C: exp(-i 2 pi (q << twb_bits) / nf)
     void* d_twb = nullptr;         // [1 << twb_bits]  C: exp(-i 2 pi q / nf)
     void* d_twn1 = nullptr;        // packed path: [n1] C, exp(-i 2 pi q / n1) full circle
-    void* d_tw1024 = nullptr;      // packed path: [1024] C, exp(-i 2 pi q / 1024) full circle
+    void* d_tw1024 = nullptr;      // packed path: [32][32] C, [cc][l] = exp(-i 2 pi cc l / 1024)
     void* d_colT = nullptr;        // packed path: [F][1024] C, exp(-i 2 pi l2 C q / nf) (column-FFT output twiddle)
     void* d_colB = nullptr;        // packed path: [C][1024] C, exp(-i 2 pi l2 r / nf) (per-coset factor)
     void* d_wsum = nullptr;        // [K] R: W_k^0(0) = sum_n w_k(t_n) (F-statistic)

@@ -36,9 +36,13 @@ struct Tw32 {
     float2 w[16];  // exp(-i 2 pi e / 32), e < 16
 };
 
+// Complex product and squared magnitude with the rounding spelled out (one product rounded, the
+// other fused), so that every kernel that inlines a stage -- whatever the compiler would contract
+// there -- computes the same bits.
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
+__device__ __forceinline__ float norm2f(float2 a) { return __fmaf_rn(a.x, a.x, __fmul_rn(a.y, a.y)); }
 
 __host__ __device__ constexpr int brev(int v, int bits) {
     int r = 0;
@@ -89,7 +93,7 @@ struct __align__(16) Ctx {
     const float2* tw_n1;   // [n1]
     const float2* colT;    // [F][1024]
     const float2* colB;    // [C][1024]
-    const float2* tw1024;  // [1024]
+    const float2* tw1024;  // [32][32]: [cc][l] = W_1024^{cc l}
     const float2* deconv;  // [I]
     const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
     float wq;              // sum_k W_k^0(0)^2
@@ -324,6 +328,32 @@ __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const f
 // shared memory of one column group (float2 units, excluding the [n1] twiddles)
 __host__ __device__ inline size_t cols_group_f2(int rows, int F) { return (size_t)rows * 32 + (size_t)F * 32; }
 
+// One 1024-point row FFT by one warp: S[k2] = sum_{l2} Zr[l2] W_1024^{l2 k2} in natural
+// order; S holds >= 32 x 33 float2 (the padded transpose between the two radix-32 passes).
+template <bool kStream>
+__device__ __forceinline__ void rowfft_one(const Ctx& c, const Tw32& tw, const float2* __restrict__ Zr,
+                                           float2* S) {
+    const int lane = threadIdx.x & 31;
+    float2 v[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) v[a] = ld_inter<kStream>(Zr + lane + 32 * a);
+    fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
+    // twiddle W_1024^{lane cc} from the (L1-resident) [cc][lane] table: 256 contiguous bytes per warp
+    const float2* twl = c.tw1024 + lane;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int cc = brev(q, 5);
+        S[cc * 33 + lane] = cmulf(v[q], __ldg(twl + 32 * cc));
+    }
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
+    __syncwarp();
+    fft_reg<32>(v, tw);  // over b for column cc = lane: v[q] = X[lane + 32 brev(q)]
+#pragma unroll
+    for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
+}
+
 // ---------------------------------------------------------------------------
 // row FFTs of rows [r0, r0 + nr), nr <= R (warp w < nr = row r0 + w; the other
 // warps only take part in the barriers), written transposed for the in-band
@@ -336,31 +366,8 @@ __device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, const 
                                             float2* __restrict__ Xtj, int r0, int nr, float2* smem) {
     constexpr int NT = 32 * R;
     float2* s_row = smem;  // [R][kRowPad]
-    const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float2* S = s_row + warp * kRowPad;
-    const bool active = warp < nr;
-    float2 v[32];
-    if (active) {
-        const float2* Zr = Zj + (int64_t)(r0 + warp) * kRowLen + lane;
-#pragma unroll
-        for (int a = 0; a < 32; ++a) v[a] = ld_inter<kStream>(Zr + 32 * a);
-        fft_reg<32>(v, tw);  // over a for column b = lane: v[q] = Y[lane][brev(q)]
-        // twiddle W_1024^{lane cc} straight from the (L1-resident) table: lane cc <= 961
-        const float2* twl = c.tw1024;
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int cc = brev(q, 5);
-            S[cc * 33 + lane] = cmulf(v[q], __ldg(twl + cc * lane));
-        }
-        __syncwarp();
-#pragma unroll
-        for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
-        __syncwarp();
-        fft_reg<32>(v, tw);  // over b for column cc = lane: v[q] = X[lane + 32 brev(q)]
-#pragma unroll
-        for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
-    }
+    if (warp < nr) rowfft_one<kStream>(c, tw, Zj + (int64_t)(r0 + warp) * kRowLen, s_row + warp * kRowPad);
     __syncthreads();
     // Xt[k2][r0 + rr] for rr < nr: consecutive threads take consecutive rows
     float2* Xb = Xtj + r0;
@@ -436,7 +443,7 @@ __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restr
         const float2 Bc = ld_inter<kStream>(X2 + (int64_t)j * plane);
         // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
         const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd);
-        const float p0 = j0.x * j0.x + j0.y * j0.y;
+        const float p0 = norm2f(j0);
         const int64_t o0 = (int64_t)(2 * j) * I;
         if (J) {
             if (v1) __stcs(J + o0 + i1, j0);
@@ -461,7 +468,7 @@ __device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restr
                 csum.x += j1.x * w1;
                 csum.y += j1.y * w1;
             }
-            const float p1 = j1.x * j1.x + j1.y * j1.y;
+            const float p1 = norm2f(j1);
             const int64_t o1 = o0 + I;
             if (J) {
                 if (v1) __stcs(J + o1 + i1, j1);

@@ -994,19 +994,22 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     g.rw = (int)std::max<int64_t>(1, std::min<int64_t>(g.n1, ecta / g.n2));
     const size_t csz = opts.precision == 32 ? 8 : 16;
     {
-        // chunk so that the FFT workspace of a chunk stays well inside L2
-        // generic path: keep a chunk's workspace within L2.  Packed path: its kernels need
-        // large grids more than L2 residency, so a chunk is up to 16 signals (workspace
-        // 2 * K/2 * nf complex per signal)
+        // generic path: keep a chunk's workspace within L2.  Packed four-kernel path: 4 to 16
+        // signals, as many as keep a chunk's workspace (2 * K/2 * nf complex per signal) within
+        // half of L2 -- consecutive chunks run overlapped on two streams -- but at least 4, so
+        // the grids stay large.  The persistent kernel: up to 16 (its ring of workspace slots).
         const size_t z_per_signal = (size_t)g.kp * g.nf * csz * (g.path >= 2 ? 2 : 1);
         int64_t chunk;
-        if (g.path >= 2) {
+        if (g.path == 2) {
+            chunk = std::max<int64_t>(4, std::min<int64_t>(16, (int64_t)((size_t(64) << 20) / z_per_signal)));
+        } else if (g.path == 3) {
             chunk = std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)((size_t(1) << 30) / z_per_signal)));
         } else {
             chunk = std::max<int64_t>(1, (int64_t)((48u << 20) / std::max<size_t>(z_per_signal, 1)));
             chunk = std::min<int64_t>(chunk, 1024);
         }
-        if (opts.max_batch > 0) chunk = std::min<int64_t>(chunk, opts.max_batch);
+        if (opts.max_batch > 0)  // packed paths: the chunk asked for (at most 64); generic: a cap
+            chunk = g.path >= 2 ? std::min<int64_t>(opts.max_batch, 64) : std::min<int64_t>(chunk, opts.max_batch);
         g.chunk = (int)chunk;
     }
     g.twb_bits = (g.log_nf + 1) / 2;
@@ -1070,7 +1073,15 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twb, unit_roots(int64_t(1) << g.twb_bits, g.nf, 1)));
     if (g.path >= 2) {
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_twn1, unit_roots(g.n1, g.n1, 1)));
-        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, unit_roots(1024, 1024, 1)));
+        {
+            // row-FFT twiddles in the order a warp reads them: [cc][lane] = W_1024^{cc lane}
+            std::vector<double> t32(2 * 1024);
+            for (int cc = 0; cc < 32; ++cc) {
+                const std::vector<double> r = unit_roots(32, 1024, cc);
+                std::copy(r.begin(), r.end(), t32.begin() + 64 * cc);
+            }
+            M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, t32));
+        }
         int64_t F = 1;
         while (F < 32 && g.n1 % (F * 2) == 0) F *= 2;
         g.colF = (int)F;
@@ -1283,9 +1294,9 @@ m2_status time_exec(m2nufft_plan_t p, int64_t B, int reps, double* ms) {
 }
 
 // Autotuning (m2_opts.tune = 1): the default plan, then candidates built from its tapers --
-// sigma 2, half the chunk, the persistent path -- each timed on a synthetic batch of two default
-// chunks; the fastest configuration is rebuilt with the plan's eigenvalues (for the leakage
-// estimate) and returned.  Plans that take the generic path are returned untuned.
+// sigma 2, chunks of 4, 8 and 16 signals (those other than the default), the persistent path --
+// each timed on a synthetic batch of 32 signals; the fastest configuration is rebuilt with the plan's eigenvalues
+// (for the leakage estimate) and returned.  Plans that take the generic path are returned untuned.
 m2_status tuned_plan(const double* t, int64_t N, double fs, double f_w, int K, const m2_fgrid* fc,
                      const double* w_given, const double* lam_given, const m2_opts* opts_in, m2nufft_plan_t* out) {
     m2_opts base = *opts_in;
@@ -1300,17 +1311,20 @@ m2_status tuned_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const std::vector<double> w = p0->w;
     const std::vector<double> lam = p0->lambda;
     const bool have_lam = p0->have_lambda != 0;
-    const int64_t B = std::min<int64_t>(2 * p0->g.chunk, 64);
+    const int64_t B = 32;  // two chunks of the largest candidate
     std::vector<m2_opts> cand;
     m2_opts c = base;
     c.path = 2;
     cand.push_back(c);  // the default configuration (p0)
     c.sigma = 2.0;
     cand.push_back(c);
-    c = base;
-    c.path = 2;
-    c.max_batch = std::max(1, p0->g.chunk / 2);
-    cand.push_back(c);
+    for (int ch : {4, 8, 16}) {
+        if (ch == p0->g.chunk) continue;
+        c = base;
+        c.path = 2;
+        c.max_batch = ch;
+        cand.push_back(c);
+    }
     c = base;
     c.path = 3;
     cand.push_back(c);

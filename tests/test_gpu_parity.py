@@ -800,8 +800,8 @@ def test_sigma_option_rejects_out_of_range(dev):
 
 
 def test_autotuned_plan(dev):
-    """tune = True: the report lists the four packed configurations (default, sigma 2, half chunk,
-    persistent), the plan kept is the fastest of them, its output meets the parity bar, and the
+    """tune = True: the report lists the packed configurations (default, sigma 2, chunks of 4, 8
+    and 16 signals other than the default, persistent), the plan kept is the fastest of them, its output meets the parity bar, and the
     eigenvalues handed in survive the rebuild (the leakage estimate is the untuned plan's)."""
     wl = synth.workload("jitter16k", batch=3)
     w = seeded_tapers(wl.K, wl.N, 8)
@@ -810,16 +810,18 @@ def test_autotuned_plan(dev):
     ref = pkg.Plan(*args, precision=32, tapers=w, lam=lam)
     plan = pkg.Plan(*args, precision=32, tapers=w, lam=lam, tune=True)
     rep = plan.tuning()
-    assert [r[0] for r in rep] == [2, 2, 2, 3]
-    assert rep[1][1] == 2.0 and rep[2][2] == ref.info["chunk"] // 2
+    ch = ref.info["chunk"]
+    chunks = [c for c in (4, 8, 16) if c != ch]
+    assert [r[0] for r in rep] == [2, 2] + [2] * len(chunks) + [3]
+    assert rep[1][1] == 2.0 and [r[2] for r in rep[2:-1]] == chunks
     ms = [r[3] for r in rep]
     assert all(0 < m < 1e3 for m in ms)
     best = int(np.argmin(ms))
     assert plan.info["path"] == rep[best][0]
     if best == 1:
         assert plan.info["nf"] >= 2 * wl.I
-    if best == 2:
-        assert plan.info["chunk"] == rep[2][2]
+    if 2 <= best < len(rep) - 1:
+        assert plan.info["chunk"] == rep[best][2]
     assert ref.tuning() == []
     out = run_plan(plan, wl.x, dev)
     idx = sample_bands(wl.I, 256, 3)
