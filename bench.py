@@ -165,21 +165,22 @@ class ClockSampler:
 
 
 def profiled_traffic(workload: str, kernel: str, nb: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture (profiles/), scaled to nb
-    signals per launch; None if there is no capture for this kernel/workload or the kernel source
-    changed since it was taken."""
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload
+    (profiles/exec_kernels_<workload>_traffic.json), scaled to nb signals per launch; None if there
+    is no capture for this kernel/workload, it was taken at another chunk size, or the kernel
+    sources changed since it was taken."""
     import hashlib
-    names = {"epi": "epi_kernel", "pipe": "pipe_kernel"}
-    if kernel not in names:
-        return None
-    path = os.path.join(ROOT, "profiles", f"{names[kernel]}_{workload}_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"exec_kernels_{workload}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         for rel, h in d["sources"].items():
             if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16] != h:
                 return None
-        return float(d["traffic_bytes_per_launch"]) * nb / float(d["signals_per_launch"])
+        k = d["kernels"][kernel]
+        if int(d["signals_per_launch"]) != nb:
+            return None
+        return float(k["dram_bytes_read_per_launch"]) + float(k["dram_bytes_write_per_launch"])
     except Exception:
         return None
 

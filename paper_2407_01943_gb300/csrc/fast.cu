@@ -143,9 +143,20 @@ __global__ void __launch_bounds__(128) epi_kernel(Ctx c, const float2* __restric
     const int b = blockIdx.z;
     if (k1 >= c.n1) return;
     const int64_t KI = (int64_t)c.K * c.I;
-    packed::epi_position<true, kF>(c, Xt + (int64_t)b * c.Kp * c.n1 * kRowLen, k1, blockIdx.y,
-                                   J ? J + b * KI : nullptr, E ? E + b * KI : nullptr,
+    const float2* Xtb = Xt + (int64_t)b * c.Kp * c.n1 * kRowLen;
+    packed::epi_position<true, kF>(c, Xtb, k1, blockIdx.y, J ? J + b * KI : nullptr, E ? E + b * KI : nullptr,
                                    P ? P + (int64_t)b * c.I : nullptr, F ? F + (int64_t)b * c.I : nullptr);
+    // Xt[j][k2][k1] for k2 <= k2max is read by position (k1, k2) alone (its partners lie in the
+    // columns k2 >= 1023 - k2max, or are itself), so once the warp has consumed them, the 16-entry
+    // lines of its 32 consecutive k1 are dead.  Warp-uniform condition: whole warp in range and
+    // lines aligned (n1 % 16 == 0; Xt planes are n1 * 1024 complex).
+    const int kw = k1 & ~31;
+    if ((c.n1 & 15) == 0 && kw + 32 <= c.n1) {
+        __syncwarp();
+        if ((threadIdx.x & 15) == 0)
+            for (int j = 0; j < c.Kp; ++j)
+                packed::discard_l2(Xtb + (int64_t)j * c.n1 * kRowLen + (int64_t)blockIdx.y * c.n1 + k1);
+    }
 }
 
 template <int F>

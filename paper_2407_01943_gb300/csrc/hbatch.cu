@@ -33,7 +33,7 @@ using packed::kRowLen;
 constexpr int kEpiThreads = 128;
 constexpr int kColThreads = 128;  // 4 warps: one group of 4 warps, or 4 one-warp groups
 constexpr int kRowWarps = 8;
-constexpr int kSpreadTiles = 1;  // spread tiles per CTA
+constexpr int kSpreadTiles = 2;  // spread tiles per CTA
 
 struct __align__(16) HTask {
     const float* x;

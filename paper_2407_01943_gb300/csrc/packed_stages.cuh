@@ -99,6 +99,13 @@ struct __align__(16) Ctx {
     float wq;              // sum_k W_k^0(0)^2
 };
 
+// Drop a dead 128-byte line of an intermediate from L2 without writing it back (its contents
+// become undefined; the next writer of the workspace overwrites it before anyone reads it).
+// p: 128-byte aligned.
+__device__ __forceinline__ void discard_l2(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Load of an intermediate written earlier: kStream = streaming (evict-first) for the
 // stand-alone kernels, where each value is read once; otherwise L2-only (.cg), which
 // is coherent with stores made by other CTAs of the same kernel.
@@ -346,6 +353,12 @@ __device__ __forceinline__ void rowfft_one(const Ctx& c, const Tw32& tw, const f
         S[cc * 33 + lane] = cmulf(v[q], __ldg(twl + 32 * cc));
     }
     __syncwarp();
+    // stand-alone kernels: this warp was the row's only reader, and every lane's loads have been
+    // consumed, so its 64 lines are dead (Zr is 8 KB aligned: Z rows are 1024 complex)
+    if (kStream) {
+        discard_l2(Zr + 32 * lane);
+        discard_l2(Zr + 32 * lane + 16);
+    }
 #pragma unroll
     for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
     __syncwarp();
