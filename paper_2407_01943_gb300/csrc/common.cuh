@@ -176,13 +176,12 @@ struct m2nufft_plan_s {
     double* d_Lhat = nullptr;      // [K][I]
     double* d_Ehat = nullptr;      // [I]
     void* d_g = nullptr;           // workspace [chunk][K][Lg] C
-    void* d_Z = nullptr;           // workspace [chunk][K][nf] C
-    void* d_X = nullptr;           // packed path workspace [chunk][K/2][1024][n1] C: row transforms, transposed
+    void* d_Z = nullptr;           // workspace [chunk][K][nf] C (packed path: [chunk][K/2][n1][1024], the
+                                   // column DFTs, then in place the in-band row transforms)
     // packed path, execs of more than one chunk: a second workspace and two internal streams, so
     // that chunk c's epilogue (HBM-bound) overlaps chunk c+1's spread and FFTs (issue-bound)
     void* d_g2 = nullptr;
     void* d_Z2 = nullptr;
-    void* d_X2 = nullptr;
     cudaStream_t lane_st[2] = {nullptr, nullptr};
     cudaEvent_t lane_ev[2] = {nullptr, nullptr};
     cudaEvent_t fork_ev = nullptr;

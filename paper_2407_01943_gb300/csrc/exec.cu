@@ -381,17 +381,14 @@ m2_status ensure_lanes(m2nufft_plan_s* p) {
     if (p->lane_st[0]) return M2_OK;
     const Geometry& g = p->g;
     const size_t ng = (size_t)g.chunk * g.kp * g.Lg, nz = (size_t)g.chunk * g.kp * g.nf;
-    void *a = nullptr, *b = nullptr, *c = nullptr;
+    void *a = nullptr, *b = nullptr;
     M2_CUDA_TRY(cudaMalloc(&a, sizeof(float2) * ng));
     p->allocations.push_back(a);
     M2_CUDA_TRY(cudaMalloc(&b, sizeof(float2) * nz));
     p->allocations.push_back(b);
-    M2_CUDA_TRY(cudaMalloc(&c, sizeof(float2) * nz));
-    p->allocations.push_back(c);
-    p->device_bytes += sizeof(float2) * (ng + 2 * nz);
+    p->device_bytes += sizeof(float2) * (ng + nz);
     p->d_g2 = a;
     p->d_Z2 = b;
-    p->d_X2 = c;
     M2_CUDA_TRY(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
     for (int L = 0; L < 2; ++L) {
         M2_CUDA_TRY(cudaStreamCreateWithFlags(&p->lane_st[L], cudaStreamNonBlocking));

@@ -5,8 +5,8 @@
 //
 // Layout per chunk of nb signals (plan workspace):
 //   g  [nb][Kp][rows * 1024]   spread grids of the taper pairs
-//   Z  [nb][Kp][n1][1024]      after the column DFTs and the nf twiddle
-//   Xt [nb][Kp][1024][n1]      row transforms, transposed (in-band columns only)
+//   Z  [nb][Kp][n1][1024]      after the column DFTs and the nf twiddle; then, in place, the
+//                              row transforms (in-band columns only)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -125,38 +125,31 @@ __global__ void __launch_bounds__(32 * kColWarps) cols_fast_kernel(Ctx c, Tw32 t
                           threadIdx.x >> 5, kColWarps, s_tw, s_tw + c.n1);
 }
 
-// grid (n1 / R, Kp, nb): R consecutive rows of one taper pair per CTA, one warp per row
+// grid (n1 / R, Kp, nb): R consecutive rows of one taper pair per CTA, one warp per row, in place
 template <int R>
-__global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1))
-rowfft_kernel(Ctx c, Tw32 tw, const float2* __restrict__ Z, float2* __restrict__ Xt) {
+__global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1)) rowfft_kernel(Ctx c, Tw32 tw, float2* __restrict__ Z) {
     extern __shared__ float2 smem_f2[];
     const int64_t base = ((int64_t)blockIdx.z * c.Kp + blockIdx.y) * (int64_t)c.n1 * kRowLen;
-    packed::rowfft_rows<R, true>(c, tw, Z + base, Xt + base, blockIdx.x * R, R, smem_f2);
+    packed::rowfft_rows<R, true>(c, tw, Z + base, blockIdx.x * R, R, smem_f2);
 }
 
-// grid (ceil(n1 / 128), k2max + 1, nb): thread = position (k1, k2) and its mirror; kF adds the
-// F-statistic output
+// grid (epi_tiles(n1, k2max, T1), nb): one T1 x 16 tile of positions per CTA (and its partners);
+// kF adds the F-statistic output (32 x 16 tiles, 512 threads, one position each)
+constexpr int kEpiT1 = 32;
+constexpr int kEpiMinBlocks = 4;
+__host__ __device__ constexpr int epi_t1(bool kF) { return kF ? 32 : kEpiT1; }
+__host__ __device__ constexpr int epi_threads(bool kF) { return 16 * epi_t1(kF); }  // one position per thread
 template <bool kF>
-__global__ void __launch_bounds__(128) epi_kernel(Ctx c, const float2* __restrict__ Xt, float2* __restrict__ J,
-                                                  float* __restrict__ E, float* __restrict__ P, float* __restrict__ F) {
-    const int k1 = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.z;
-    if (k1 >= c.n1) return;
+__global__ void __launch_bounds__(epi_threads(kF), kF ? 1 : kEpiMinBlocks) epi_kernel(Ctx c, const float2* __restrict__ Y,
+                                                              float2* __restrict__ J, float* __restrict__ E,
+                                                              float* __restrict__ P, float* __restrict__ F) {
+    __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(epi_t1(kF)) / sizeof(float2)];
+    const int b = blockIdx.y;
     const int64_t KI = (int64_t)c.K * c.I;
-    const float2* Xtb = Xt + (int64_t)b * c.Kp * c.n1 * kRowLen;
-    packed::epi_position<true, kF>(c, Xtb, k1, blockIdx.y, J ? J + b * KI : nullptr, E ? E + b * KI : nullptr,
-                                   P ? P + (int64_t)b * c.I : nullptr, F ? F + (int64_t)b * c.I : nullptr);
-    // Xt[j][k2][k1] for k2 <= k2max is read by position (k1, k2) alone (its partners lie in the
-    // columns k2 >= 1023 - k2max, or are itself), so once the warp has consumed them, the 16-entry
-    // lines of its 32 consecutive k1 are dead.  Warp-uniform condition: whole warp in range and
-    // lines aligned (n1 % 16 == 0; Xt planes are n1 * 1024 complex).
-    const int kw = k1 & ~31;
-    if ((c.n1 & 15) == 0 && kw + 32 <= c.n1) {
-        __syncwarp();
-        if ((threadIdx.x & 15) == 0)
-            for (int j = 0; j < c.Kp; ++j)
-                packed::discard_l2(Xtb + (int64_t)j * c.n1 * kRowLen + (int64_t)blockIdx.y * c.n1 + k1);
-    }
+    packed::epi_tile<epi_t1(kF), epi_threads(kF), true, kF, true>(c, Y + (int64_t)b * c.Kp * c.n1 * kRowLen, blockIdx.x,
+                                                     J ? J + b * KI : nullptr, E ? E + b * KI : nullptr,
+                                                     P ? P + (int64_t)b * c.I : nullptr,
+                                                     F ? F + (int64_t)b * c.I : nullptr, smem);
 }
 
 template <int F>
@@ -169,9 +162,9 @@ m2_status launch_cols_fast(const Ctx& c, const Tw32& tw, const float2* g, float2
 }
 
 template <int R>
-m2_status launch_rowfft(const Ctx& c, const Tw32& tw, const float2* Z, float2* Xt, int nb, cudaStream_t st) {
+m2_status launch_rowfft(const Ctx& c, const Tw32& tw, float2* Z, int nb, cudaStream_t st) {
     dim3 grid((unsigned)(c.n1 / R), (unsigned)c.Kp, (unsigned)nb);
-    rowfft_kernel<R><<<grid, 32 * R, packed::rowfft_smem_bytes(R), st>>>(c, tw, Z, Xt);
+    rowfft_kernel<R><<<grid, 32 * R, packed::rowfft_smem_bytes(R), st>>>(c, tw, Z);
     M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
 }
@@ -197,7 +190,6 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     // workspace of lane 0 (the plan's) or lane 1 (the second half, for overlapped chunks)
     float2* dg = reinterpret_cast<float2*>(lane ? p->d_g2 : p->d_g);
     float2* dZ = reinterpret_cast<float2*>(lane ? p->d_Z2 : p->d_Z);
-    float2* dX = reinterpret_cast<float2*>(lane ? p->d_X2 : p->d_X);
 
     mark(p, 0, 0, st);
     {
@@ -222,17 +214,21 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     {
         int R = 1;  // rows per CTA: largest power of two <= 8 dividing n1
         while (R < 8 && g.n1 % (R * 2) == 0) R *= 2;
-        if (R == 8) M2_TRY(launch_rowfft<8>(c, tw, dZ, dX, nb, st));
-        else if (R == 4) M2_TRY(launch_rowfft<4>(c, tw, dZ, dX, nb, st));
-        else M2_TRY(launch_rowfft<2>(c, tw, dZ, dX, nb, st));
+        if (R == 8) M2_TRY(launch_rowfft<8>(c, tw, dZ, nb, st));
+        else if (R == 4) M2_TRY(launch_rowfft<4>(c, tw, dZ, nb, st));
+        else M2_TRY(launch_rowfft<2>(c, tw, dZ, nb, st));
     }
     mark(p, 2, 1, st);
 
     mark(p, 3, 0, st);
     {
-        dim3 grid((unsigned)((g.n1 + 127) / 128), (unsigned)(c.k2max + 1), (unsigned)nb);
-        if (F) epi_kernel<true><<<grid, 128, 0, st>>>(c, dX, J, E, P, F);
-        else epi_kernel<false><<<grid, 128, 0, st>>>(c, dX, J, E, P, nullptr);
+        if (F) {
+            dim3 grid((unsigned)packed::epi_tiles(c.n1, c.k2max, epi_t1(true)), (unsigned)nb);
+            epi_kernel<true><<<grid, epi_threads(true), 0, st>>>(c, dZ, J, E, P, F);
+        } else {
+            dim3 grid((unsigned)packed::epi_tiles(c.n1, c.k2max, epi_t1(false)), (unsigned)nb);
+            epi_kernel<false><<<grid, epi_threads(false), 0, st>>>(c, dZ, J, E, P, nullptr);
+        }
         M2_CUDA_TRY(cudaGetLastError());
     }
     mark(p, 3, 1, st);

@@ -30,7 +30,7 @@ using packed::Ctx;
 using packed::Tw32;
 using packed::kRowLen;
 
-constexpr int kEpiThreads = 128;
+constexpr int kEpiThreads = 256;  // one 32 x 16 epilogue tile per CTA
 constexpr int kColThreads = 128;  // 4 warps: one group of 4 warps, or 4 one-warp groups
 constexpr int kRowWarps = 8;
 constexpr int kSpreadTiles = 2;  // spread tiles per CTA
@@ -41,7 +41,7 @@ struct __align__(16) HTask {
     float* E;
     float* P;
     int64_t g_off;  // spread grids [Kp][Lg] at ws + g_off
-    int64_t z_off;  // Z [Kp][n1][1024] at ws + z_off, Xt [Kp][1024][n1] right after
+    int64_t z_off;  // Z [Kp][n1][1024] at ws + z_off (then, in place, the row transforms)
     int ctx;
     int pad0, pad1, pad2;
 };
@@ -102,25 +102,20 @@ __global__ void __launch_bounds__(32 * kRowWarps, 2) hb_rows_kernel(const int4* 
     const int4 m = map[blockIdx.x];
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
     const Ctx& c = s_ctx;
-    const int64_t plane = (int64_t)c.n1 * kRowLen;
-    float2* Z = ws + s_task.z_off + (int64_t)m.y * plane;
-    float2* Xt = ws + s_task.z_off + (int64_t)c.Kp * plane + (int64_t)m.y * plane;
-    packed::rowfft_rows<kRowWarps, true>(c, tw, Z, Xt, m.z, m.w, smem_f2);
+    float2* Z = ws + s_task.z_off + (int64_t)m.y * c.n1 * kRowLen;
+    packed::rowfft_rows<kRowWarps, true>(c, tw, Z, m.z, m.w, smem_f2);
 }
 
-// map entry: (task, first flattened position k2 * n1 + k1)
+// map entry: (task, epilogue tile)
 __global__ void __launch_bounds__(kEpiThreads) hb_epi_kernel(const int2* __restrict__ map, const HTask* tasks,
                                                              const Ctx* ctxs, const float2* ws) {
     __shared__ __align__(16) Ctx s_ctx;
     __shared__ __align__(16) HTask s_task;
+    __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(32) / sizeof(float2)];
     const int2 m = map[blockIdx.x];
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
-    const Ctx& c = s_ctx;
-    const int pos = m.y + threadIdx.x;
-    if (pos >= c.n1 * (c.k2max + 1)) return;
-    const int k2 = pos / c.n1;
-    const float2* Xt = ws + s_task.z_off + (int64_t)c.Kp * c.n1 * kRowLen;
-    packed::epi_position<true>(c, Xt, pos - k2 * c.n1, k2, s_task.J, s_task.E, s_task.P);
+    packed::epi_tile<32, kEpiThreads, true, false, true>(s_ctx, ws + s_task.z_off, m.y, s_task.J, s_task.E, s_task.P,
+                                                     nullptr, smem);
 }
 
 template <typename T>
@@ -194,7 +189,7 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
         return o;
     };
     t.g_off = take((int64_t)c.Kp * c.Lg);
-    t.z_off = take(2 * (int64_t)c.Kp * c.n1 * kRowLen);
+    t.z_off = take((int64_t)c.Kp * c.n1 * kRowLen);
     // spread: kSpreadTiles tiles per CTA
     const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
     for (int64_t tile = 0; tile < ntiles; tile += kSpreadTiles)
@@ -211,9 +206,9 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
     // row FFTs: up to 8 rows per CTA
     for (int j = 0; j < c.Kp; ++j)
         for (int r0 = 0; r0 < c.n1; r0 += kRowWarps) m.ro.push_back(make_int4(task, j, r0, std::min(kRowWarps, c.n1 - r0)));
-    // epilogue: 128 positions per CTA
-    const int npos = c.n1 * (c.k2max + 1);
-    for (int p0 = 0; p0 < npos; p0 += kEpiThreads) m.ep.push_back(make_int2(task, p0));
+    // epilogue: one 32 x 16 tile per CTA
+    const int ntile = packed::epi_tiles(c.n1, c.k2max, 32);
+    for (int e = 0; e < ntile; ++e) m.ep.push_back(make_int2(task, e));
 }
 
 // Device work-map pointers and counts of one launch.

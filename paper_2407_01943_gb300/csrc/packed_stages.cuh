@@ -10,14 +10,16 @@
 //         X_{2j+1}[k] = (Zp[k] - conj(Zp[nf-k])) / (2i);
 //   * four-step FFT nf = n1 * 1024 with the spread support in the first `rows`
 //     rows: column DFTs per coset k1 = r + C q (C = n1/F) by folding the inputs
-//     modulo F and one F-point register FFT, then 1024-point row FFTs (one warp
-//     per row, 32 x 32 in registers, one padded shared-memory transpose),
-//     written transposed (Xt[k2][k1]);
+//     modulo F and one F-point register FFT, then 1024-point row FFTs in place
+//     (one warp per row, 32 x 32 in registers, one padded shared-memory
+//     transpose; only the in-band columns are written back);
 //   * epilogue: one thread per output pair (m, -m): J(-m) = conj J(m) since
 //     both tapers are real and the deconvolution factor satisfies
-//     s(-m) = conj s(m); P-hat summed over the pairs in registers.
-// Intermediates (g, Z, Xt) are read with ld.global.cg (L2, not L1), so stages
-// may consume data written by other CTAs of the same kernel.
+//     s(-m) = conj s(m); P-hat summed over the pairs in registers.  Tiles of
+//     32 rows x 16 columns and their partners are staged in shared memory so
+//     that both the loads and the J/E/P stores are coalesced.
+// Intermediates (g, Z) are read with ld.global.cg (L2, not L1), so stages may
+// consume data written by other CTAs of the same kernel.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -335,11 +337,14 @@ __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const f
 // shared memory of one column group (float2 units, excluding the [n1] twiddles)
 __host__ __device__ inline size_t cols_group_f2(int rows, int F) { return (size_t)rows * 32 + (size_t)F * 32; }
 
-// One 1024-point row FFT by one warp: S[k2] = sum_{l2} Zr[l2] W_1024^{l2 k2} in natural
-// order; S holds >= 32 x 33 float2 (the padded transpose between the two radix-32 passes).
+// One 1024-point row FFT by one warp, in place: the in-band transforms
+//   Y[k2] = sum_{l2} Zr[l2] W_1024^{l2 k2},   k2 <= k2max or k2 >= 1023 - k2max,
+// overwrite Zr[k2]; the other columns keep stale values (nothing reads them).  Lane l loads and
+// stores only the entries l + 32 a, so the lanes need no ordering among themselves.  Each store
+// of the warp covers 32 consecutive columns (256 bytes).  S: >= 32 x 33 float2 of this warp's
+// shared memory, the padded transpose between the two radix-32 passes.
 template <bool kStream>
-__device__ __forceinline__ void rowfft_one(const Ctx& c, const Tw32& tw, const float2* __restrict__ Zr,
-                                           float2* S) {
+__device__ __forceinline__ void rowfft_row(const Ctx& c, const Tw32& tw, float2* __restrict__ Zr, float2* S) {
     const int lane = threadIdx.x & 31;
     float2 v[32];
 #pragma unroll
@@ -353,177 +358,210 @@ __device__ __forceinline__ void rowfft_one(const Ctx& c, const Tw32& tw, const f
         S[cc * 33 + lane] = cmulf(v[q], __ldg(twl + 32 * cc));
     }
     __syncwarp();
-    // stand-alone kernels: this warp was the row's only reader, and every lane's loads have been
-    // consumed, so its 64 lines are dead (Zr is 8 KB aligned: Z rows are 1024 complex)
-    if (kStream) {
-        discard_l2(Zr + 32 * lane);
-        discard_l2(Zr + 32 * lane + 16);
-    }
 #pragma unroll
     for (int a = 0; a < 32; ++a) v[a] = S[lane * 33 + a];
-    __syncwarp();
+    __syncwarp();         // S is free again
     fft_reg<32>(v, tw);  // over b for column cc = lane: v[q] = X[lane + 32 brev(q)]
+    const int nlo = c.k2max + 1;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) S[lane + 32 * brev(q, 5)] = v[q];
+    for (int q = 0; q < 32; ++q) {
+        const int k2 = lane + 32 * brev(q, 5);
+        if (k2 < nlo || k2 >= kRowLen - nlo) __stcg(Zr + k2, v[q]);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// row FFTs of rows [r0, r0 + nr), nr <= R (warp w < nr = row r0 + w; the other
-// warps only take part in the barriers), written transposed for the in-band
-// columns k2 <= k2max and k2 >= 1023 - k2max only:
-//   Xt[k2][k1] = sum_{l2} Z[k1][l2] W_1024^{l2 k2}
-// Called by all 32 R threads of the CTA.  smem (float2): R * kRowPad.
+// row FFTs of rows [r0, r0 + nr), nr <= R, in place (warp w < nr = row r0 + w):
+//   Z[k1][k2] <- sum_{l2} Z[k1][l2] W_1024^{l2 k2} for the in-band columns.
+// Called by all 32 R threads of the CTA; the warps are independent.  smem (float2): R * kRowPad.
 // ---------------------------------------------------------------------------
 template <int R, bool kStream>
-__device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, const float2* __restrict__ Zj,
-                                            float2* __restrict__ Xtj, int r0, int nr, float2* smem) {
-    constexpr int NT = 32 * R;
-    float2* s_row = smem;  // [R][kRowPad]
+__device__ __forceinline__ void rowfft_rows(const Ctx& c, const Tw32& tw, float2* __restrict__ Zj, int r0, int nr,
+                                            float2* smem) {
     const int warp = threadIdx.x >> 5;
-    if (warp < nr) rowfft_one<kStream>(c, tw, Zj + (int64_t)(r0 + warp) * kRowLen, s_row + warp * kRowPad);
-    __syncthreads();
-    // Xt[k2][r0 + rr] for rr < nr: consecutive threads take consecutive rows
-    float2* Xb = Xtj + r0;
-    const int nlo = c.k2max + 1;  // k2 in [0, nlo)
-    const int nout = 2 * nlo;     // plus k2 in [1024 - nlo, 1024)
-    const int n1 = c.n1;
-    if (nr == R) {
-#pragma unroll 4
-        for (int e = threadIdx.x; e < R * nout; e += NT) {
-            const int rr = e % R, q = e / R;
-            const int k2 = q < nlo ? q : kRowLen - nout + q;
-            Xb[(int64_t)k2 * n1 + rr] = s_row[rr * kRowPad + k2];
-        }
-    } else {
-        for (int e = threadIdx.x; e < nr * nout; e += NT) {
-            const int rr = e % nr, q = e / nr;
-            const int k2 = q < nlo ? q : kRowLen - nout + q;
-            Xb[(int64_t)k2 * n1 + rr] = s_row[rr * kRowPad + k2];
-        }
-    }
-    __syncthreads();  // smem reuse
+    if (warp < nr) rowfft_row<kStream>(c, tw, Zj + (int64_t)(r0 + warp) * kRowLen, smem + warp * kRowPad);
 }
 
 inline size_t rowfft_smem_bytes(int R) { return sizeof(float2) * (size_t)R * kRowPad; }
 
 // ---------------------------------------------------------------------------
-// epilogue for position k = k1 + n1 k2 (k2 <= k2max) and its partner nf - k:
-// (n1 - k1, 1023 - k2), or (0, 1024 - k2) for k1 = 0.  Unpack each taper pair,
-// deconvolve, write J and |J|^2 at m and -m, and the taper average P-hat.
-// Xtb: [Kp][1024][n1]; J, E: [K][I]; P: [I] (this signal; NULL = not wanted).
+// epilogue tiles.  Position k = k1 + n1 k2 (k2 <= k2max, the m >= 0 side) pairs with nf - k at
+// (n1 - k1, 1023 - k2), or (0, 1024 - k2) for k1 = 0, in the row transforms Y[j][k1][k2] of the
+// taper pairs j.  A tile is k1 in [k1a, k1a + T1) x k2 in [k2a, k2a + 16): per pair, its T1 row
+// segments and their partners' (one 128-byte line each) are staged in shared memory with
+// coalesced loads, then each thread unpacks, deconvolves and writes J and |J|^2 at m and -m for
+// its positions -- consecutive threads take consecutive k1, so consecutive bands.  P-hat (and
+// with kF Thomson's F-statistic) accumulates over the pairs in registers.
+// Every in-band entry of Y is read by one position only (lower columns k2 <= k2max < 512 by
+// (k1, k2); upper columns >= 512 by their partner), so with kDiscard the tile's lines are dropped
+// from L2 once staged (row 0's partner columns 1024 - k2 straddle two tiles: kept).
+// Yb: [Kp][n1][1024] of this signal; J, E: [K][I]; P, Fout: [I] (NULL = not wanted).
+// Called by all NT threads of the CTA (NT >= 2 T1; T1 * 16 / NT positions each).
+// kF (Sec. 3, Eq. f_stat): C = sum_k J_k W_k / sum_k W_k^2,
+//   F = |C|^2 (K - 1) sum_k W_k^2 / sum_k |J_k - C W_k|^2, equal at m and -m.
 // ---------------------------------------------------------------------------
-// With kF, also Thomson's F-statistic (Sec. 3, Eq. f_stat) at m and -m (equal, since
-// J_k(-m) = conj J_k(m) and W_k^0(0) is real):
-//   C = sum_k J_k W_k / sum_k W_k^2,  F = |C|^2 (K - 1) sum_k W_k^2 / sum_k |J_k - C W_k|^2.
-template <bool kStream, bool kF = false>
-__device__ __forceinline__ void epi_position(const Ctx& c, const float2* __restrict__ Xtb, int k1, int k2,
-                                             float2* __restrict__ J, float* __restrict__ E,
-                                             float* __restrict__ Pout, float* __restrict__ Fout = nullptr) {
-    const int n1 = c.n1, nf = c.nf, I = c.I, K = c.K;
-    const int half = nf >> 1;
-    int pk1, pk2;
-    if (k1 == 0) {
-        pk1 = 0;
-        pk2 = (kRowLen - k2) & (kRowLen - 1);
-    } else {
-        pk1 = n1 - k1;
-        pk2 = kRowLen - 1 - k2;
-    }
-    const int kk1 = k1 + n1 * k2;
-    const int kk2 = pk1 + n1 * pk2;
-    const int i1 = (kk1 < half ? kk1 : kk1 - nf) + c.i_c;
-    const int i2 = (kk2 < half ? kk2 : kk2 - nf) + c.i_c;
-    const bool v1 = (unsigned)i1 < (unsigned)I;
-    const bool v2 = (unsigned)i2 < (unsigned)I && kk2 != kk1;
-    if (!v1 && !v2) return;
-    float2 sd;
-    if (v1) {
-        sd = __ldg(c.deconv + i1);
-    } else {
-        sd = __ldg(c.deconv + i2);
-        sd.y = -sd.y;
-    }
+constexpr int kEpiT2 = 16;  // k2 extent of an epilogue tile: one 128-byte line
+__host__ __device__ inline int epi_tiles_k2(int k2max) { return k2max / kEpiT2 + 1; }
+__host__ __device__ inline int epi_tiles(int n1, int k2max, int T1) { return (n1 + T1 - 1) / T1 * epi_tiles_k2(k2max); }
+__host__ __device__ constexpr size_t epi_tile_smem_bytes(int T1) { return sizeof(float2) * 2 * T1 * (kEpiT2 + 1); }
+
+template <int kEpiT1, int NT, bool kStream, bool kF, bool kDiscard>
+__device__ __forceinline__ void epi_tile(const Ctx& c, const float2* __restrict__ Yb, int tile,
+                                         float2* __restrict__ J, float* __restrict__ E, float* __restrict__ P,
+                                         float* __restrict__ Fout, float2* smem) {
+    constexpr int LD = kEpiT2 + 1;
+    constexpr int PPT = kEpiT1 * kEpiT2 / NT;
+    static_assert(PPT >= 1 && PPT * NT == kEpiT1 * kEpiT2, "tile / thread count");
+    static_assert(!kF || PPT == 1, "the F-statistic keeps every J_k of one position in registers");
+    float2* sA = smem;                // [T1][LD] Y[j][k1][k2]
+    float2* sB = smem + kEpiT1 * LD;  // [T1][LD] the partner entries
+    const int n1 = c.n1, nf = c.nf, half = nf >> 1, I = c.I, K = c.K, Kp = c.Kp;
+    // consecutive tiles take consecutive k1 blocks of the same 16 columns, so the CTAs running
+    // together write one contiguous stretch of bands (n1 * 16 of them) of each output plane
+    const int ntk1 = (n1 + kEpiT1 - 1) / kEpiT1;
+    const int k1a = (tile % ntk1) * kEpiT1, k2a = (tile / ntk1) * kEpiT2;
+    const int nlo = c.k2max + 1;
     const int64_t plane = (int64_t)n1 * kRowLen;
-    const float2* X1 = Xtb + (int64_t)k2 * n1 + k1;
-    const float2* X2 = Xtb + (int64_t)pk2 * n1 + pk1;
-    const int Kp = c.Kp;
-    float pacc = 0.f;
-    constexpr int kMaxPairs = kF ? (kMaxK + 1) / 2 : 1;
-    float2 jk[kMaxPairs][2];  // kF: J of every taper at m, for the residual of the line fit
-    float2 csum = make_float2(0.f, 0.f);
-    auto pair = [&](int j) {
-        const float2 A = ld_inter<kStream>(X1 + (int64_t)j * plane);
-        const float2 Bc = ld_inter<kStream>(X2 + (int64_t)j * plane);
-        // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
-        const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd);
-        const float p0 = norm2f(j0);
-        const int64_t o0 = (int64_t)(2 * j) * I;
-        if (J) {
-            if (v1) __stcs(J + o0 + i1, j0);
-            if (v2) __stcs(J + o0 + i2, make_float2(j0.x, -j0.y));
-        }
-        if (E) {
-            if (v1) __stcs(E + o0 + i1, p0);
-            if (v2) __stcs(E + o0 + i2, p0);
-        }
-        pacc += p0;
-        if (kF) {
-            const float w0 = c.wsum[2 * j];
-            jk[kF ? j : 0][0] = j0;
-            csum.x += j0.x * w0;
-            csum.y += j0.y * w0;
-        }
-        if (2 * j + 1 < K) {
-            const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd);
-            if (kF) {
-                const float w1 = c.wsum[2 * j + 1];
-                jk[kF ? j : 0][1] = j1;
-                csum.x += j1.x * w1;
-                csum.y += j1.y * w1;
+
+    // this thread's positions (r, cc) = (e % T1, e / T1)
+    int i1[PPT], i2[PPT];
+    bool v1[PPT], v2[PPT];
+    float2 sd[PPT];
+    float pacc[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+        const int e = threadIdx.x + u * NT;
+        const int k1 = k1a + e % kEpiT1, k2 = k2a + e / kEpiT1;
+        v1[u] = v2[u] = false;
+        i1[u] = i2[u] = 0;
+        pacc[u] = 0.f;
+        sd[u] = make_float2(0.f, 0.f);
+        if (k1 < n1 && k2 < nlo) {
+            const int pk1 = k1 == 0 ? 0 : n1 - k1;
+            const int pk2 = k1 == 0 ? (kRowLen - k2) & (kRowLen - 1) : kRowLen - 1 - k2;
+            const int kk1 = k1 + n1 * k2, kk2 = pk1 + n1 * pk2;
+            i1[u] = (kk1 < half ? kk1 : kk1 - nf) + c.i_c;
+            i2[u] = (kk2 < half ? kk2 : kk2 - nf) + c.i_c;
+            v1[u] = (unsigned)i1[u] < (unsigned)I;
+            v2[u] = (unsigned)i2[u] < (unsigned)I && kk2 != kk1;
+            if (v1[u]) {
+                sd[u] = __ldg(c.deconv + i1[u]);
+            } else if (v2[u]) {
+                sd[u] = __ldg(c.deconv + i2[u]);
+                sd[u].y = -sd[u].y;
             }
-            const float p1 = norm2f(j1);
-            const int64_t o1 = o0 + I;
+        }
+    }
+    constexpr int kMaxPairs = kF ? (kMaxK + 1) / 2 : 1;
+    float2 jk[kMaxPairs][2];  // kF: J of every taper at this position, for the residual of the line fit
+    float2 csum = make_float2(0.f, 0.f);
+
+    auto pair = [&](int j) {
+        const float2* Yj = Yb + (int64_t)j * plane;
+        __syncthreads();  // the previous pair's reads of the tile are done
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            const int e = threadIdx.x + u * NT;
+            const int lr = e / kEpiT2, lc = e % kEpiT2;  // 16 threads per 128-byte row segment
+            const int k1 = k1a + lr, k2 = k2a + lc;
+            if (k1 < n1 && k2 < nlo) {
+                sA[lr * LD + lc] = ld_inter<kStream>(Yj + (int64_t)k1 * kRowLen + k2);
+                const int pk1 = k1 == 0 ? 0 : n1 - k1;
+                const int pk2 = k1 == 0 ? (kRowLen - k2) & (kRowLen - 1) : kRowLen - 1 - k2;
+                sB[lr * LD + lc] = ld_inter<kStream>(Yj + (int64_t)pk1 * kRowLen + pk2);
+            }
+        }
+        __syncthreads();
+        if (kDiscard) {
+            const int t = threadIdx.x;
+            if (t < kEpiT1) {
+                const int k1 = k1a + t;
+                if (k1 < n1) discard_l2(Yj + (int64_t)k1 * kRowLen + k2a);
+            } else if (t < 2 * kEpiT1) {
+                const int k1 = k1a + t - kEpiT1;
+                if (k1 < n1 && k1 > 0) discard_l2(Yj + (int64_t)(n1 - k1) * kRowLen + (kRowLen - kEpiT2 - k2a));
+            }
+        }
+        const bool odd = 2 * j + 1 < K;
+        const int64_t o0 = (int64_t)(2 * j) * I, o1 = o0 + I;
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            if (!v1[u] && !v2[u]) continue;
+            const int e = threadIdx.x + u * NT;
+            const float2 A = sA[(e % kEpiT1) * LD + e / kEpiT1];
+            const float2 Bc = sB[(e % kEpiT1) * LD + e / kEpiT1];
+            // X_even = (A + conj(B)) / 2 ; X_odd = (A - conj(B)) / (2i)
+            const float2 j0 = cmulf(make_float2(0.5f * (A.x + Bc.x), 0.5f * (A.y - Bc.y)), sd[u]);
+            const float p0 = norm2f(j0);
             if (J) {
-                if (v1) __stcs(J + o1 + i1, j1);
-                if (v2) __stcs(J + o1 + i2, make_float2(j1.x, -j1.y));
+                if (v1[u]) __stcs(J + o0 + i1[u], j0);
+                if (v2[u]) __stcs(J + o0 + i2[u], make_float2(j0.x, -j0.y));
             }
             if (E) {
-                if (v1) __stcs(E + o1 + i1, p1);
-                if (v2) __stcs(E + o1 + i2, p1);
+                if (v1[u]) __stcs(E + o0 + i1[u], p0);
+                if (v2[u]) __stcs(E + o0 + i2[u], p0);
             }
-            pacc += p1;
+            pacc[u] += p0;
+            if (kF) {
+                const float w0 = c.wsum[2 * j];
+                jk[kF ? j : 0][0] = j0;
+                csum.x += j0.x * w0;
+                csum.y += j0.y * w0;
+            }
+            if (odd) {
+                const float2 j1 = cmulf(make_float2(0.5f * (A.y + Bc.y), -0.5f * (A.x - Bc.x)), sd[u]);
+                if (kF) {
+                    const float w1 = c.wsum[2 * j + 1];
+                    jk[kF ? j : 0][1] = j1;
+                    csum.x += j1.x * w1;
+                    csum.y += j1.y * w1;
+                }
+                const float p1 = norm2f(j1);
+                if (J) {
+                    if (v1[u]) __stcs(J + o1 + i1[u], j1);
+                    if (v2[u]) __stcs(J + o1 + i2[u], make_float2(j1.x, -j1.y));
+                }
+                if (E) {
+                    if (v1[u]) __stcs(E + o1 + i1[u], p1);
+                    if (v2[u]) __stcs(E + o1 + i2[u], p1);
+                }
+                pacc[u] += p1;
+            }
         }
     };
     if constexpr (kF) {
 #pragma unroll
         for (int j = 0; j < kMaxPairs; ++j)
-            if (j < Kp) pair(j);  // fully unrolled: jk stays in registers
+            if (j < Kp) pair(j);  // fully unrolled: jk stays in registers (Kp is uniform: the barriers line up)
     } else {
         for (int j = 0; j < Kp; ++j) pair(j);
     }
-    if (Pout) {
-        const float pv = pacc * (1.0f / (float)K);
-        if (v1) __stcs(Pout + i1, pv);
-        if (v2) __stcs(Pout + i2, pv);
-    }
-    if (kF && Fout) {
-        const float2 ch = make_float2(csum.x / c.wq, csum.y / c.wq);  // line amplitude C at m
-        float res = 0.f;
 #pragma unroll
-        for (int j = 0; j < kMaxPairs; ++j) {
-            if (j >= Kp) break;
+    for (int u = 0; u < PPT; ++u) {
+        if (P) {
+            const float pv = pacc[u] * (1.0f / (float)K);
+            if (v1[u]) __stcs(P + i1[u], pv);
+            if (v2[u]) __stcs(P + i2[u], pv);
+        }
+        if (kF && Fout && (v1[u] || v2[u])) {
+            const float2 ch = make_float2(csum.x / c.wq, csum.y / c.wq);  // line amplitude C at m
+            float res = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (2 * j + h < K) {
-                    const float wk = c.wsum[2 * j + h];
-                    const float rx = jk[j][h].x - ch.x * wk, ry = jk[j][h].y - ch.y * wk;
-                    res += rx * rx + ry * ry;
+            for (int j = 0; j < kMaxPairs; ++j) {
+                if (j >= Kp) break;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (2 * j + h < K) {
+                        const float wk = c.wsum[2 * j + h];
+                        const float rx = jk[j][h].x - ch.x * wk, ry = jk[j][h].y - ch.y * wk;
+                        res += rx * rx + ry * ry;
+                    }
                 }
             }
+            const float fv = (ch.x * ch.x + ch.y * ch.y) * (float)(K - 1) * c.wq / res;
+            if (v1[u]) __stcs(Fout + i1[u], fv);
+            if (v2[u]) __stcs(Fout + i2[u], fv);
         }
-        const float fv = (ch.x * ch.x + ch.y * ch.y) * (float)(K - 1) * c.wq / res;
-        if (v1) __stcs(Fout + i1, fv);
-        if (v2) __stcs(Fout + i2, fv);
     }
 }
 

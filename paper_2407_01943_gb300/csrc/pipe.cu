@@ -7,12 +7,12 @@
 //   S  one 256-cell spread tile                       (ntiles items)
 //   C  cm passes over 256 / cgw columns of one pair  (Kp * 4 cgw / cm items)
 //   R  up to 8 rows of one taper pair                 (Kp * ceil(n1 / 8) items)
-//   E  kEpiItem epilogue positions                    (ceil(n1 (k2max + 1) / kEpiItem) items)
+//   E  one 32 x 16 epilogue tile                      (epi_tiles(n1, k2max, 32) items)
 // A host-built item list orders the items in rounds: round t holds the E items
 // of task t - 3L, the R items of task t - 2L, the C items of task t - L and the
 // S items of task t, so stages of different signals run side by side (compute-
 // bound FFT items next to HBM-bound epilogue items) and the intermediates of a
-// task (g, Z, Xt) are consumed a few rounds after they are written, while they
+// task (g, Z) are consumed a few rounds after they are written, while they
 // are still in L2.  Task t uses workspace slot t mod ring.
 //
 // Scheduling: CTAs claim items in list order with one atomic counter and run
@@ -45,8 +45,6 @@ using packed::Tw32;
 using packed::kRowLen;
 
 constexpr int kPipeThreads = 256;
-constexpr int kEpiPerThread = 2;
-constexpr int kEpiItem = kPipeThreads * kEpiPerThread;
 constexpr int kRowsPerItem = 8;
 constexpr int kSpinCap = 1 << 24;  // iteration cap of one wait (the wall-clock limit normally ends it first)
 
@@ -90,8 +88,7 @@ struct PipeArgs {
     const Ctx* ctxs;
     float2* wg;  // workspace slots
     float2* wz;
-    float2* wx;
-    int64_t sg, sz, sxt;  // slot strides (float2)
+    int64_t sg, sz;  // slot strides (float2)
     int* ctrl;            // [kCtrlWords] then [ntasks][4] completion counters
     int* hstat;           // mapped pinned [abort, status, item]: written when a wait gives up
     unsigned long long* prof;  // NULL, or per stage: [0..3] busy ns, [4..7] items, [8..11] wait ns
@@ -176,26 +173,18 @@ __device__ __forceinline__ void stage_cols(const Ctx& c, const Tw32& tw, const f
 
 // Kept out of line: the row FFT needs all 128 registers the kernel's occupancy of two
 // CTAs per SM allows, and inlined next to the column stage it spills far more.
-__device__ __noinline__ void stage_rows(const Ctx& c, const Tw32& tw, const float2* Zb, float2* Xb, int idx,
-                                        float2* sm) {
+__device__ __noinline__ void stage_rows(const Ctx& c, const Tw32& tw, float2* Zb, int idx, float2* sm) {
     const int nrb = (c.n1 + kRowsPerItem - 1) / kRowsPerItem;
     const int j = idx / nrb, rb = idx - j * nrb;
     const int r0 = rb * kRowsPerItem;
     const int64_t plane = (int64_t)c.n1 * kRowLen;
-    packed::rowfft_rows<kRowsPerItem, false>(c, tw, Zb + j * plane, Xb + j * plane, r0,
-                                             min(kRowsPerItem, c.n1 - r0), sm);
+    packed::rowfft_rows<kRowsPerItem, false>(c, tw, Zb + j * plane, r0, min(kRowsPerItem, c.n1 - r0), sm);
 }
 
-__device__ __forceinline__ void stage_epi(const Ctx& c, const float2* Xb, int idx, float2* J, float* E, float* P) {
-    const int npos = c.n1 * (c.k2max + 1);
-#pragma unroll
-    for (int u = 0; u < kEpiPerThread; ++u) {
-        const int pos = idx * kEpiItem + u * kPipeThreads + threadIdx.x;
-        if (pos < npos) {
-            const int k2 = pos / c.n1;
-            packed::epi_position<false>(c, Xb, pos - k2 * c.n1, k2, J, E, P);
-        }
-    }
+// one 32 x 16 epilogue tile per item (L2-coherent loads; no discards: the ring slot is reused)
+__device__ __forceinline__ void stage_epi(const Ctx& c, const float2* Zb, int idx, float2* J, float* E, float* P,
+                                          float2* sm) {
+    packed::epi_tile<32, kPipeThreads, false, false, false>(c, Zb, idx, J, E, P, nullptr, sm);
 }
 
 __global__ void __launch_bounds__(kPipeThreads, 2) pipe_kernel(PipeArgs a) {
@@ -266,12 +255,11 @@ __global__ void __launch_bounds__(kPipeThreads, 2) pipe_kernel(PipeArgs a) {
         const int slot = s_task.slot;
         float2* gb = a.wg + (int64_t)slot * a.sg;
         float2* Zb = a.wz + (int64_t)slot * a.sz;
-        float2* Xb = a.wx + (int64_t)slot * a.sxt;
         float2* sm = reinterpret_cast<float2*>(smem);
         if (stage == kStageS) stage_spread(c, s_task.x, idx, gb, smem);
         else if (stage == kStageC) stage_cols(c, a.tw, gb, Zb, idx, sm);
-        else if (stage == kStageR) stage_rows(c, a.tw, Zb, Xb, idx, sm);
-        else stage_epi(c, Xb, idx, s_task.J, s_task.E, s_task.P);
+        else if (stage == kStageR) stage_rows(c, a.tw, Zb, idx, sm);
+        else stage_epi(c, Zb, idx, s_task.J, s_task.E, s_task.P, sm);
         // publish completion: the data of S, C and R items is read by other CTAs (fence first);
         // E items only have to have finished reading their slot
         if (stage != kStageE) __threadfence();
@@ -300,7 +288,7 @@ StageCounts stage_counts(const Ctx& c, int ntiles) {
     s.n[kStageS] = ntiles;
     s.n[kStageC] = c.Kp * (4 * c.cgw / c.cm);
     s.n[kStageR] = c.Kp * ((c.n1 + kRowsPerItem - 1) / kRowsPerItem);
-    s.n[kStageE] = (int)(((int64_t)c.n1 * (c.k2max + 1) + kEpiItem - 1) / kEpiItem);
+    s.n[kStageE] = packed::epi_tiles(c.n1, c.k2max, 32);
     return s;
 }
 
@@ -384,8 +372,8 @@ struct PipeLaunch {
     int* h_status = nullptr;  // mapped pinned [abort, status, item] (owned if own_status)
     int* d_status = nullptr;  // its device alias
     bool own_status = false;
-    float2 *wg = nullptr, *wz = nullptr, *wx = nullptr;
-    int64_t sg = 0, sz = 0, sxt = 0;
+    float2 *wg = nullptr, *wz = nullptr;
+    int64_t sg = 0, sz = 0;
     unsigned long long* d_prof = nullptr;  // batch launches: stage accounting (owned), accumulated
     std::vector<void*> owned;  // device buffers owned by this launch
     Tw32 tw;
@@ -496,10 +484,8 @@ m2_status pipe_run(PipeLaunch& L, const float* x0, float2* J0, float* E0, float*
     a.ctxs = L.d_ctxs;
     a.wg = L.wg;
     a.wz = L.wz;
-    a.wx = L.wx;
     a.sg = L.sg;
     a.sz = L.sz;
-    a.sxt = L.sxt;
     a.ctrl = L.d_ctrl;
     a.hstat = L.d_status;
     a.prof = prof;
@@ -549,10 +535,8 @@ m2_status pipe_prepare(m2nufft_plan_s* p, int64_t B) {
     // ring slots: the plan's chunk workspace, slot s = signal s of a chunk
     nl->wg = reinterpret_cast<float2*>(p->d_g);
     nl->wz = reinterpret_cast<float2*>(p->d_Z);
-    nl->wx = reinterpret_cast<float2*>(p->d_X);
     nl->sg = (int64_t)g.kp * g.Lg;
     nl->sz = (int64_t)g.kp * g.nf;
-    nl->sxt = (int64_t)g.kp * g.nf;
     p->pipe_cache.emplace(B, nl.release());
     return M2_OK;
 }
@@ -614,16 +598,13 @@ m2_status pipe_batch_create(m2nufft_plan_s* const* plans, const void* const* xs,
     M2_CUDA_TRY(cudaMalloc(&L->d_prof, 12 * sizeof(unsigned long long)));
     L->owned.push_back(L->d_prof);
     M2_CUDA_TRY(cudaMemset(L->d_prof, 0, 12 * sizeof(unsigned long long)));
-    // ring workspace: g, Z and Xt slots sized for the largest plan
+    // ring workspace: g and Z slots sized for the largest plan
     L->sg = sg;
     L->sz = sz;
-    L->sxt = sz;
     M2_CUDA_TRY(cudaMalloc(&L->wg, sizeof(float2) * (size_t)(sg * ring)));
     L->owned.push_back(L->wg);
     M2_CUDA_TRY(cudaMalloc(&L->wz, sizeof(float2) * (size_t)(sz * ring)));
     L->owned.push_back(L->wz);
-    M2_CUDA_TRY(cudaMalloc(&L->wx, sizeof(float2) * (size_t)(sz * ring)));
-    L->owned.push_back(L->wx);
     *out = L.release();
     return M2_OK;
 }

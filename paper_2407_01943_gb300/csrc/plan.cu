@@ -1220,11 +1220,6 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         M2_TRY_OR(pb.alloc(&dZ, (size_t)g.chunk * g.kp * g.nf));
         p->d_g = dg;
         p->d_Z = dZ;
-        if (g.path >= 2) {
-            float2* dX = nullptr;
-            M2_TRY_OR(pb.alloc(&dX, (size_t)g.chunk * g.kp * g.nf));
-            p->d_X = dX;
-        }
     } else {
         double2 *dg = nullptr, *dZ = nullptr;
         M2_TRY_OR(pb.alloc(&dg, (size_t)g.chunk * g.kp * g.Lg));
