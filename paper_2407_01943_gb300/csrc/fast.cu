@@ -134,13 +134,14 @@ __global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1)) rowfft_kernel(Ctx c,
 }
 
 // grid (epi_tiles(n1, k2max, T1), nb): one T1 x 16 tile of positions per CTA (and its partners);
-// kF adds the F-statistic output (32 x 16 tiles, 512 threads, one position each)
+// kF adds the F-statistic output (16 x 16 tiles, 256 threads, one position each: every J_k of
+// the position stays in registers; 256 threads at <= 64 registers keep four CTAs per SM)
 constexpr int kEpiT1 = 32;
 constexpr int kEpiMinBlocks = 4;
-__host__ __device__ constexpr int epi_t1(bool kF) { return kF ? 32 : kEpiT1; }
+__host__ __device__ constexpr int epi_t1(bool kF) { return kF ? 16 : kEpiT1; }
 __host__ __device__ constexpr int epi_threads(bool kF) { return 16 * epi_t1(kF); }  // one position per thread
 template <bool kF>
-__global__ void __launch_bounds__(epi_threads(kF), kF ? 1 : kEpiMinBlocks) epi_kernel(Ctx c, const float2* __restrict__ Y,
+__global__ void __launch_bounds__(epi_threads(kF), kF ? 4 : kEpiMinBlocks) epi_kernel(Ctx c, const float2* __restrict__ Y,
                                                               float2* __restrict__ J, float* __restrict__ E,
                                                               float* __restrict__ P, float* __restrict__ F) {
     __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(epi_t1(kF)) / sizeof(float2)];
