@@ -41,6 +41,7 @@ template <> struct CT<double> { using C = double2; };
 constexpr int kSpreadTile = 256;
 // Points staged in shared memory per chunk of the spread kernel.
 constexpr int kSpreadChunk = 256;
+constexpr int kLanes = 2;  // packed path: consecutive chunks overlapped on this many internal streams
 // Largest K the exec kernels are instantiated for.
 constexpr int kMaxK = 16;
 
@@ -139,6 +140,7 @@ unsigned long long* pipe_last_batch_profile(int* device);
 struct m2nufft_plan_s {
     m2::Geometry g;
     int device = 0;
+    int sm_count = 0;  // multiprocessors of the device (grid sizing)
     int precision = 32;
     double fs = 1.0, f_w = 0.0;
     double tol = 0.0;
@@ -180,10 +182,10 @@ struct m2nufft_plan_s {
                                    // column DFTs, then in place the in-band row transforms)
     // packed path, execs of more than one chunk: a second workspace and two internal streams, so
     // that chunk c's epilogue (HBM-bound) overlaps chunk c+1's spread and FFTs (issue-bound)
-    void* d_g2 = nullptr;
-    void* d_Z2 = nullptr;
-    cudaStream_t lane_st[2] = {nullptr, nullptr};
-    cudaEvent_t lane_ev[2] = {nullptr, nullptr};
+    void* lane_g[m2::kLanes] = {};  // lane L > 0 workspace (lane 0 uses d_g / d_Z)
+    void* lane_Z[m2::kLanes] = {};
+    cudaStream_t lane_st[m2::kLanes] = {};
+    cudaEvent_t lane_ev[m2::kLanes] = {};
     cudaEvent_t fork_ev = nullptr;
     std::vector<void*> allocations;
     // persistent pipelined path: launch configurations by batch size, and a mapped pinned

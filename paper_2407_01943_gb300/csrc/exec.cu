@@ -375,22 +375,26 @@ m2_status exec_chunk(m2nufft_plan_s* p, const R* x, int nb, typename CT<R>::C* J
     return M2_OK;
 }
 
-// Second workspace and the two internal streams of a packed plan, created on first use (an exec
-// of more than one chunk; never during stream capture, where B = 1).
+// Workspaces of lanes 1 .. kLanes - 1 and the internal streams of a packed plan, created on first
+// use (an exec of more than one chunk; never during stream capture, where B = 1).
 m2_status ensure_lanes(m2nufft_plan_s* p) {
     if (p->lane_st[0]) return M2_OK;
     const Geometry& g = p->g;
     const size_t ng = (size_t)g.chunk * g.kp * g.Lg, nz = (size_t)g.chunk * g.kp * g.nf;
-    void *a = nullptr, *b = nullptr;
-    M2_CUDA_TRY(cudaMalloc(&a, sizeof(float2) * ng));
-    p->allocations.push_back(a);
-    M2_CUDA_TRY(cudaMalloc(&b, sizeof(float2) * nz));
-    p->allocations.push_back(b);
-    p->device_bytes += sizeof(float2) * (ng + nz);
-    p->d_g2 = a;
-    p->d_Z2 = b;
+    p->lane_g[0] = p->d_g;
+    p->lane_Z[0] = p->d_Z;
+    for (int L = 1; L < kLanes; ++L) {
+        void *a = nullptr, *b = nullptr;
+        M2_CUDA_TRY(cudaMalloc(&a, sizeof(float2) * ng));
+        p->allocations.push_back(a);
+        M2_CUDA_TRY(cudaMalloc(&b, sizeof(float2) * nz));
+        p->allocations.push_back(b);
+        p->device_bytes += sizeof(float2) * (ng + nz);
+        p->lane_g[L] = a;
+        p->lane_Z[L] = b;
+    }
     M2_CUDA_TRY(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
-    for (int L = 0; L < 2; ++L) {
+    for (int L = 0; L < kLanes; ++L) {
         M2_CUDA_TRY(cudaStreamCreateWithFlags(&p->lane_st[L], cudaStreamNonBlocking));
         M2_CUDA_TRY(cudaEventCreateWithFlags(&p->lane_ev[L], cudaEventDisableTiming));
     }
@@ -445,19 +449,19 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     }
     if constexpr (std::is_same<R, float>::value) {
         if (g.path >= 2 && B > g.chunk && !p->timing) {
-            // two lanes: chunk c on lane c % 2 with that lane's workspace, forked from and joined
-            // back to the caller's stream
+            // kLanes lanes: chunk c on lane c % kLanes with that lane's workspace, forked from and
+            // joined back to the caller's stream
             M2_TRY(ensure_lanes(p));
             M2_CUDA_TRY(cudaEventRecord(p->fork_ev, st));
-            for (int L = 0; L < 2; ++L) M2_CUDA_TRY(cudaStreamWaitEvent(p->lane_st[L], p->fork_ev, 0));
+            for (int L = 0; L < kLanes; ++L) M2_CUDA_TRY(cudaStreamWaitEvent(p->lane_st[L], p->fork_ev, 0));
             int c = 0;
             for (int64_t b0 = 0; b0 < B; b0 += g.chunk, ++c) {
                 const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
                 M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, J ? J + b0 * g.K * g.I : nullptr,
                                        E ? E + b0 * g.K * g.I : nullptr, P ? P + b0 * g.I : nullptr,
-                                       F ? F + b0 * g.I : nullptr, p->lane_st[c & 1], c & 1));
+                                       F ? F + b0 * g.I : nullptr, p->lane_st[c % kLanes], c % kLanes));
             }
-            for (int L = 0; L < 2; ++L) {
+            for (int L = 0; L < kLanes; ++L) {
                 M2_CUDA_TRY(cudaEventRecord(p->lane_ev[L], p->lane_st[L]));
                 M2_CUDA_TRY(cudaStreamWaitEvent(st, p->lane_ev[L], 0));
             }

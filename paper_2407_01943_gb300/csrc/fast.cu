@@ -92,24 +92,30 @@ using packed::Tw32;
 using packed::kColWarps;
 using packed::kRowLen;
 
-// grid (ntiles, ceil(nb / SB)): one 256-cell tile of up to SB signals per CTA (SB = 4, or 2 for
-// five or more taper pairs, which keeps the accumulators in registers)
+// grid (ntiles, ceil(nb / SB)): one 256-cell tile of up to SB signals per CTA (SB <= 4, or <= 2
+// for five or more taper pairs, which keeps the accumulators in registers); the tile's points are
+// staged once for its SB signals
 __host__ __device__ constexpr int spread_signals(int KP) { return KP <= 4 ? 4 : 2; }
-template <int KP>
+template <int KP, int SB>
 __global__ void __launch_bounds__(kSpreadTile) spread_packed_kernel(Ctx c, const float* __restrict__ x, int nb,
                                                                     float2* __restrict__ g) {
-    constexpr int SB = spread_signals(KP);
     __shared__ __align__(16) unsigned char smem[packed::spread_multi_smem_bytes(KP, SB)];
     const int b0 = blockIdx.y * SB;
     packed::spread_tile_multi<KP, SB>(c, x + (int64_t)b0 * c.N, min(SB, nb - b0), blockIdx.x,
                                       g + (int64_t)b0 * c.Kp * c.Lg, smem);
 }
 
+// Signals per CTA: the most (sharing the staging of a tile's points) that still give the launch
+// about two CTAs per SM; fewer when a chunk is small.
 template <int KP>
-void launch_spread_packed(const Ctx& c, const float* x, int nb, float2* g, cudaStream_t st) {
-    constexpr int SB = spread_signals(KP);
-    dim3 grid((unsigned)((c.Lg + kSpreadTile - 1) / kSpreadTile), (unsigned)((nb + SB - 1) / SB));
-    spread_packed_kernel<KP><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
+void launch_spread_packed(const Ctx& c, const float* x, int nb, float2* g, int sm_count, cudaStream_t st) {
+    const int64_t ntiles = (c.Lg + kSpreadTile - 1) / kSpreadTile;
+    int sb = spread_signals(KP);
+    while (sb > 1 && ntiles * ((nb + sb - 1) / sb) < 2 * (int64_t)sm_count) sb /= 2;
+    dim3 grid((unsigned)ntiles, (unsigned)((nb + sb - 1) / sb));
+    if (sb >= 4) spread_packed_kernel<KP, spread_signals(KP) >= 4 ? 4 : 2><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
+    else if (sb == 2) spread_packed_kernel<KP, 2><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
+    else spread_packed_kernel<KP, 1><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
 }
 
 // grid (1024 / 32, Kp, nb): 32 columns of one taper pair per CTA of 4 warps
@@ -188,15 +194,15 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
     const Geometry& g = p->g;
     static const Tw32 tw = packed::make_tw32();
     const Ctx c = packed_ctx(p);
-    // workspace of lane 0 (the plan's) or lane 1 (the second half, for overlapped chunks)
-    float2* dg = reinterpret_cast<float2*>(lane ? p->d_g2 : p->d_g);
-    float2* dZ = reinterpret_cast<float2*>(lane ? p->d_Z2 : p->d_Z);
+    // workspace of lane 0 (the plan's) or of lane L > 0 (for overlapped chunks)
+    float2* dg = reinterpret_cast<float2*>(lane ? p->lane_g[lane] : p->d_g);
+    float2* dZ = reinterpret_cast<float2*>(lane ? p->lane_Z[lane] : p->d_Z);
 
     mark(p, 0, 0, st);
     {
-        if (g.kp <= 2) launch_spread_packed<2>(c, x, nb, dg, st);
-        else if (g.kp <= 4) launch_spread_packed<4>(c, x, nb, dg, st);
-        else launch_spread_packed<8>(c, x, nb, dg, st);
+        if (g.kp <= 2) launch_spread_packed<2>(c, x, nb, dg, p->sm_count, st);
+        else if (g.kp <= 4) launch_spread_packed<4>(c, x, nb, dg, p->sm_count, st);
+        else launch_spread_packed<8>(c, x, nb, dg, p->sm_count, st);
         M2_CUDA_TRY(cudaGetLastError());
     }
     mark(p, 0, 1, st);

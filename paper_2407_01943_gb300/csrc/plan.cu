@@ -331,7 +331,7 @@ void free_plan(m2nufft_plan_s* p) {
         DeviceGuard guard(p->device);
         cudaDeviceSynchronize();
         for (auto& kv : p->pipe_cache) pipe_free(kv.second);
-        for (int L = 0; L < 2; ++L) {
+        for (int L = 0; L < kLanes; ++L) {
             if (p->lane_st[L]) cudaStreamDestroy(p->lane_st[L]);
             if (p->lane_ev[L]) cudaEventDestroy(p->lane_ev[L]);
         }
@@ -707,8 +707,11 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     DeviceGuard guard(dev);
     M2_TRY(init_device_kernels(dev));
 
+    int nsm = 0;
+    M2_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     auto* p = new m2nufft_plan_s();
     p->device = dev;
+    p->sm_count = nsm;
     p->precision = opts.precision;
     p->fs = fs;
     p->f_w = f_w;
