@@ -32,7 +32,6 @@ namespace packed {
 constexpr int kRowLen = 1024;  // n2
 constexpr int kRowPad = 1060;  // per-warp transpose / row buffer: >= 32 x 33 (padded transpose)
 constexpr int kColWarps = 4;   // warps per 32-column group of the column pass
-constexpr int kRowsPerGroup = 8;  // rows per row-FFT work item (one warp each)
 
 struct Tw32 {
     float2 w[16];  // exp(-i 2 pi e / 32), e < 16

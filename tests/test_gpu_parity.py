@@ -440,13 +440,21 @@ def test_pipe_matches_four_kernels_full_size(dev, B):
 
 def test_default_path_selection(dev):
     """Automatic choice: packed four-kernel path for qualifying FP32 plans, the persistent
-    kernel on request, the generic path for FP64."""
+    kernel on request, the generic path for FP64; the packed chunk is 4 to 16 signals by the
+    workspace rule (4 for this size) and exactly max_batch when given (at most 64)."""
     wl = synth.workload("jitter16k")
     w = seeded_tapers(wl.K, wl.N, 1)
     args = (wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I)
-    assert pkg.Plan(*args, precision=32, tapers=w).info["path"] == 2
+    p2 = pkg.Plan(*args, precision=32, tapers=w)
+    assert p2.info["path"] == 2 and p2.info["chunk"] == 4
+    assert pkg.Plan(*args, precision=32, tapers=w, max_batch=24).info["chunk"] == 24
+    assert pkg.Plan(*args, precision=32, tapers=w, max_batch=500).info["chunk"] == 64
     assert pkg.Plan(*args, precision=32, tapers=w, path=3).info["path"] == 3
     assert pkg.Plan(*args, precision=64, tapers=w).info["path"] == 1
+    small = synth.workload("grid1024")
+    ws = seeded_tapers(small.K, small.N, 1)
+    assert pkg.Plan(small.t, small.fs, small.f_w, small.K, small.f_lo, small.df, small.I, precision=32,
+                    tapers=ws).info["chunk"] == 16
 
 
 def test_pipe_bounded_wait_reports_timeout(dev):
