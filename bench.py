@@ -280,7 +280,7 @@ def run_reference(args):
 
 
 def run_uneven(args):
-    """Uneven batch (SURVEY config 3): nsig signals with their own sampling patterns (grid length
+    """Uneven batch (2048 signals by default): nsig signals with their own sampling patterns (grid length
     log-uniform in [1024, 16384], Markov gaps, K in {4,6,8}, I = 4G) through m2nufft_exec_batch
     (one cached CUDA graph per call) against the plain per-signal path (one m2nufft_exec per
     signal on one stream).  Plans use taper-shaped inputs instead of 2048 dense GEPs; the exec
@@ -501,7 +501,7 @@ def run_subopt(args):
 
 
 def run_serve(args):
-    """Serving (SURVEY config 5): Poisson arrivals of PSD requests over 64 fixed sampling patterns
+    """Serving: Poisson arrivals of PSD requests over 64 fixed sampling patterns
     (grid length uniform in [2048, 16384], jittered or Bernoulli-missing 10-30%, K = 8, I = 4G),
     plans cached before the trace, 40 GB device-memory budget; continuous batching (4 slots,
     up to 16 requests per launch) against the plain per-request path.  The 64 plans take their
