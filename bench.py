@@ -668,7 +668,11 @@ def run_ours(args):
     units_per_signal = wl.K * wl.N * wl.I
     value = job_throughput(B * units_per_signal, args.steps, world, total_ms)
     pipelined = info["path"] == 3
-    launches = args.steps * (1 if pipelined else chunks * (4 if info["path"] == 2 else 3))
+    per_step = chunks * (4 if info["path"] == 2 else 3)
+    kp = (wl.K + 1) // 2
+    if info["path"] == 2 and chunks > 1 and B * kp * info["rows"] * 1024 * 8 <= (256 << 20):
+        per_step = 1 + 3 * chunks  # one spread launch for all signals, then three kernels per chunk
+    launches = args.steps * (1 if pipelined else per_step)
     per_launch = B if pipelined else min(B, info["chunk"])
 
     # ---- per-kernel roofline from the live event timing ----

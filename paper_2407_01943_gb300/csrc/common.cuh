@@ -100,7 +100,9 @@ m2_status spline_tapers(const std::vector<double>& ts, double fmax, double fw, i
                         std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
-                          cudaStream_t st, int lane = 0);
+                          cudaStream_t st, int lane = 0, const float2* g_pre = nullptr);
+// spread grids of nb signals (packed path) into g_out [nb][Kp][Lg]
+m2_status spread_fast(m2nufft_plan_s* p, const float* x, int nb, float2* g_out, cudaStream_t st);
 // Stage-batched executor of uneven batches of packed plans (hbatch.cu).
 struct HBatch;
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
@@ -182,6 +184,8 @@ struct m2nufft_plan_s {
                                    // column DFTs, then in place the in-band row transforms)
     // packed path, execs of more than one chunk: a second workspace and two internal streams, so
     // that chunk c's epilogue (HBM-bound) overlaps chunk c+1's spread and FFTs (issue-bound)
+    void* d_gall = nullptr;  // packed path, multi-chunk execs: the spread grids of all signals
+    int64_t gall_signals = 0;
     void* lane_g[m2::kLanes] = {};  // lane L > 0 workspace (lane 0 uses d_g / d_Z)
     void* lane_Z[m2::kLanes] = {};
     cudaStream_t lane_st[m2::kLanes] = {};

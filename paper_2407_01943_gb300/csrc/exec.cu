@@ -452,6 +452,26 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
             // kLanes lanes: chunk c on lane c % kLanes with that lane's workspace, forked from and
             // joined back to the caller's stream
             M2_TRY(ensure_lanes(p));
+            // the spread grids of all signals in one launch (the spread is a fixed-latency chain
+            // of dependent loads, cheaper once than once per chunk), while they fit in 256 MiB
+            const size_t gsig = sizeof(float2) * (size_t)g.kp * (size_t)g.Lg;
+            const float2* gall = nullptr;
+            if ((size_t)B * gsig <= (size_t(256) << 20)) {
+                if (p->gall_signals < B) {
+                    if (p->d_gall) {
+                        M2_CUDA_TRY(cudaStreamSynchronize(st));
+                        cudaFree(p->d_gall);
+                        p->device_bytes -= gsig * (size_t)p->gall_signals;
+                        p->d_gall = nullptr;
+                        p->gall_signals = 0;
+                    }
+                    M2_CUDA_TRY(cudaMalloc(&p->d_gall, gsig * (size_t)B));
+                    p->gall_signals = B;
+                    p->device_bytes += gsig * (size_t)B;
+                }
+                M2_TRY(spread_fast(p, x, (int)B, reinterpret_cast<float2*>(p->d_gall), st));
+                gall = reinterpret_cast<const float2*>(p->d_gall);
+            }
             M2_CUDA_TRY(cudaEventRecord(p->fork_ev, st));
             for (int L = 0; L < kLanes; ++L) M2_CUDA_TRY(cudaStreamWaitEvent(p->lane_st[L], p->fork_ev, 0));
             int c = 0;
@@ -459,7 +479,8 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
                 const int nb = (int)std::min<int64_t>(g.chunk, B - b0);
                 M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, J ? J + b0 * g.K * g.I : nullptr,
                                        E ? E + b0 * g.K * g.I : nullptr, P ? P + b0 * g.I : nullptr,
-                                       F ? F + b0 * g.I : nullptr, p->lane_st[c % kLanes], c % kLanes));
+                                       F ? F + b0 * g.I : nullptr, p->lane_st[c % kLanes], c % kLanes,
+                                       gall ? gall + b0 * g.kp * g.Lg : nullptr));
             }
             for (int L = 0; L < kLanes; ++L) {
                 M2_CUDA_TRY(cudaEventRecord(p->lane_ev[L], p->lane_st[L]));

@@ -189,15 +189,27 @@ m2_status init_fast_kernels(int smem_optin) {
     return M2_OK;
 }
 
+m2_status spread_fast(m2nufft_plan_s* p, const float* x, int nb, float2* g_out, cudaStream_t st) {
+    const Geometry& g = p->g;
+    const Ctx c = packed_ctx(p);
+    if (g.kp <= 2) launch_spread_packed<2>(c, x, nb, g_out, p->sm_count, st);
+    else if (g.kp <= 4) launch_spread_packed<4>(c, x, nb, g_out, p->sm_count, st);
+    else launch_spread_packed<8>(c, x, nb, g_out, p->sm_count, st);
+    M2_CUDA_TRY(cudaGetLastError());
+    return M2_OK;
+}
+
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
-                          cudaStream_t st, int lane) {
+                          cudaStream_t st, int lane, const float2* g_pre) {
     const Geometry& g = p->g;
     static const Tw32 tw = packed::make_tw32();
     const Ctx c = packed_ctx(p);
     // workspace of lane 0 (the plan's) or of lane L > 0 (for overlapped chunks)
     float2* dg = reinterpret_cast<float2*>(lane ? p->lane_g[lane] : p->d_g);
     float2* dZ = reinterpret_cast<float2*>(lane ? p->lane_Z[lane] : p->d_Z);
+    if (g_pre) dg = const_cast<float2*>(g_pre);  // spread grids made beforehand for the whole exec
 
+    if (!g_pre) {
     mark(p, 0, 0, st);
     {
         if (g.kp <= 2) launch_spread_packed<2>(c, x, nb, dg, p->sm_count, st);
@@ -206,6 +218,7 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
         M2_CUDA_TRY(cudaGetLastError());
     }
     mark(p, 0, 1, st);
+    }
 
     mark(p, 1, 0, st);
     switch (g.colF) {
