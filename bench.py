@@ -781,8 +781,9 @@ def run_ours(args):
                        "kernel_width": info["width"], "chunk": info["chunk"], "exec_path": info["path"],
                        "autotune": ([{"path": r[0], "sigma": r[1], "max_batch": r[2], "ms": r[3]}
                                      for r in plan.tuning()] if args.tune else None),
-                       "kernel_timing": ("separate instrumented pass (chunks one after the other); the timed "
-                                         "steps overlap consecutive chunks on two streams"
+                       "kernel_timing": ("separate instrumented pass (chunks one after the other, each with its "
+                                         "own spread launch); the timed steps spread all signals in one launch "
+                                         "and overlap consecutive chunks on two streams"
                                          if separate_kernel_pass else "instrumented timed steps"),
                        "l2": "flushed between timed steps (512 MiB write + read-back)", "parallelism": f"replicas x{world}"},
             "gpu_launches": launches,
