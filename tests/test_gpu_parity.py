@@ -845,3 +845,21 @@ def test_autotune_leaves_generic_plans_untuned(dev):
     w = seeded_tapers(wl.K, wl.N, 8)
     plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=64, tapers=w, tune=True)
     assert plan.info["path"] == 1 and plan.tuning() == []
+
+
+def test_multichunk_spread_buffer_reuse_bitwise(dev):
+    """Execs of several chunks spread all their signals in one launch into a buffer the plan keeps
+    and grows: B = 9, then 20, then 5 on one plan give, signal by signal, the same bits as execs
+    of one signal (spread per chunk, one signal per CTA)."""
+    wl = synth.workload("jitter16k", batch=20)
+    w = seeded_tapers(wl.K, wl.N, 13)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=2)
+    assert plan.info["chunk"] < 9
+    xt = torch.from_numpy(wl.x.astype(np.float32)).to(dev)
+    alone = [plan.run(xt[b:b + 1], want=("J", "P")) for b in range(20)]
+    for B in (9, 20, 5):
+        out = plan.run(xt[:B], want=("J", "P"))
+        torch.cuda.synchronize()
+        for b in range(B):
+            assert torch.equal(out["J"][b], alone[b]["J"][0]), (B, b)
+            assert torch.equal(out["P"][b], alone[b]["P"][0]), (B, b)
