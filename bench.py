@@ -670,7 +670,9 @@ def run_ours(args):
     pipelined = info["path"] == 3
     per_step = chunks * (4 if info["path"] == 2 else 3)
     kp = (wl.K + 1) // 2
-    if info["path"] == 2 and chunks > 1 and B * kp * info["rows"] * 1024 * 8 <= (256 << 20):
+    # execs of several chunks spread all their signals in one launch (grids up to 256 MiB)
+    hoisted = info["path"] == 2 and chunks > 1 and B * kp * info["rows"] * 1024 * 8 <= (256 << 20)
+    if hoisted:
         per_step = 1 + 3 * chunks  # one spread launch for all signals, then three kernels per chunk
     launches = args.steps * (1 if pipelined else per_step)
     per_launch = B if pipelined else min(B, info["chunk"])
@@ -683,7 +685,7 @@ def run_ours(args):
         if klaunch[i] == 0:
             continue
         avg_ms = kms[i] / klaunch[i]
-        byts = algorithmic_bytes(info, n, per_launch, csz, rsz, args.outputs)
+        byts = algorithmic_bytes(info, n, B if (hoisted and n == "spread") else per_launch, csz, rsz, args.outputs)
         kern[n] = {"launches": int(klaunch[i]), "total_ms": float(kms[i]), "avg_us": 1e3 * avg_ms,
                    "alg_bytes_per_launch": byts, "gbs": byts / (avg_ms * 1e-3) / 1e9,
                    "share": float(kms[i] / max(sum(kms), 1e-12))}
@@ -781,9 +783,9 @@ def run_ours(args):
                        "kernel_width": info["width"], "chunk": info["chunk"], "exec_path": info["path"],
                        "autotune": ([{"path": r[0], "sigma": r[1], "max_batch": r[2], "ms": r[3]}
                                      for r in plan.tuning()] if args.tune else None),
-                       "kernel_timing": ("separate instrumented pass (chunks one after the other, each with its "
-                                         "own spread launch); the timed steps spread all signals in one launch "
-                                         "and overlap consecutive chunks on two streams"
+                       "kernel_timing": ("separate instrumented pass (one spread launch for all signals, then the "
+                                         "chunks one after the other); the timed steps overlap consecutive "
+                                         "chunks on two streams"
                                          if separate_kernel_pass else "instrumented timed steps"),
                        "l2": "flushed between timed steps (512 MiB write + read-back)", "parallelism": f"replicas x{world}"},
             "gpu_launches": launches,

@@ -447,15 +447,13 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
         p->allocations.push_back(p->d_Jscratch);
         p->device_bytes += sizeof(C) * (size_t)g.chunk * g.K * g.I;
     }
+    const float2* gall = nullptr;
     if constexpr (std::is_same<R, float>::value) {
-        if (g.path >= 2 && B > g.chunk && !p->timing) {
-            // kLanes lanes: chunk c on lane c % kLanes with that lane's workspace, forked from and
-            // joined back to the caller's stream
-            M2_TRY(ensure_lanes(p));
-            // the spread grids of all signals in one launch (the spread is a fixed-latency chain
-            // of dependent loads, cheaper once than once per chunk), while they fit in 256 MiB
+        // multi-chunk execs of the packed path: the spread grids of all signals in one launch (the
+        // spread is a fixed-latency chain of dependent loads, cheaper once than once per chunk),
+        // while they fit in 256 MiB
+        if (g.path >= 2 && B > g.chunk) {
             const size_t gsig = sizeof(float2) * (size_t)g.kp * (size_t)g.Lg;
-            const float2* gall = nullptr;
             if ((size_t)B * gsig <= (size_t(256) << 20)) {
                 if (p->gall_signals < B) {
                     if (p->d_gall) {
@@ -469,9 +467,16 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
                     p->gall_signals = B;
                     p->device_bytes += gsig * (size_t)B;
                 }
+                mark(p, 0, 0, st);
                 M2_TRY(spread_fast(p, x, (int)B, reinterpret_cast<float2*>(p->d_gall), st));
+                mark(p, 0, 1, st);
                 gall = reinterpret_cast<const float2*>(p->d_gall);
             }
+        }
+        if (g.path >= 2 && B > g.chunk && !p->timing) {
+            // kLanes lanes: chunk c on lane c % kLanes with that lane's workspace, forked from and
+            // joined back to the caller's stream
+            M2_TRY(ensure_lanes(p));
             M2_CUDA_TRY(cudaEventRecord(p->fork_ev, st));
             for (int L = 0; L < kLanes; ++L) M2_CUDA_TRY(cudaStreamWaitEvent(p->lane_st[L], p->fork_ev, 0));
             int c = 0;
@@ -497,7 +502,8 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
         R* Fc = F ? F + b0 * g.I : nullptr;
         if constexpr (std::is_same<R, float>::value) {
             if (g.path >= 2) {
-                M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, Jc, Ec, Pc, Fc, st));
+                M2_TRY(exec_fast_chunk(p, x + b0 * g.N, nb, Jc, Ec, Pc, Fc, st, 0,
+                                       gall ? gall + b0 * g.kp * g.Lg : nullptr));
                 continue;
             }
         }
