@@ -457,7 +457,8 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
             if ((size_t)B * gsig <= (size_t(256) << 20)) {
                 if (p->gall_signals < B) {
                     if (p->d_gall) {
-                        M2_CUDA_TRY(cudaStreamSynchronize(st));
+                        // growing (rare): no earlier exec, on whatever stream, may still read it
+                        M2_CUDA_TRY(cudaDeviceSynchronize());
                         cudaFree(p->d_gall);
                         p->device_bytes -= gsig * (size_t)p->gall_signals;
                         p->d_gall = nullptr;
