@@ -212,6 +212,13 @@ m2_status m2nufft_plan_subband(const double* t, int64_t N, double fs, double f_w
  * reported here; device faults surface at the caller's next synchronisation.
  * Calls on one plan must not overlap on the device (they share the plan's
  * workspace); order them on one stream or synchronise between streams.
+ * Path 2 with B above the plan's chunk: the spread grids of all B signals are
+ * made in one launch first (kept by the plan, B * ceil(K/2) * rows * 1024
+ * complex, up to 256 MiB; larger batches spread per chunk), then the chunks run
+ * alternately on two internal streams with a second chunk workspace, forked
+ * from and joined back to `stream`.  Both buffers are allocated on first use
+ * (the grid buffer grows with B, after a device synchronisation), so the first
+ * such call is not capturable into a CUDA graph.
  * Path 3 runs all B signals in one launch; the first call for a new B builds
  * that launch's work list (synchronous upload, not allowed during stream
  * capture).  Its inter-CTA waits are bounded (2 s each): a launch that gave up
