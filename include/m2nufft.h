@@ -217,8 +217,9 @@ m2_status m2nufft_plan_subband(const double* t, int64_t N, double fs, double f_w
  * complex, up to 256 MiB; larger batches spread per chunk), then the chunks run
  * alternately on two internal streams with a second chunk workspace, forked
  * from and joined back to `stream`.  Both buffers are allocated on first use
- * (the grid buffer grows with B, after a device synchronisation), so the first
- * such call is not capturable into a CUDA graph.
+ * (the grid buffer grows with B: before freeing the old one, the call waits on
+ * the host for this plan's last exec that read it), so the first such call, and
+ * a call that grows the buffer, is not capturable into a CUDA graph.
  * Path 3 runs all B signals in one launch; the first call for a new B builds
  * that launch's work list (synchronous upload, not allowed during stream
  * capture).  Its inter-CTA waits are bounded (2 s each): a launch that gave up
@@ -326,9 +327,10 @@ m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* launches);
 m2_status m2nufft_get_pipe_profile(m2nufft_plan_t p, double* busy_ms, double* wait_ms, int64_t* items);
 
 /*
- * Leakage estimate without a plan and without allocating (the paper has no
- * counterpart to this entry point; it computes the same L-hat / E-hat as the
- * plan, App. B Eq. lambda_hat_ki, by the direct pair sum).
+ * Leakage estimate without a plan and without allocating.  The paper has no
+ * counterpart to this entry point: it computes the same L-hat / E-hat as
+ * m2nufft_get_leakage returns for a plan with these tapers and eigenvalues,
+ * by the direct pair sum.
  *
  * For callers that may not call cudaMalloc: code running where the device
  * allocator is off limits, e.g. worker threads of a host that reserves all
@@ -353,11 +355,14 @@ m2_status m2nufft_get_pipe_profile(m2nufft_plan_t p, double* busy_ms, double* wa
  *   stream  cudaStream_t (NULL = legacy default stream); asynchronous
  * Work is O(N^2 I K).  The scratch holds ceil(N/64) partial sums of K x I
  * doubles: calls needing more than 32 MiB return M2_ERR_ARG with a message.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's partial sums (each call writes every entry it later reads), so
- * calls that overlap on the GPU race: order them on one stream.
+ * Each call made outside stream capture looks up the scratch array's device
+ * address on the current device (cudaGetSymbolAddress); a call on a capturing
+ * stream uses the address found by the last call on that device outside
+ * capture, so the first call on a device must come before any stream capture
+ * (otherwise M2_ERR_ARG), and a capture made after cudaDeviceReset needs one
+ * uncaptured call first.  All calls share the one array, which keeps the last
+ * call's partial sums (each call writes every entry it later reads), so calls
+ * that overlap on the GPU race: order them on one stream.
  */
 m2_status m2nufft_leakage_static(const double* t, int64_t N, double fs, double f_w, int K,
                                  const m2_fgrid* fc, const double* w, const double* lambda,

@@ -186,6 +186,7 @@ struct m2nufft_plan_s {
     // that chunk c's epilogue (HBM-bound) overlaps chunk c+1's spread and FFTs (issue-bound)
     void* d_gall = nullptr;  // packed path, multi-chunk execs: the spread grids of all signals
     int64_t gall_signals = 0;
+    cudaEvent_t gall_ev = nullptr;  // recorded on the caller's stream after each exec that read d_gall
     void* lane_g[m2::kLanes] = {};  // lane L > 0 workspace (lane 0 uses d_g / d_Z)
     void* lane_Z[m2::kLanes] = {};
     cudaStream_t lane_st[m2::kLanes] = {};

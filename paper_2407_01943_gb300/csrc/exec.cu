@@ -457,13 +457,16 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
             if ((size_t)B * gsig <= (size_t(256) << 20)) {
                 if (p->gall_signals < B) {
                     if (p->d_gall) {
-                        // growing (rare): no earlier exec, on whatever stream, may still read it
-                        M2_CUDA_TRY(cudaDeviceSynchronize());
+                        // growing (rare): the last exec that read the old buffer (every reader is
+                        // joined back to its caller's stream before gall_ev is recorded there) must
+                        // be done before it is freed; other plans and streams are not waited for
+                        M2_CUDA_TRY(cudaEventSynchronize(p->gall_ev));
                         cudaFree(p->d_gall);
                         p->device_bytes -= gsig * (size_t)p->gall_signals;
                         p->d_gall = nullptr;
                         p->gall_signals = 0;
                     }
+                    if (!p->gall_ev) M2_CUDA_TRY(cudaEventCreateWithFlags(&p->gall_ev, cudaEventDisableTiming));
                     M2_CUDA_TRY(cudaMalloc(&p->d_gall, gsig * (size_t)B));
                     p->gall_signals = B;
                     p->device_bytes += gsig * (size_t)B;
@@ -492,6 +495,7 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
                 M2_CUDA_TRY(cudaEventRecord(p->lane_ev[L], p->lane_st[L]));
                 M2_CUDA_TRY(cudaStreamWaitEvent(st, p->lane_ev[L], 0));
             }
+            if (gall) M2_CUDA_TRY(cudaEventRecord(p->gall_ev, st));
             return M2_OK;
         }
     }
@@ -516,6 +520,7 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
             M2_CUDA_TRY(cudaGetLastError());
         }
     }
+    if (gall) M2_CUDA_TRY(cudaEventRecord(p->gall_ev, st));
     return M2_OK;
 }
 

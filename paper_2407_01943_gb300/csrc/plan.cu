@@ -337,6 +337,7 @@ void free_plan(m2nufft_plan_s* p) {
         }
         if (p->fork_ev) cudaEventDestroy(p->fork_ev);
         if (p->d_gall) cudaFree(p->d_gall);
+        if (p->gall_ev) cudaEventDestroy(p->gall_ev);
         if (p->pipe_status) cudaFreeHost(p->pipe_status);
         if (p->d_pipe_prof) cudaFree(p->d_pipe_prof);
         for (void* d : p->allocations) cudaFree(d);

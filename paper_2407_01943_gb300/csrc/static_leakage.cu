@@ -25,14 +25,19 @@ double* g_scratch_ptr[kMaxDevices] = {};
 
 constexpr double kPiS = 3.141592653589793238462643383279502884;
 
-// Device address of the scratch array on the current device, looked up once per device.
-m2_status scratch_address(int dev, double** out) {
+// Device address of the scratch array on the current device.  Looked up again on every call made
+// outside stream capture (cheap once the module is loaded, and right again after a
+// cudaDeviceReset has given the device a new context); during a capture the address cached by
+// the last call on this device outside capture is used.
+m2_status scratch_address(int dev, cudaStream_t st, double** out) {
     if (dev < 0 || dev >= kMaxDevices) {
         m2::set_error("m2nufft_leakage_static: device ordinal %d out of range", dev);
         return M2_ERR_ARG;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    M2_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, m2_static_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -40,6 +45,9 @@ m2_status scratch_address(int dev, double** out) {
             return M2_ERR_CUDA;
         }
         g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    } else if (!g_scratch_ptr[dev]) {
+        m2::set_error("m2nufft_leakage_static: the first call on a device must come before any stream capture");
+        return M2_ERR_ARG;
     }
     *out = g_scratch_ptr[dev];
     return M2_OK;
@@ -107,9 +115,11 @@ extern "C" m2_status m2nufft_leakage_static(const double* t, int64_t N, double f
     }
     const int64_t I = fc->I;
     // one partial sum per block of kRowsPerBlock values of n, as many blocks as fit the scratch
-    if ((int64_t)K * I > kStaticScratchDoubles) {
-        m2::set_error("m2nufft_leakage_static: K * I = %lld exceeds the static scratch of %lld doubles (%zu MiB)",
-                      (long long)((int64_t)K * I), (long long)kStaticScratchDoubles, kStaticScratchBytes >> 20);
+    // (I is compared before K * I is formed, so no product can wrap)
+    if (I > kStaticScratchDoubles / K) {
+        m2::set_error("m2nufft_leakage_static: K = %d, I = %lld: K * I exceeds the static scratch of %lld doubles "
+                      "(%zu MiB)",
+                      K, (long long)I, (long long)kStaticScratchDoubles, kStaticScratchBytes >> 20);
         return M2_ERR_ARG;
     }
     const int64_t want = (N + kRowsPerBlock - 1) / kRowsPerBlock;
@@ -121,10 +131,10 @@ extern "C" m2_status m2nufft_leakage_static(const double* t, int64_t N, double f
     }
     int dev = 0;
     M2_CUDA_TRY(cudaGetDevice(&dev));
-    double* scratch = nullptr;
-    m2_status s = scratch_address(dev, &scratch);
-    if (s != M2_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double* scratch = nullptr;
+    m2_status s = scratch_address(dev, st, &scratch);
+    if (s != M2_OK) return s;
     const int nblk = (int)want;
     dim3 g1((unsigned)((I + 127) / 128), (unsigned)nblk);
     leakage_partial_kernel<<<g1, 128, 0, st>>>((int)N, K, I, t, w, 0.5 * fs, fc->f_lo, fc->df, scratch);

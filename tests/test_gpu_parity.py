@@ -1,8 +1,13 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-J_k(A_i) and P-hat are compared element by element (relative l2 over the
-array, Eq. eigencoefficients / Eq. power_spectrum_estimator): <= 1e-5 for
-the FP32 path and <= 1e-10 for the FP64 path.  Where the oracle's dense GEP
+J_k(A_i) and P-hat are compared element by element at every compared band
+(Eq. eigencoefficients / Eq. power_spectrum_estimator): the NuFFT's
+per-output bound |dJ_k| <= tol * sum_n |w_k x| and the bounds it implies for
+|J_k|^2 and P-hat (tests/_util.py), beside the relative l2 over the array;
+tol = 1e-5 for the FP32 path and 1e-10 for the FP64 path.  The full-size
+cases compare sampled bands plus the packed path's special positions (both
+ends of the band grid, the first and last in-band FFT columns at every row,
+row 0's partner columns).  Where the oracle's dense GEP
 is cheap, the tapers come from the oracle and are handed to the GPU plan
 (m2nufft_plan_with_tapers), so J is compared with identical tapers; the
 GPU's own GEP is checked separately (eigenvalues, subspace, residuals) and
@@ -15,7 +20,7 @@ import synth
 from oracle import estimator as oest
 from oracle import gpss as ogpss
 from oracle import leakage as oleak
-from tests._util import TOL, rel_l2, sample_bands, seeded_tapers
+from tests._util import TOL, assert_elementwise, packed_edge_bands, rel_l2, sample_bands, seeded_tapers, source_l1
 
 torch = pytest.importorskip("torch")
 pkg = pytest.importorskip("paper_2407_01943_gb300")
@@ -46,6 +51,36 @@ def oracle_all(t, X, w, f_lo, df, I, idx=None):
     return np.stack(Js), np.stack(Ps)
 
 
+_ORACLE_CACHE = {}
+
+
+def oracle_cached(key, t, X, w, f_lo, df, I, idx):
+    """oracle_all for a full-size workload, computed once per module for the same inputs (key names
+    the workload, its signals and tapers; idx is part of the key)."""
+    k = (key, I, idx.tobytes())
+    if k not in _ORACLE_CACHE:
+        _ORACLE_CACHE[k] = oracle_all(t, X, w, f_lo, df, I, idx)
+    return _ORACLE_CACHE[k]
+
+
+def full_size_bands(I, n1, n, seed):
+    """Sampled bands plus the packed path's special positions for its n1 (test infrastructure)."""
+    return np.union1d(sample_bands(I, n, seed), packed_edge_bands(I, n1))
+
+
+def check(out, Jr, Pr, w, X, prec, idx=None, with_E=True):
+    """Relative l2 over the compared array and the element-wise bound at every compared band for J,
+    P-hat and (when present) the eigenspectra; returns the worst ratio to the bound per output."""
+    sel = (lambda a: a) if idx is None else (lambda a: a[..., idx])
+    Jg, Pg = sel(out["J"]), sel(out["P"])
+    Eg = sel(out["E"]) if with_E and "E" in out else None
+    assert rel_l2(Jg, Jr) <= TOL[prec]
+    assert rel_l2(Pg, Pr) <= TOL[prec]
+    if Eg is not None:
+        assert rel_l2(Eg, np.abs(Jr) ** 2) <= TOL[prec]
+    return assert_elementwise(Jg, Jr, source_l1(w, X), TOL[prec], Pg, Pr, Eg)
+
+
 # ---------------------------------------------------------------------------
 # full-array parity at oracle-friendly sizes
 # ---------------------------------------------------------------------------
@@ -63,9 +98,7 @@ def test_grid1024_full_parity(dev, prec, path):
     assert plan.info["path"] == path
     out = run_plan(plan, wl.x, dev)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I)
-    assert rel_l2(out["J"], Jr) <= TOL[prec]
-    assert rel_l2(out["P"], Pr) <= TOL[prec]
-    assert rel_l2(out["E"], np.abs(Jr) ** 2) <= TOL[prec]
+    check(out, Jr, Pr, w, wl.x, prec)
     assert plan.info["wrap"] == 1  # span ~ period: wrap-around spreading
 
 
@@ -81,8 +114,7 @@ def test_jittered_medium_full_parity(dev, prec, path):
     out = run_plan(plan, X, dev)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
     assert plan.info["wrap"] == 0 and plan.info["rows"] < plan.info["n1"]
-    assert rel_l2(out["J"], Jr) <= TOL[prec]
-    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    check(out, Jr, Pr, w, X, prec)
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -98,8 +130,7 @@ def test_general_band_grid_complex_taper(dev, prec):
     assert plan.info["real_taper"] == 0
     out = run_plan(plan, x, dev)
     Jr, Pr = oracle_all(t, x, w, f_lo, df, I)
-    assert rel_l2(out["J"], Jr) <= TOL[prec]
-    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    check(out, Jr, Pr, w, x, prec)
 
 
 @pytest.mark.parametrize("I", [1, 2, 7, 63, 65, 1023])
@@ -111,8 +142,7 @@ def test_small_and_odd_band_counts(dev, I):
     plan = pkg.Plan(t, 1.0, 0.03, 3, -0.45, 0.9 / max(I, 1), I, precision=64, tapers=w)
     out = run_plan(plan, x, dev)
     Jr, Pr = oracle_all(t, x, w, -0.45, 0.9 / max(I, 1), I)
-    assert rel_l2(out["J"], Jr) <= TOL[64]
-    assert rel_l2(out["P"], Pr) <= TOL[64]
+    check(out, Jr, Pr, w, x, 64)
 
 
 def test_single_sample_single_taper(dev):
@@ -134,7 +164,7 @@ def test_many_chunks_and_empty_batch(dev):
     assert plan.info["chunk"] == 2
     out = run_plan(plan, X, dev)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1 / 512, 512)
-    assert rel_l2(out["J"], Jr) <= TOL[64]
+    check(out, Jr, Pr, w, X, 64)
     xe = torch.zeros((0, 300), dtype=torch.float64, device=dev)
     plan.run(xe)
     torch.cuda.synchronize()
@@ -176,9 +206,8 @@ def test_packed_path_edge_cases(dev, K, I, N):
         for k in ("J", "E", "P"):
             assert np.array_equal(o3[k], o2[k]), (mb, k)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
-    assert rel_l2(o2["J"], Jr) <= TOL[32]
-    assert rel_l2(o2["P"], Pr) <= TOL[32]
-    assert rel_l2(o2["E"], np.abs(Jr) ** 2) <= TOL[32]
+    check(o2, Jr, Pr, w, X, 32)
+    check(o1, Jr, Pr, w, X, 32)
     assert rel_l2(o2["P"], o1["P"]) <= TOL[32]
 
 
@@ -279,10 +308,9 @@ def test_jitter16k_full_size_fp32(dev, path):
     w = seeded_tapers(wl.K, wl.N, 7)
     plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=path)
     out = run_plan(plan, wl.x, dev)
-    idx = sample_bands(wl.I, 384, 1)
-    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
-    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
-    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+    idx = full_size_bands(wl.I, 384, 384, 1)  # 384 = n1 of the packed path at this size
+    Jr, Pr = oracle_cached("jitter16k/b2/w7", wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    check(out, Jr, Pr, w, wl.x, 32, idx)
     # P-hat is the taper average of the eigenspectra everywhere
     np.testing.assert_allclose(out["P"], out["E"].mean(axis=1), rtol=2e-6, atol=1e-30)
 
@@ -315,10 +343,9 @@ def test_periodic16k_full_size_fp32(dev, path):
     w = seeded_tapers(wl.K, wl.N, 9)
     plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, path=path)
     out = run_plan(plan, wl.x, dev)
-    idx = sample_bands(wl.I, 256, 2)
-    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
-    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
-    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+    idx = full_size_bands(wl.I, 1536, 256, 2)  # 1536 = n1 of the packed path at this size
+    Jr, Pr = oracle_cached("periodic16k/b1/w9", wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    check(out, Jr, Pr, w, wl.x, 32, idx)
 
 
 def test_jitter16k_fp64_path(dev):
@@ -326,10 +353,9 @@ def test_jitter16k_fp64_path(dev):
     w = seeded_tapers(wl.K, wl.N, 5)
     plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=64, tapers=w)
     out = run_plan(plan, wl.x, dev, want=("J", "P"))
-    idx = sample_bands(wl.I, 128, 3)
+    idx = full_size_bands(wl.I, 384, 128, 3)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
-    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[64]
-    assert rel_l2(out["P"][:, idx], Pr) <= TOL[64]
+    check(out, Jr, Pr, w, wl.x, 64, idx)
 
 
 def test_exec_batch_uneven_matches_single(dev, batch_mode):
@@ -473,7 +499,7 @@ def test_pipe_bounded_wait_reports_timeout(dev):
     plan = pkg.Plan(t, 1.0, 2.0 / 900, 4, -0.5, 1.0 / 2048, 2048, precision=32, tapers=w, path=3)
     out = run_plan(plan, X, dev)
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / 2048, 2048)
-    assert rel_l2(out["J"], Jr) <= TOL[32] and rel_l2(out["P"], Pr) <= TOL[32]
+    check(out, Jr, Pr, w, X, 32)
 
 
 @pytest.fixture(params=[0, 1], ids=["stage_batched", "persistent"])
@@ -512,10 +538,10 @@ def test_exec_batch_pipe_heterogeneous_matches_oracle(dev, batch_mode):
             torch.cuda.synchronize()
             assert torch.equal(single["J"][0], J) and torch.equal(single["E"][0], E)
             assert torch.equal(single["P"][0], P)
-    for (wl, w), J, P in list(zip(ws2, Js, Ps))[:4]:
+    for (wl, w), J, E, P in zip(ws2, Js, Es, Ps):
         Jr, _, Pr = oest.m2nufft(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I)
-        assert rel_l2(J.cpu().numpy(), Jr) <= TOL[32]
-        assert rel_l2(P.cpu().numpy(), Pr) <= TOL[32]
+        o = {"J": J.cpu().numpy()[None], "E": E.cpu().numpy()[None], "P": P.cpu().numpy()[None]}
+        check(o, Jr[None], Pr[None], w, wl.x, 32)
 
 
 def test_exec_batch_mixed_generic_and_pipelined(dev):
@@ -572,7 +598,7 @@ def test_ftest_parity(dev, prec, path):
         assert np.all(rel <= bound), (np.max(rel / bound), int(np.argmax(rel / bound)))
         line = int(round((0.1 + 0.01 * b + 0.5) * I))
         assert out["F"][b][line] > crit
-    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    check(out, Jr, Pr, w, X, prec)
 
 
 def test_ftest_generic_without_J(dev):
@@ -633,8 +659,7 @@ def test_spline_tapers_match_oracle(dev, kind):
     X = np.stack([synth.white(t, 1.0, 33 + b) for b in range(2)])
     out = run_plan(plan, X, dev, want=("J", "P"))
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
-    assert rel_l2(out["J"], Jr) <= TOL[64]
-    assert rel_l2(out["P"], Pr) <= TOL[64]
+    check(out, Jr, Pr, w, X, 64)
 
 
 def test_spline_tapers_full_size(dev):
@@ -683,8 +708,7 @@ def test_subband_parity(dev, prec):
     assert plan.info["path"] == 1 and plan.info["real_taper"] == 0
     out = run_plan(plan, X, dev, want=("J", "P"))
     Jr, Pr = _subband_oracle(t, X, w, f_c0, f_lo, df, I)
-    assert rel_l2(out["J"], Jr) <= TOL[prec]
-    assert rel_l2(out["P"], Pr) <= TOL[prec]
+    check(out, Jr, Pr, w, X, prec)
     wg, lg = plan.tapers()
     np.testing.assert_array_equal(wg, w)
 
@@ -737,8 +761,10 @@ def test_multiband_partition_batch(dev):
         single = p.run(xs[0][None, :], want=("P",))
         torch.cuda.synchronize()
         assert torch.equal(single["P"][0], P)
-        _, Pr = _subband_oracle(t, x[None, :], w, f_c0, lo, 0.1 / I, I)
+        Jr, Pr = _subband_oracle(t, x[None, :], w, f_c0, lo, 0.1 / I, I)
         assert rel_l2(P.cpu().numpy(), Pr[0]) <= TOL[64]
+        l1 = source_l1(w, x)
+        assert_elementwise(None, Jr, l1, TOL[64], P.cpu().numpy()[None], Pr)
 
 
 def test_subband_rejects_band_outside(dev):
@@ -793,10 +819,9 @@ def test_sigma_option_parity(dev, prec, path, sigma):
     if path >= 2:
         assert plan.info["width"] < base.info["width"]
     out = run_plan(plan, wl.x, dev)
-    idx = sample_bands(wl.I, 256, 2)
-    Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
-    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[prec]
-    assert rel_l2(out["P"][:, idx], Pr) <= TOL[prec]
+    idx = full_size_bands(wl.I, plan.info["n1"] if path >= 2 else 384, 256, 2)
+    Jr, Pr = oracle_cached(f"jitter16k/b2/w5/n1={plan.info['n1']}", wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    check(out, Jr, Pr, w, wl.x, prec, idx)
 
 
 def test_sigma_option_rejects_out_of_range(dev):
@@ -832,10 +857,9 @@ def test_autotuned_plan(dev):
         assert plan.info["chunk"] == rep[best][2]
     assert ref.tuning() == []
     out = run_plan(plan, wl.x, dev)
-    idx = sample_bands(wl.I, 256, 3)
+    idx = full_size_bands(wl.I, plan.info["n1"], 256, 3)
     Jr, Pr = oracle_all(wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
-    assert rel_l2(out["J"][:, :, idx], Jr) <= TOL[32]
-    assert rel_l2(out["P"][:, idx], Pr) <= TOL[32]
+    check(out, Jr, Pr, w, wl.x, 32, idx)
     for a, b in zip(plan.leakage(), ref.leakage()):
         np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
 
@@ -863,3 +887,67 @@ def test_multichunk_spread_buffer_reuse_bitwise(dev):
         for b in range(B):
             assert torch.equal(out["J"][b], alone[b]["J"][0]), (B, b)
             assert torch.equal(out["P"][b], alone[b]["P"][0]), (B, b)
+
+
+# ---------------------------------------------------------------------------
+# the uneven batch at its full size: 2048 signals in one exec_batch, 64 of them against the oracle
+# ---------------------------------------------------------------------------
+def _uneven_subset(ws, n, seed):
+    """A seeded subset of the batch that holds its shortest and longest signals and every K class."""
+    rng = np.random.default_rng(seed)
+    Ns = np.array([wl.N for wl in ws])
+    pick = {int(np.argmin(Ns)), int(np.argmax(Ns))}
+    for K in sorted({wl.K for wl in ws}):
+        pick.add(int(next(s for s, wl in enumerate(ws) if wl.K == K)))
+    rest = [s for s in rng.permutation(len(ws)) if s not in pick]
+    return sorted(pick | set(int(s) for s in rest[: n - len(pick)]))
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["stage_batched", "persistent"])
+def test_uneven_2048_batch_against_oracle(dev, mode):
+    """The uneven-batch workload at its size: 2048 signals (grid length log-uniform in
+    [1024, 16384], Markov gaps, K in {4, 6, 8}, I = 4G) planned with taper-shaped inputs and run as
+    one m2nufft_exec_batch; 64 of them (the shortest and longest, every K) against the oracle on
+    sampled bands plus each plan's packed special positions, and the persistent form (batch mode 1)
+    equal to the stage-batched one bit for bit on the subset."""
+    ws = synth.batched_uneven(2048, seed=0)
+    sub = _uneven_subset(ws, 64, 5)
+    plans, xs, Js, Es, Ps, tap = [], [], [], [], [], []
+    for s, wl in enumerate(ws):
+        w = seeded_tapers(wl.K, wl.N, s)
+        plans.append(pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w,
+                              max_batch=1))
+        xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
+        Js.append(torch.empty((wl.K, wl.I), dtype=torch.complex64, device=dev))
+        Es.append(torch.empty((wl.K, wl.I), dtype=torch.float32, device=dev))
+        Ps.append(torch.empty((wl.I,), dtype=torch.float32, device=dev))
+        tap.append(w if s in sub else None)
+    assert all(p.info["path"] == 2 for p in plans)
+    prev = pkg.binding.set_batch_mode(0)
+    try:
+        pkg.exec_batch(plans, xs, Js, Es, Ps)
+        torch.cuda.synchronize()
+        got = {s: {"J": Js[s].cpu().numpy()[None], "E": Es[s].cpu().numpy()[None], "P": Ps[s].cpu().numpy()[None]}
+               for s in sub}
+        if mode == 1:
+            pkg.binding.set_batch_mode(1)
+            for J in Js:
+                J.zero_()
+            pkg.exec_batch(plans, xs, Js, Es, Ps)
+            torch.cuda.synchronize()
+            for s in sub:
+                assert np.array_equal(Js[s].cpu().numpy()[None], got[s]["J"]), s
+                assert np.array_equal(Ps[s].cpu().numpy()[None], got[s]["P"]), s
+    finally:
+        pkg.binding.set_batch_mode(prev)
+    worst = {}
+    for s in sub:
+        wl = ws[s]
+        idx = np.union1d(sample_bands(wl.I, 64, s), packed_edge_bands(wl.I, plans[s].info["n1"]))
+        Jr, _, Pr = oest.m2nufft(wl.t, wl.x[0], tap[s], wl.f_lo, wl.df, wl.I, idx)
+        r = check(got[s], Jr[None], Pr[None], tap[s], wl.x, 32, idx)
+        for k, v in r.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+    assert set(worst) == {"J", "P", "E"}
+    for p in plans:
+        p.close()

@@ -5,7 +5,8 @@ import numpy as np
 import pytest
 
 import synth
-from tests._util import TOL, rel_l2
+from oracle import estimator as oest
+from tests._util import TOL, assert_elementwise, packed_edge_bands, rel_l2, sample_bands, source_l1
 
 torch = pytest.importorskip("torch")
 pkg = pytest.importorskip("paper_2407_01943_gb300")
@@ -47,6 +48,16 @@ def test_server_results_equal_alone(path):
         alone = p.run(x, want=("P",))["P"].cpu().numpy()[0]
         assert np.array_equal(alone, r.P)
         assert rel_l2(r.P, alone) <= TOL[32]
+    # served P-hat against the oracle (Eq. power_spectrum_estimator with the plan's tapers) on a
+    # sample of requests, at sampled bands plus the packed path's special positions
+    for r in reqs[::10]:
+        p = plans[r.pattern]
+        pt = pats[r.pattern]
+        w = synth.taper_like(4, pt["t"].shape[0], r.pattern)  # the tapers the plan was made with
+        idx = np.union1d(sample_bands(p.I, 64, r.rid), packed_edge_bands(p.I, p.info["n1"]))
+        Jr, _, Pr = oest.m2nufft(pt["t"], r.x.astype(np.float64), w, pt["f_lo"], pt["df"], p.I, idx)
+        assert rel_l2(r.P[idx], Pr) <= TOL[32]
+        assert_elementwise(None, Jr[None], source_l1(w, r.x.astype(np.float64)), TOL[32], r.P[idx][None], Pr[None])
     # the plain path on the same server gives the same results too
     plain_reqs = [serve.Request(r.rid, r.pattern, r.x, r.arrival) for r in reqs]
     srv.serve_plain(plain_reqs)

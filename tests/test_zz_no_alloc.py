@@ -9,6 +9,7 @@ import pytest
 
 import synth
 from oracle import gpss as ogpss
+from oracle import leakage as oleak
 from tests._util import TOL
 
 torch = pytest.importorskip("torch")
@@ -47,6 +48,10 @@ def test_leakage_static_matches_plan_two_calls():
         scale = max(np.max(np.abs(L_ref)), 1e-300)
         assert np.max(np.abs(L - L_ref)) <= TOL[64] * scale
         assert np.max(np.abs(E - E_ref)) <= TOL[64] * scale
+        # and against the oracle's dense pair sum, at every band
+        Lo, Eo = oleak.leakage_at(t, w, lam, 1.0, fw, -0.5 + np.arange(I) / I)
+        np.testing.assert_allclose(L, Lo, rtol=1e-9, atol=1e-13)
+        np.testing.assert_allclose(E, Eo, rtol=1e-9, atol=1e-13)
 
 
 def test_leakage_static_rejects_oversized():
