@@ -13,6 +13,18 @@ whole job.  Multi-GPU (torchrun): each rank runs its own batch (independent
 signals, no data-path collective), weak scaling; the timed region is
 bracketed by a barrier and synchronisation and the max over ranks is taken.
 
+The default jitter16k line also carries, measured in the same run:
+  * `parity`: the timed path's outputs against the CPU-baseline leg's oracle
+    sample (the packed path's special positions plus random bands), per
+    output the relative l2 and the worst element error over its bound;
+  * `e2e` (every declared output read back to pinned host memory) and
+    `e2e_p_only` (the exec writes, and the host reads, P-hat alone);
+  * `batched`: the 2048-signal uneven batch, one m2nufft_exec_batch against
+    one m2nufft_exec per signal;
+  * `served`: the 64-pattern serving trace (p50/p99 latency and throughput at
+    2000 req/s and saturated) against the plain per-request path;
+  * `fp64`: the FP64 path on the 1024-sample grid workload and on jitter16k.
+
 --impl reference times the CPU oracle (direct FP64 sum) on a bounded sample
 of the same workload on the host cores.
 """
@@ -56,6 +68,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven-batch, serving and FP64 comparisons appended to the jitter16k line")
     ap.add_argument("--chunk", type=int, default=0, help="signals per internal chunk (0 = the plan's choice)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="exec path: 0 automatic, 1 generic, 2 packed four-kernel, 3 packed persistent kernel")
@@ -186,43 +200,75 @@ def profiled_traffic(workload: str, kernel: str, nb: int):
 
 
 def algorithmic_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: str = "JEP") -> float:
-    """Compulsory bytes one launch of each exec kernel must move (per chunk of nb signals).
+    """Compulsory bytes one launch of each exec kernel must move (per launch of nb signals), HBM
+    and L2 alike.  Grids per signal: K (generic path) or ceil(K/2) taper pairs (packed paths 2 and 3,
+    two real tapers spread and transformed as one complex grid).
 
     spread : read x (N reals) + point records (cell int32, offset, source int32) + tapers (K x P),
-             write the spread grid (K x rows*n2 complex)
-    cols   : read the spread grid, write the column-FFT workspace (K x nf complex)
-    rows   : write J (K x I complex), eigenspectra (K x I real), P-hat (I real) and read the
-             deconvolution factors (I complex); its input is the L2-resident workspace
+             write the spread grids (grids x rows*n2 complex)
+    cols   : read the spread grids, write the column-FFT workspace (grids x nf complex)
+    rows   : packed: the row FFTs in place (read + write the workspace); generic: with the fused
+             epilogue, write J, eigenspectra, P-hat and read the deconvolution factors
+    epi    : write J (K x I complex), eigenspectra (K x I real), P-hat (I real) [, F (I real)] and
+             read the deconvolution factors (I complex); its input is the L2-resident workspace
     """
     N, K, I = info["N"], info["K"], info["I"]
-    grid = K * info["rows"] * info["n2"] * csz
+    grids = (K + 1) // 2 if info["path"] >= 2 else K
+    grid = grids * info["rows"] * info["n2"] * csz
     if kernel == "spread":
-        per = N * rsz + grid
-        shared = N * (8 + rsz) + K * N * (rsz if info["real_taper"] else csz)
-        return nb * per + shared
+        return nb * grid + hbm_bytes(info, kernel, nb, csz, rsz, outputs)
     if kernel == "cols":
-        return nb * (grid + K * info["nf"] * csz)
+        return nb * (grid + grids * info["nf"] * csz)
     if kernel == "rows":
-        if info["path"] == 2:  # packed path: row FFTs only (L2-resident input and output)
-            return nb * 2 * ((K + 1) // 2) * info["nf"] * csz
-        per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
-        return nb * per + I * csz
-    if kernel == "epi":
-        per = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
-        per += I * rsz if "F" in outputs else 0
-        return nb * per + I * csz
-    if kernel == "pipe":
-        # the whole path in one launch over nb signals: read x, write J, |J|^2, P-hat; the plan's
-        # point records, tapers and deconvolution factors once; the intermediates (spread grids,
-        # column-FFT and row-FFT workspaces) are consumed from L2 and are not compulsory traffic
-        per = N * rsz + I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0)
-        shared = N * (8 + rsz) + K * N * rsz + I * csz
-        return nb * per + shared
+        if info["path"] >= 2:  # packed path: row FFTs only (L2-resident input and output)
+            return nb * 2 * grids * info["nf"] * csz
+        return hbm_bytes(info, kernel, nb, csz, rsz, outputs)
+    if kernel in ("epi", "pipe"):
+        return hbm_bytes(info, kernel, nb, csz, rsz, outputs)
     raise KeyError(kernel)
 
 
-def cpu_oracle_rate(wl, target_s: float, seed: int = 0):
-    """Time the oracle's direct FP64 sum on a band subset of one signal."""
+def hbm_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: str = "JEP") -> float:
+    """The part of a launch's compulsory bytes that must cross HBM: inputs that come from device
+    memory (samples, point records, tapers, deconvolution factors) and the outputs; the FFT
+    intermediates (spread grids, column and row transforms) are produced and consumed in L2."""
+    N, K, I = info["N"], info["K"], info["I"]
+    taper = rsz if info["real_taper"] else csz
+    out = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0) + \
+        (I * rsz if "F" in outputs else 0)
+    if kernel == "spread":
+        return nb * N * rsz + N * (8 + rsz) + K * N * taper
+    if kernel == "cols":
+        return 0.0
+    if kernel == "rows":
+        return 0.0 if info["path"] >= 2 else nb * out + I * csz
+    if kernel == "epi":
+        return nb * out + I * csz
+    if kernel == "pipe":
+        # the whole path in one launch: read x, write the outputs; the plan's records, tapers and
+        # deconvolution factors once
+        return nb * (N * rsz + out) + N * (8 + rsz) + K * N * taper + I * csz
+    raise KeyError(kernel)
+
+
+def special_bands(I: int, n1: int) -> np.ndarray:
+    """Band indices at the packed path's special positions for its n1 (the FFT index k = k1 + n1 k2
+    maps to band i_c + m, m = k or k - nf, and one output thread writes m and -m): every k1 of the
+    first two and last two in-band columns, row 0 at every in-band column, both signs of m, and the
+    first and last band."""
+    i_c = I // 2
+    k2max = min(511, -(-(I - i_c) // n1))
+    ms = np.concatenate([np.arange(n1) + n1 * c for c in (0, 1, k2max - 1, k2max) if c >= 0]
+                        + [n1 * np.arange(k2max + 1)])
+    idx = np.concatenate([ms + i_c, i_c - ms, [0, I - 1]])
+    return np.unique(idx[(idx >= 0) & (idx < I)]).astype(np.int64)
+
+
+def cpu_oracle_rate(wl, target_s: float, seed: int = 0, n1: int = 0):
+    """Time the oracle's direct FP64 sum on a band subset of one signal (the packed path's special
+    positions for n1, when given, plus random bands).  Returns the rate, the sample size, the wall
+    time, the threads used, and the sample itself (bands, tapers, eigencoefficients) so that the GPU
+    result can be compared with it."""
     from oracle import _native
     from oracle import estimator as oest
     from synth import taper_like  # taper-shaped rows; the direct sum costs the same for any taper
@@ -233,12 +279,58 @@ def cpu_oracle_rate(wl, target_s: float, seed: int = 0):
     oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, probe)
     dt = time.perf_counter() - t0
     nb = int(min(wl.I, max(256, 256 * target_s / max(dt, 1e-6))))
-    idx = np.sort(rng.choice(wl.I, size=nb, replace=False)).astype(np.int64)
+    idx = special_bands(wl.I, n1) if n1 else np.zeros(0, dtype=np.int64)
+    idx = np.union1d(idx, rng.choice(wl.I, size=max(0, min(wl.I, nb) - idx.size), replace=False)).astype(np.int64)
     t0 = time.perf_counter()
-    oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, idx)
+    Jr = oest.eigencoefficients(wl.t, wl.x[0], w, wl.f_lo, wl.df, wl.I, idx)
     dt = time.perf_counter() - t0
-    units = wl.K * wl.N * nb
-    return units / dt, nb, dt, _native.num_threads()
+    units = wl.K * wl.N * idx.size
+    return units / dt, int(idx.size), dt, _native.num_threads(), (idx, w, Jr)
+
+
+def gpu_parity(wl, precision: int, path: int, chunk: int, sigma: float, dev, sample, outputs: str):
+    """Measured error of the timed path's outputs against the oracle's sample of the CPU-baseline
+    leg (one signal, its bands): a plan with the timed plan's geometry and kernels and the sample's
+    taper-shaped rows (the eigencoefficient sum is linear in the taper, and the oracle takes no
+    input from the GPU) runs the signal; per output, the relative l2 over the compared entries and
+    the largest ratio of an element's error to its bound (J: tol * sum_n |w_k x|; |J|^2 and P-hat:
+    the bounds that follow), and for P-hat also max |dP| / max P."""
+    import torch
+
+    import paper_2407_01943_gb300 as pkg
+    idx, w, Jr = sample
+    tol = 1e-5 if precision == 32 else 1e-10
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=precision, device=dev.index,
+                    tapers=w, max_batch=chunk, path=path, sigma=sigma)
+    xt = torch.from_numpy(wl.x[:1].astype(np.float32 if precision == 32 else np.float64)).to(dev)
+    want = ("J", "E", "P", "F") if "F" in outputs else ("J", "E", "P")
+    out = {k: v.cpu().numpy()[0] for k, v in plan.run(xt, want=want).items()}
+    torch.cuda.synchronize()
+    plan.close()
+    Pr = np.mean(np.abs(Jr) ** 2, axis=0)
+    Er = np.abs(Jr) ** 2
+    l1 = (np.abs(w) * np.abs(wl.x[0])[None, :]).sum(-1)[:, None]
+    bJ = tol * l1
+    bE = bJ * (2 * np.abs(Jr) + bJ)
+    Jg, Eg, Pg = out["J"][:, idx], out["E"][:, idx], out["P"][idx]
+
+    def rl2(a, b):
+        return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    rep = {"oracle": "direct FP64 sum, the CPU-baseline sample", "tol": tol, "signals": 1, "bands": int(idx.size),
+           "tapers": "seeded taper-shaped rows on the timed plan's geometry and kernels",
+           "J": {"rel_l2": rl2(Jg, Jr), "max_elem_err_over_bound": float(np.max(np.abs(Jg - Jr) / bJ)),
+                 "max_abs_err_over_l1": float(np.max(np.abs(Jg - Jr) / l1))},
+           "E": {"rel_l2": rl2(Eg, Er), "max_elem_err_over_bound": float(np.max(np.abs(Eg - Er) / bE))},
+           "P": {"rel_l2": rl2(Pg, Pr), "max_elem_err_over_bound": float(np.max(np.abs(Pg - Pr) / bE.mean(axis=0))),
+                 "max_abs_err_over_max_P": float(np.max(np.abs(Pg - Pr)) / np.max(Pr))}}
+    if "F" in out:
+        from oracle import ftest as oft
+        Fr = oft.f_statistic(Jr, w)
+        Fg = out["F"][idx]
+        rep["F"] = {"rel_l2": rl2(Fg, Fr), "median_rel_err": float(np.median(np.abs(Fg - Fr) / Fr))}
+    rep["pass"] = bool(rep["J"]["max_elem_err_over_bound"] <= 1 and rep["P"]["max_elem_err_over_bound"] <= 1
+                       and rep["J"]["rel_l2"] <= tol and rep["P"]["rel_l2"] <= tol)
+    return rep
 
 
 def run_reference(args):
@@ -252,7 +344,7 @@ def run_reference(args):
     from synth import taper_like
     w = taper_like(wl.K, wl.N, 0)
     # bounded sample per step so that warmup + steps stay within a few minutes
-    rate, nb, dt, cores = cpu_oracle_rate(wl, min(args.cpu_seconds, 4.0))
+    rate, nb, dt, cores, _ = cpu_oracle_rate(wl, min(args.cpu_seconds, 4.0))
     per_step_s = max(0.5, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
     nb_step = int(min(wl.I, max(64, rate * per_step_s / (wl.K * wl.N))))
     rng = np.random.default_rng(1)
@@ -279,27 +371,48 @@ def run_reference(args):
     return 0
 
 
-def run_uneven(args):
-    """Uneven batch (2048 signals by default): nsig signals with their own sampling patterns (grid length
-    log-uniform in [1024, 16384], Markov gaps, K in {4,6,8}, I = 4G) through m2nufft_exec_batch
-    (one cached CUDA graph per call) against the plain per-signal path (one m2nufft_exec per
-    signal on one stream).  Plans use taper-shaped inputs instead of 2048 dense GEPs; the exec
-    kernels and their shapes are the same."""
+def timed_ms(torch, stream, dev, fn, steps: int, warmup: int):
+    """Average device time of fn() over `steps` calls after `warmup`, the L2 flushed (512 MiB write
+    + read-back) before each call, CUDA events on the launching stream."""
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def flush_l2():
+        flush.fill_(1)
+        flush.view(torch.int32).max()
+    for _ in range(warmup):
+        flush_l2()
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s_ in range(steps):
+        flush_l2()
+        evs[s_][0].record(stream)
+        fn()
+        evs[s_][1].record(stream)
+    torch.cuda.synchronize()
+    del flush
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, persistent: bool = True):
+    """Uneven batch (the 2048-signal workload by default): nsig signals with their own sampling
+    patterns (grid length log-uniform in [1024, 16384], Markov gaps 15 %, K in {4, 6, 8},
+    f_w = (K/2 + 1)/G, I = 4G) through m2nufft_exec_batch (one cached CUDA graph per call) against
+    the plain per-signal path (one m2nufft_exec per signal on one stream), outputs J, |J|^2 and
+    P-hat.  Plans take seeded taper-shaped rows instead of 2048 dense GEPs; the exec kernels and
+    their shapes are the same."""
     import torch
 
     import paper_2407_01943_gb300 as pkg
     import synth
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pkg.build()
-    ws = synth.batched_uneven(args.nsig, seed=rank)
+    ws = synth.batched_uneven(nsig, seed=seed)
     t_plan = time.perf_counter()
     plans, xs, Js, Es, Ps = [], [], [], [], []
     units = 0
     for s_, wl in enumerate(ws):
         p = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, device=local, max_batch=1,
-                     tapers=synth.taper_like(wl.K, wl.N, s_), lam=np.linspace(0.999, 0.99, wl.K))
+                     tapers=synth.taper_like(wl.K, wl.N, s_))
         plans.append(p)
         xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
         Js.append(torch.empty((wl.K, wl.I), dtype=torch.complex64, device=dev))
@@ -308,48 +421,30 @@ def run_uneven(args):
         units += wl.K * wl.N * wl.I
     t_plan = time.perf_counter() - t_plan
     stream = torch.cuda.current_stream()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    def flush_l2():
-        flush.fill_(1)
-        flush.view(torch.int32).max()
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            flush_l2()
-            fn()
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for s_ in range(args.steps):
-            flush_l2()
-            evs[s_][0].record(stream)
-            fn()
-            evs[s_][1].record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs) / args.steps
-
     all_packed = all(p.info["path"] >= 2 for p in plans)
-
+    t0 = time.perf_counter()
+    pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: build + capture + instantiate
+    torch.cuda.synchronize()
+    t_capture = time.perf_counter() - t0
+    ms_batch = timed_ms(torch, stream, dev, lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream),
+                        steps, warmup)
     def coset_len(n1):
         f = 1
         while f < 32 and n1 % (2 * f) == 0:
             f *= 2
         return f
+    # one spread launch per taper-pair class, one column launch per coset length, the row FFTs, the epilogue
     kp_classes = {0 if (p.info["K"] + 1) // 2 <= 2 else (1 if (p.info["K"] + 1) // 2 <= 4 else 2) for p in plans}
-    hb_launches = len(kp_classes) + len({coset_len(p.info["n1"]) for p in plans}) + 2
-    t0 = time.perf_counter()
-    pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: build + capture + instantiate
-    torch.cuda.synchronize()
-    t_capture = time.perf_counter() - t0
-    ms_batch = timed(lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream))
-    # the same batch as one persistent pipelined kernel (batch mode 1), for comparison
+    hb_launches = (len(kp_classes) + len({coset_len(p.info["n1"]) for p in plans}) + 2) if all_packed else None
     stage_split, ms_pipe = None, None
-    if all_packed:
+    if all_packed and persistent:
+        # the same batch as one persistent pipelined kernel (batch mode 1), for comparison
         prev = pkg.binding.set_batch_mode(1)
         pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)
         torch.cuda.synchronize()
         pkg.binding.batch_pipe_profile()  # reset the stage accounting
-        ms_pipe = timed(lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream))
+        ms_pipe = timed_ms(torch, stream, dev, lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream),
+                           steps, warmup)
         pkg.binding.set_batch_mode(prev)
         busy, waitms, nitems = pkg.binding.batch_pipe_profile()
         tot = max(float(busy.sum()), 1e-12)
@@ -362,30 +457,45 @@ def run_uneven(args):
             p.exec(x[None, :], J[None], E[None], P[None], stream=stream)
 
     wall0 = time.perf_counter()
-    ms_plain = timed(plain)
+    ms_plain = timed_ms(torch, stream, dev, plain, steps, warmup)
     wall_plain = time.perf_counter() - wall0
-    line = {
-        "metric": METRIC, "value": units / (ms_batch * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"uneven batch: {args.nsig} signals, grid length log-uniform in [1024, 16384], "
-                               f"Markov gaps 15%, K in {{4,6,8}}, I = 4G; m2nufft_exec_batch (one CUDA graph: "
-                               f"one launch per stage over all signals)",
-                   "signals": args.nsig, "units_per_step": units,
-                   "l2": "flushed between timed steps (512 MiB write + read-back)"},
-        "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain,
-                             "host_wall_s": wall_plain},
-        "batch_over_plain": ms_plain / ms_batch,
+    out = {
+        "workload": f"uneven batch: {nsig} signals, grid length log-uniform in [1024, 16384], Markov gaps 15%, "
+                    f"K in {{4,6,8}}, I = 4G; outputs J, |J|^2, P-hat",
+        "signals": nsig, "units_per_step": units, "steps": steps, "warmup": warmup,
+        "l2": "flushed between timed steps (512 MiB write + read-back)",
+        "batched": {"value": units / (ms_batch * 1e-3), "ms_per_step": ms_batch, "gpu_launches": hb_launches,
+                    "form": "m2nufft_exec_batch, batch mode 0: one CUDA graph, one launch per stage over all signals"},
+        "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain, "host_wall_s": wall_plain,
+                             "gpu_launches": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
+                                                 for p in plans)},
+        "batched_over_plain": ms_plain / ms_batch,
         "persistent_kernel": None if ms_pipe is None else {
             "value": units / (ms_pipe * 1e-3), "ms_per_step": ms_pipe, "gpu_launches": 1, "stages": stage_split},
-        "gpu_launches": hb_launches if all_packed else 4 * args.nsig,
-        "plain_gpu_launches_per_step": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
-                                           for p in plans),
         "plan_seconds": t_plan, "capture_seconds": t_capture,
     }
-    print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+    return out
+
+
+def run_uneven(args):
+    """The uneven-batch workload as its own bench line (value = the batched form)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2407_01943_gb300 as pkg
+    pkg.build()
+    m = measure_uneven(args.nsig, args.steps, args.warmup, local, seed=rank)
+    line = {
+        "metric": METRIC, "value": m["batched"]["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["batched"]["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": m["workload"], "signals": args.nsig, "units_per_step": m["units_per_step"],
+                   "l2": m["l2"]},
+        "gpu_launches": m["batched"]["gpu_launches"], "uneven": m,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -500,30 +610,26 @@ def run_subopt(args):
     return 0
 
 
-def run_serve(args):
+def measure_serve(requests: int, rate: float, local: int, seed: int):
     """Serving: Poisson arrivals of PSD requests over 64 fixed sampling patterns
     (grid length uniform in [2048, 16384], jittered or Bernoulli-missing 10-30%, K = 8, I = 4G),
     plans cached before the trace, 40 GB device-memory budget; continuous batching (4 slots,
-    up to 16 requests per launch) against the plain per-request path.  The 64 plans take their
-    tapers from interpolated DPSS (Table 1 step 3 a-c: no GEP), built before the trace."""
-    import torch
-
+    up to 16 requests per launch) against the plain per-request path, at the given arrival rate
+    and saturated (every request at t = 0).  The 64 plans take their tapers from interpolated
+    DPSS (Table 1 step 3 a-c: no GEP), built before the trace."""
     import paper_2407_01943_gb300 as pkg
     import synth
     from paper_2407_01943_gb300 import serve
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    pkg.build()
-    pats = synth.serving_patterns(64, seed=rank)
+    pats = synth.serving_patterns(64, seed=seed)
     t_plan = time.perf_counter()
     plans = {i: pkg.Plan(pt["t"], 1.0, pt["f_w"], pt["K"], pt["f_lo"], pt["df"], pt["I"], precision=32,
                          device=local, max_batch=16, taper_design="spline")
              for i, pt in enumerate(pats)}
     t_plan = time.perf_counter() - t_plan
 
-    def trace(n, rate, seed):
-        arr = synth.poisson_arrivals(rate, n, seed) if rate > 0 else np.zeros(n)
-        rng = np.random.default_rng(seed + 1)
+    def trace(n, rate_, seed_):
+        arr = synth.poisson_arrivals(rate_, n, seed_) if rate_ > 0 else np.zeros(n)
+        rng = np.random.default_rng(seed_ + 1)
         out = []
         for k, a in enumerate(arr):
             pid = int(rng.integers(0, len(pats)))
@@ -531,29 +637,158 @@ def run_serve(args):
                                      float(a)))
         return out
 
-    budget = 40 << 30
-    srv = serve.PSDServer(plans, mem_budget=budget, slots=4, max_batch=16, device=local)
+    srv = serve.PSDServer(plans, mem_budget=40 << 30, slots=4, max_batch=16, device=local)
     srv.serve(trace(200, 0, 99))                               # warm-up (allocator, pinned pools)
-    loaded = srv.serve(trace(args.requests, args.rate, 1))
-    plain = srv.serve_plain(trace(args.requests, args.rate, 1))
-    sat = srv.serve(trace(args.requests, 0, 2))               # all requests at t = 0
-    sat_plain = srv.serve_plain(trace(args.requests, 0, 2))
+    loaded = srv.serve(trace(requests, rate, 1))
+    plain = srv.serve_plain(trace(requests, rate, 1))
+    sat = srv.serve(trace(requests, 0, 2))                     # all requests at t = 0
+    sat_plain = srv.serve_plain(trace(requests, 0, 2))
+    srv.close()
+    for p in plans.values():
+        p.close()
+    return {
+        "workload": f"serving: 64 cached patterns, G uniform in [2048, 16384], K = 8, I = 4G; {requests} requests, "
+                    f"Poisson at {rate:g} req/s and saturated; continuous batching, 4 slots, <= 16 per launch, "
+                    f"40 GB budget; latency = arrival to P-hat in host memory",
+        "served_at_rate": loaded, "plain_at_rate": plain,
+        "served_saturated": sat, "plain_saturated": sat_plain,
+        "saturated_served_over_plain": sat["throughput_units_per_s"] / sat_plain["throughput_units_per_s"],
+        "plan_seconds": t_plan,
+    }
+
+
+def run_serve(args):
+    """The serving workload as its own bench line (value = saturated served throughput)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2407_01943_gb300 as pkg
+    pkg.build()
+    m = measure_serve(args.requests, args.rate, local, seed=rank)
+    sat = m["served_saturated"]
     line = {
         "metric": METRIC, "value": sat["throughput_units_per_s"], "unit": UNIT, "n_gpus": world, "steps": 1,
         "warmup": 1, "ms_per_step": sat["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"serving: 64 cached patterns, G uniform in [2048, 16384], K = 8, I = 4G; "
-                               f"{args.requests} requests; continuous batching, 4 slots, <= 16 per launch, "
-                               f"40 GB budget", "rate_req_per_s": args.rate},
-        "served_at_rate": loaded, "plain_at_rate": plain,
-        "served_saturated": sat, "plain_saturated": sat_plain,
-        "plan_seconds": t_plan,
+        "config": {"workload": m["workload"], "rate_req_per_s": args.rate},
+        "served": m,
     }
     print(json.dumps(line), flush=True)
-    srv.close()
-    for p in plans.values():
-        p.close()
     return 0
+
+
+def e2e_run(plan, torch, stream, dev, x, xh, outs, steps, world, barrier, units_per_step, step_outputs):
+    """End-to-end steps through the public API: x copied in from pinned host memory, every output in
+    `outs` (device tensors or None) read back to pinned host memory, double-buffered over two copy
+    streams; returns the e2e object of the bench line."""
+    names = [k for k, v in outs.items() if v is not None]
+    dbuf = [dict(outs), {k: (torch.empty_like(outs[k]) if k in names else None) for k in outs}]
+    hbuf = [{k: torch.empty(outs[k].shape, dtype=outs[k].dtype).pin_memory() for k in names} for _ in range(2)]
+    xd = [torch.empty_like(x) for _ in range(2)]
+    cstream = torch.cuda.Stream(device=dev)  # device -> host
+    hstream = torch.cuda.Stream(device=dev)  # host -> device
+    d2h_done = [torch.cuda.Event() for _ in range(2)]
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    step_done = [torch.cuda.Event() for _ in range(2)]
+
+    def one(xin, o):
+        if o.get("F") is not None:
+            plan.exec(xin, o["J"], o["E"], o["P"], stream=stream, F=o["F"])
+            if o["Lh"] is not None:
+                plan.exec(xin[:0], None, None, None, o["Lh"], o["Eh"], stream=stream)
+        else:
+            plan.exec(xin, o["J"], o["E"], o["P"], o["Lh"], o["Eh"], stream=stream)
+
+    def steps_(n):
+        go = torch.cuda.Event()  # the first input's copy starts when the compute stream gets here
+        go.record(stream)
+        hstream.wait_event(go)
+        with torch.cuda.stream(hstream):
+            xd[0].copy_(xh, non_blocking=True)
+            h2d_done[0].record(hstream)
+        for s_ in range(n):
+            b = s_ % 2
+            stream.wait_event(h2d_done[b])  # this step's x is in
+            stream.wait_event(d2h_done[b])  # output buffers b were read back two steps ago
+            one(xd[b], dbuf[b])
+            step_done[b].record(stream)
+            cstream.wait_event(step_done[b])
+            with torch.cuda.stream(cstream):
+                for k in names:
+                    hbuf[b][k].copy_(dbuf[b][k], non_blocking=True)
+                d2h_done[b].record(cstream)
+            if s_ + 1 < n:
+                nb_ = (s_ + 1) % 2
+                if s_ >= 1:
+                    hstream.wait_event(step_done[nb_])  # step s-1 is done with x buffer nb_
+                with torch.cuda.stream(hstream):
+                    xd[nb_].copy_(xh, non_blocking=True)
+                    h2d_done[nb_].record(hstream)
+        stream.wait_stream(cstream)
+
+    for ev in d2h_done:
+        ev.record(stream)
+    steps_(2)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    steps_(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = job_time_ms(float(e0.elapsed_time(e1)), world, dev)
+    d2h = int(sum(hbuf[0][k].numel() * hbuf[0][k].element_size() for k in names))
+    return {"value": job_throughput(units_per_step, steps, world, ms), "unit": UNIT,
+            "h2d_bytes_per_step": int(xh.numel() * xh.element_size()), "d2h_bytes_per_step": d2h,
+            "ms_per_step": ms / steps, "outputs_read_back": "".join(k[0] for k in names if k != "Eh"),
+            "exec_outputs": step_outputs,
+            "overlap": "double-buffered: step s+1's x copy-in and step s's output read-back overlap the execs of step s",
+            "l2": "not flushed between steps (each step's outputs are larger than the 129 MB L2)"
+                  if d2h > (129 << 20) else "not flushed between steps"}
+
+
+def measure_secondary(name: str, precision: int, B: int, steps: int, warmup: int, local: int, cpu_s: float,
+                      gep: bool):
+    """A further workload timed on its own (outputs J, |J|^2, P-hat; L2 flushed between steps), with
+    its own CPU-baseline leg and the parity of its outputs against that leg's oracle sample."""
+    import torch
+
+    import paper_2407_01943_gb300 as pkg
+    import synth
+    dev = torch.device("cuda", local)
+    wl = synth.workload(name, batch=B, seed=0)
+    t0 = time.perf_counter()
+    if gep:
+        plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=precision, device=local)
+    else:  # taper-shaped rows: the exec kernels and their shapes are those of a GEP plan
+        plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=precision, device=local,
+                        tapers=synth.taper_like(wl.K, wl.N, 0))
+    t_plan = time.perf_counter() - t0
+    rdt = torch.float32 if precision == 32 else torch.float64
+    cdt = torch.complex64 if precision == 32 else torch.complex128
+    x = torch.from_numpy(wl.x.astype(np.float32 if precision == 32 else np.float64)).to(dev)
+    J = torch.empty((B, wl.K, wl.I), dtype=cdt, device=dev)
+    E = torch.empty((B, wl.K, wl.I), dtype=rdt, device=dev)
+    P = torch.empty((B, wl.I), dtype=rdt, device=dev)
+    stream = torch.cuda.current_stream()
+    ms = timed_ms(torch, stream, dev, lambda: plan.exec(x, J, E, P, stream=stream), steps, warmup)
+    info = plan.info
+    plan.close()
+    units = B * wl.K * wl.N * wl.I
+    rate, nb, dt, cores, sample = cpu_oracle_rate(wl, cpu_s, n1=info["n1"] if info["path"] >= 2 else 0)
+    return {
+        "workload": f"{name}: N={wl.N}, K={wl.K}, I={wl.I}, B={B} signals per exec, outputs J, |J|^2, P-hat",
+        "dtype": "f64" if precision == 64 else "f32", "exec_path": info["path"], "nf": info["nf"],
+        "kernel_width": info["width"], "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_exec": ms,
+        "us_per_signal": 1e3 * ms / B, "steps": steps, "warmup": warmup,
+        "l2": "flushed between timed steps (512 MiB write + read-back)",
+        "tapers": "FP64 GEP on the GPU" if gep else "seeded taper-shaped rows",
+        "plan_seconds": t_plan,
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one signal, {nb} of {wl.I} band centres, {dt:.1f} s wall"},
+        "parity": gpu_parity(wl, precision, info["path"], info["chunk"], 0.0, dev, sample, "JEP"),
+    }
 
 
 def run_ours(args):
@@ -685,95 +920,51 @@ def run_ours(args):
         if klaunch[i] == 0:
             continue
         avg_ms = kms[i] / klaunch[i]
-        byts = algorithmic_bytes(info, n, B if (hoisted and n == "spread") else per_launch, csz, rsz, args.outputs)
+        nbl = B if (hoisted and n == "spread") else per_launch
+        byts = algorithmic_bytes(info, n, nbl, csz, rsz, args.outputs)
+        hb = hbm_bytes(info, n, nbl, csz, rsz, args.outputs)
         kern[n] = {"launches": int(klaunch[i]), "total_ms": float(kms[i]), "avg_us": 1e3 * avg_ms,
-                   "alg_bytes_per_launch": byts, "gbs": byts / (avg_ms * 1e-3) / 1e9,
-                   "frac_of_hbm_peak": byts / (avg_ms * 1e-3) / 1e9 / hbm_peak,
-                   # where the algorithmic bytes live: the FFT intermediates stay in L2, so their
-                   # fraction is an L2 rate measured against the HBM peak, not HBM efficiency
-                   "alg_bytes_in": {"spread": "HBM (samples, point records, tapers) and L2 (grids)",
-                                    "cols": "L2", "rows": "L2", "epi": "HBM", "pipe": "HBM"}.get(n, "HBM"),
+                   "signals_per_launch": nbl,
+                   # all compulsory bytes (HBM and L2): the FFT intermediates stay in L2, so this
+                   # rate is not an HBM efficiency for spread, cols and rows
+                   "alg_bytes_per_launch": byts, "alg_gbs": byts / (avg_ms * 1e-3) / 1e9,
+                   # only the bytes that must cross HBM (inputs from device memory and the outputs),
+                   # against the measured HBM copy peak
+                   "hbm_bytes_per_launch": hb, "hbm_gbs": hb / (avg_ms * 1e-3) / 1e9,
+                   "frac_of_hbm_peak": hb / (avg_ms * 1e-3) / 1e9 / hbm_peak,
                    "share": float(kms[i] / max(sum(kms), 1e-12))}
     dom = max(kern, key=lambda n: kern[n]["total_ms"]) if kern else None
     roofline = None
     if dom:
-        achieved = kern[dom]["gbs"]
+        achieved = kern[dom]["hbm_gbs"]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
-                    "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"],
+                    "alg_bytes_per_launch": kern[dom]["hbm_bytes_per_launch"],
                     "traffic": profiled_traffic(args.workload, dom, per_launch)}
 
     # ---- end to end through the public API with host buffers ----
-    # Every step copies its x from pinned host memory and reads its P-hat back to pinned host
-    # memory.  Steps are double-buffered the way a streaming caller would run them: step s+1's
-    # input is copied in on one copy stream and step s's P-hat read back on another while step s
-    # computes (the execs themselves stay ordered on one stream, as a plan requires).
-    e2e = None
+    # Every step copies its x from pinned host memory and reads back to pinned host memory every
+    # output the step declares (J, eigenspectra, P-hat, and the leakage estimates when asked for).
+    # Steps are double-buffered the way a streaming caller would run them: step s+1's input is
+    # copied in on one copy stream and step s's outputs read back on another while step s computes
+    # (the execs themselves stay ordered on one stream, as a plan requires).  A second measurement
+    # runs the PSD-only form (the exec writes and the host reads P-hat alone).
+    e2e = e2e_p = None
     if not args.no_e2e:
         xh = torch.from_numpy(wl.x.astype(np.float32 if args.precision == 32 else np.float64)).pin_memory()
-        ph = [torch.empty((B, wl.I), dtype=rdt).pin_memory() for _ in range(2)]
-        xd = [torch.empty_like(x) for _ in range(2)]
-        Pd = [P, torch.empty_like(P)]
-        cstream = torch.cuda.Stream(device=dev)  # device -> host
-        hstream = torch.cuda.Stream(device=dev)  # host -> device
-        out_bytes = B * wl.I * rsz + (B * wl.K * wl.I * csz if J is not None else 0) + \
-            (B * wl.K * wl.I * rsz if E is not None else 0)
-        d2h_done = [torch.cuda.Event() for _ in range(2)]
-        h2d_done = [torch.cuda.Event() for _ in range(2)]
-        step_done = [torch.cuda.Event() for _ in range(2)]
+        e2e = e2e_run(plan, torch, stream, dev, x, xh, {"J": J, "E": E, "P": P, "Lh": Lh, "Eh": Eh, "F": Fb},
+                      args.steps, world, barrier, B * units_per_signal, step_outputs=args.outputs)
+        e2e_p = e2e_run(plan, torch, stream, dev, x, xh, {"J": None, "E": None, "P": P, "Lh": None, "Eh": None},
+                        args.steps, world, barrier, B * units_per_signal, step_outputs="P")
 
-        def e2e_steps(n):
-            go = torch.cuda.Event()  # the first input's copy starts when the compute stream gets here
-            go.record(stream)
-            hstream.wait_event(go)
-            with torch.cuda.stream(hstream):
-                xd[0].copy_(xh, non_blocking=True)
-                h2d_done[0].record(hstream)
-            for s_ in range(n):
-                b = s_ % 2
-                stream.wait_event(h2d_done[b])  # this step's x is in
-                stream.wait_event(d2h_done[b])  # P-hat buffer b was read back two steps ago
-                step(xd[b], Pd[b])
-                step_done[b].record(stream)
-                cstream.wait_event(step_done[b])
-                with torch.cuda.stream(cstream):
-                    ph[b].copy_(Pd[b], non_blocking=True)
-                    d2h_done[b].record(cstream)
-                if s_ + 1 < n:
-                    nb_ = (s_ + 1) % 2
-                    if s_ >= 1:
-                        hstream.wait_event(step_done[nb_])  # step s-1 is done with x buffer nb_
-                    with torch.cuda.stream(hstream):
-                        xd[nb_].copy_(xh, non_blocking=True)
-                        h2d_done[nb_].record(hstream)
-            stream.wait_stream(cstream)
-
-        for ev in d2h_done:
-            ev.record(stream)
-        e2e_steps(2)
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_steps(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = job_time_ms(float(e0.elapsed_time(e1)), world, dev)
-        e2e = {"value": job_throughput(B * units_per_signal, args.steps, world, e2e_ms), "unit": UNIT,
-               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
-               "d2h_bytes_per_step": int(ph[0].numel() * ph[0].element_size()),
-               "ms_per_step": e2e_ms / args.steps,
-               "overlap": "double-buffered: step s+1's x copy-in and step s's P-hat read-back overlap the execs of step s",
-               "l2": f"not flushed between steps: each step writes {out_bytes / 1e9:.2f} GB of outputs "
-                     f"({out_bytes / 129e6:.1f}x the 129 MB L2)"}
-
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, nb, dt, cores = cpu_oracle_rate(wl, args.cpu_seconds)
+        rate, nb, dt, cores, sample = cpu_oracle_rate(wl, args.cpu_seconds, n1=info["n1"] if info["path"] >= 2 else 0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.workload}: one signal, {nb} of {wl.I} band centres, direct FP64 sum, "
-                         f"{dt:.1f} s wall"}
+               "sample": f"{args.workload}: one signal, {nb} of {wl.I} band centres (the packed path's special "
+                         f"positions and random bands), direct FP64 sum, {dt:.1f} s wall"}
+        # the same sample is the parity reference of the timed path's outputs
+        parity = gpu_parity(wl, args.precision, info["path"], info["chunk"], args.sigma, dev, sample, args.outputs)
 
     if rank == 0:
         line = {
@@ -798,6 +989,8 @@ def run_ours(args):
             "kernels": kern,
             "pipe_stages": stage_split,
             "e2e": e2e,
+            "e2e_p_only": e2e_p,
+            "parity": parity,
             "cpu_baseline": cpu,
             "clocks": clk,
             "plan_seconds": t_plan,
@@ -805,8 +998,24 @@ def run_ours(args):
             "taper_design": "taper-shaped inputs" if args.skip_gep else args.taper_design,
             "wall_seconds_timed": wall,
         }
+        if world == 1 and args.workload == "jitter16k" and not args.no_extras:
+            # the metric's own comparisons, measured in the same run: the batched form of the
+            # uneven-batch workload and the served form of the serving workload against the plain
+            # per-signal / per-request path on the same GPU, and the FP64 path
+            plan.close()
+            plan = None
+            torch.cuda.empty_cache()
+            line["batched"] = measure_uneven(2048, 5, 3, local, seed=0)
+            torch.cuda.empty_cache()
+            line["served"] = measure_serve(2000, 2000.0, local, seed=0)
+            torch.cuda.empty_cache()
+            line["fp64"] = {
+                "grid1024": measure_secondary("grid1024", 64, 1, 20, 5, local, 1.0, gep=True),
+                "jitter16k": measure_secondary("jitter16k", 64, 4, 5, 3, local, 3.0, gep=False),
+            }
         print(json.dumps(line), flush=True)
-    plan.close()
+    if plan is not None:
+        plan.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -188,32 +188,49 @@ __global__ void leakage_const_kernel(int K, int64_t I, const double* __restrict_
 }
 
 // General sampling, small problems: D_k^i = sum_{n,m} w_n w_m R(B|n,m) cos(2 pi f_i (t_n - t_m))
-// evaluated directly (App. B, Eq. lambda_hat_ki); one thread per band.
-__global__ void leakage_direct_kernel(int N, int K, int64_t I, const double* __restrict__ tc,
-                                      const double* __restrict__ w /*[K][N] sorted*/, double fmax,
-                                      double f_lo, double df, const double* __restrict__ lam, double fw,
-                                      double* __restrict__ L, double* __restrict__ Eh) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= I) return;
+// evaluated directly (App. B, Eq. lambda_hat_ki).  One CTA per band: the threads split the rows n
+// (n = tid, tid + blockDim, ...; row n adds the diagonal term and twice the pairs m > n), then a
+// fixed-order tree reduction over the CTA gives D_k, so the result is the same on every run.
+constexpr int kLeakThreads = 256;
+__global__ void __launch_bounds__(kLeakThreads) leakage_direct_kernel(
+    int N, int K, int64_t I, const double* __restrict__ tc, const double* __restrict__ w /*[K][N] sorted*/,
+    double fmax, double f_lo, double df, const double* __restrict__ lam, double fw, double* __restrict__ L,
+    double* __restrict__ Eh) {
+    __shared__ double s_red[kLeakThreads];
+    __shared__ double s_D[kMaxK];
+    const int64_t i = blockIdx.x;
     const double f = f_lo + (double)i * df;
     double D[kMaxK];
     for (int k = 0; k < K; ++k) D[k] = 0.0;
-    for (int n = 0; n < N; ++n) {
+    for (int n = threadIdx.x; n < N; n += kLeakThreads) {
+        const double tn = tc[n];
         for (int k = 0; k < K; ++k) D[k] += w[(int64_t)k * N + n] * w[(int64_t)k * N + n] * 2.0 * fmax;
         for (int m = n + 1; m < N; ++m) {
-            const double d = tc[n] - tc[m];
+            const double d = tn - tc[m];
             const double r = sinpi(2.0 * fmax * d) / (kPi * d) * 2.0 * cospi(2.0 * f * d);
             for (int k = 0; k < K; ++k) D[k] += w[(int64_t)k * N + n] * w[(int64_t)k * N + m] * r;
         }
     }
-    double s = 0.0;
     for (int k = 0; k < K; ++k) {
-        const double lh = lam[k] * 2.0 * fw / D[k];
-        const double l = fabs(lam[k] - lh);
-        L[(int64_t)k * I + i] = l;
-        s += l;
+        s_red[threadIdx.x] = D[k];
+        __syncthreads();
+        for (int h = kLeakThreads / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) s_red[threadIdx.x] += s_red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_D[k] = s_red[0];
+        __syncthreads();
     }
-    Eh[i] = s / K;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double lh = lam[k] * 2.0 * fw / s_D[k];
+            const double l = fabs(lam[k] - lh);
+            L[(int64_t)k * I + i] = l;
+            s += l;
+        }
+        Eh[i] = s / K;
+    }
 }
 
 // Windowed leakage (general sampling at scale).  R(B|n,m) is the integral of
@@ -1202,8 +1219,8 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
             cudaMemcpy(dtc, tc.data(), N * sizeof(double), cudaMemcpyHostToDevice);
             cudaMemcpy(dw, w_sorted.data(), (size_t)K * N * sizeof(double), cudaMemcpyHostToDevice);
             cudaMemcpy(dl, p->lambda.data(), K * sizeof(double), cudaMemcpyHostToDevice);
-            leakage_direct_kernel<<<blocks, 128>>>((int)N, K, g.I, dtc, dw, fmax, g.f_lo, g.df, dl, f_w,
-                                                    p->d_Lhat, p->d_Ehat);
+            leakage_direct_kernel<<<(unsigned)g.I, kLeakThreads>>>((int)N, K, g.I, dtc, dw, fmax, g.f_lo, g.df,
+                                                                    dl, f_w, p->d_Lhat, p->d_Ehat);
             cudaError_t e = cudaDeviceSynchronize();
             cudaFree(dtc);
             cudaFree(dw);

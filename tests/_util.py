@@ -23,6 +23,10 @@ def rel_l2(a, b) -> float:
 TOL = {32: 1e-5, 64: 1e-10}
 C_BOUND = 1.0  # the constant of the element-wise bound (see the module docstring)
 
+# measured errors of the current session (written out by conftest.py when M2_PARITY_LOG names a file)
+PARITY_LOG = []
+CURRENT_TEST = [""]
+
 
 def seeded_tapers(K: int, N: int, seed: int) -> np.ndarray:
     from synth import taper_like
@@ -56,6 +60,16 @@ def elementwise_errors(Jg, Jr, l1, tol, Pg=None, Pr=None, Eg=None):
 def assert_elementwise(Jg, Jr, l1, tol, Pg=None, Pr=None, Eg=None):
     """Assert the element-wise bound on J (and P-hat, eigenspectra) at every compared band."""
     r = elementwise_errors(Jg, Jr, l1, tol, Pg, Pr, Eg)
+    entry = {"test": CURRENT_TEST[0], "tol": tol, "bands": int(np.shape(Jr)[-1]),
+             "elem_over_bound": r}
+    rel = {}
+    if Jg is not None:
+        rel["J"] = rel_l2(Jg, Jr)
+    if Pg is not None:
+        rel["P"] = rel_l2(Pg, Pr)
+        rel["P_max_abs_over_max"] = float(np.max(np.abs(np.asarray(Pg) - Pr)) / np.max(Pr))
+    entry["rel_l2"] = rel
+    PARITY_LOG.append(entry)
     for k, v in r.items():
         assert v <= 1.0, f"{k}: element-wise error {v:.3g} x the bound {C_BOUND} * {tol:g} * sum|w x|"
     return r

@@ -25,3 +25,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _parity_test_name(request):
+    from tests import _util
+    _util.CURRENT_TEST[0] = request.node.nodeid
+    yield
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("M2_PARITY_LOG")
+    if not path:
+        return
+    import json
+    from tests import _util
+    with open(path, "w") as f:
+        json.dump(_util.PARITY_LOG, f, indent=0)
