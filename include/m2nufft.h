@@ -261,7 +261,9 @@ m2_status m2nufft_exec_ftest(m2nufft_plan_t p, const void* x, int64_t B, void* J
  * (default), one launch per stage over all nsig signals (spread, column DFTs
  * per coset length, row FFTs, epilogue) with a workspace for every signal, or,
  * in batch mode 1, a single launch of the persistent pipelined kernel with a
- * workspace ring; the plans' own workspaces are not used.  Otherwise signals
+ * workspace ring, or, in batch mode 2, whichever of those forms measured
+ * fastest for this batch (see m2nufft_set_batch_mode); the plans' own
+ * workspaces are not used.  Otherwise signals
  * of different plans run concurrently on internal streams inside the graph
  * (signals of one plan in order).  Results are bit-identical to m2nufft_exec
  * on each signal's plan.  A plan in the batch must not be used by other work
@@ -272,9 +274,27 @@ m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs,
                              void* const* Js, void* const* Es, void* const* Ps, void* stream);
 
 /* Select how m2nufft_exec_batch runs all-packed batches (process-wide):
- * 0 = one launch per stage (default), 1 = one persistent pipelined kernel.
- * Returns the previous mode, or -1 for an invalid mode. */
+ * 0 = one launch per stage (default; spread 2 tiles per CTA, row FFTs 8 rows
+ * per CTA, epilogue tiles of 32 x 16 positions), 1 = one persistent pipelined
+ * kernel, 2 = autotuned: the first call for a batch (same plans and buffers)
+ * builds every candidate -- the stage-per-launch form with spread tiles per CTA
+ * 1, 2 or 4, rows per CTA 8 or 4 and epilogue tiles 32 x 16 or 16 x 16, and the
+ * persistent kernel -- times each on `stream` (one warm-up launch, then the
+ * mean of three; the batch's outputs are written each time, with the same bits
+ * whichever candidate runs) and caches the fastest; later calls replay it.
+ * That first call synchronises and cannot be captured (M2_ERR_ARG while
+ * `stream` is capturing).  Returns the previous mode, or -1 for an invalid
+ * mode. */
 int m2nufft_set_batch_mode(int mode);
+
+/* Report of the most recent batch tuned in batch mode 2: *n (in: capacity of
+ * the arrays, out: number of candidates timed, 13 for all-packed batches),
+ * config host [*n][4] or NULL: (batch mode 0 or 1, spread tiles per CTA,
+ * rows per CTA, epilogue tile height) of each candidate, and ms host [*n] or
+ * NULL: its measured milliseconds per batch.  The fastest is the one cached.
+ * No counterpart in the paper (an autotuning report).  Errors: M2_ERR_ARG for
+ * n == NULL or *n < 0. */
+m2_status m2nufft_get_batch_tuning(int* n, int* config, double* ms);
 
 /* Autotuning report of a plan made with m2_opts.tune = 1: *n candidate configurations (0 for
  * an untuned plan), their options (host [*n] or NULL; path 2/3, sigma, max_batch as tried) and the

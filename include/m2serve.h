@@ -14,7 +14,9 @@
  * through one set of stage launches (spread, column DFTs, row FFTs, epilogue
  * over all its requests, the work maps built per launch and copied with one
  * transfer, the workspace in the slot's arena): one H2D copy of the samples,
- * one D2H copy of the P-hats.  Otherwise requests are grouped by pattern, each
+ * one D2H copy of the P-hats; a launch that holds a single request runs its
+ * plan's own m2nufft_exec instead while that plan is in no other slot (no work
+ * maps to stage).  Otherwise requests are grouped by pattern, each
  * group is one m2nufft_exec, and a pattern is in at most one slot at a time (a
  * plan's workspace serves one launch at a time).  Results do not depend on the
  * launch a request lands in.

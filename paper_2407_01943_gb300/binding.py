@@ -65,6 +65,7 @@ EXPORTS = [
     ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
+    ("m2nufft_get_batch_tuning", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), _VP, _DP]),
     ("m2nufft_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), _VP, _DP]),
     ("m2nufft_get_tapers", ctypes.c_int, [_VP, _DP, _DP]),
     ("m2nufft_get_tapers_complex", ctypes.c_int, [_VP, _DP, _DP]),
@@ -378,11 +379,24 @@ def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: 
 
 def set_batch_mode(mode: int) -> int:
     """0 = all-packed exec_batch as one launch per stage (default), 1 = one persistent
-    pipelined kernel; returns the previous mode."""
+    pipelined kernel, 2 = the fastest of those forms and CTA shapes, tuned on the first call for a
+    batch; returns the previous mode."""
     prev = int(load().m2nufft_set_batch_mode(int(mode)))
     if prev < 0:
         raise ValueError(load().m2nufft_last_error().decode())
     return prev
+
+
+def batch_tuning():
+    """Candidates of the most recently tuned batch (batch mode 2): a list of
+    ((mode, spread tiles per CTA, rows per CTA, epilogue tile height), ms per batch)."""
+    n = ctypes.c_int(0)
+    _check(load().m2nufft_get_batch_tuning(ctypes.byref(n), None, None), "m2nufft_get_batch_tuning")
+    cfg = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    ms = np.zeros(max(n.value, 1))
+    _check(load().m2nufft_get_batch_tuning(ctypes.byref(n), cfg.ctypes.data_as(ctypes.c_void_p), _dptr(ms)),
+           "m2nufft_get_batch_tuning")
+    return [(tuple(int(v) for v in cfg[i]), float(ms[i])) for i in range(n.value)]
 
 
 def batch_pipe_profile():

@@ -98,15 +98,24 @@ m2_status solve_gep_subband(const std::vector<double>& ts, double f_w, int K, do
 // Interpolated-DPSS nominal tapers (spline_tapers.cu): ts sorted; w_sorted [K][N], lam [K].
 m2_status spline_tapers(const std::vector<double>& ts, double fmax, double fw, int K,
                         std::vector<double>& w_sorted, std::vector<double>& lam, double& seconds);
+// M2_ERR_TIMEOUT (once) if a packed stage kernel of plan p gave up a bounded wait since the last check.
+m2_status check_stage_status(m2nufft_plan_s* p);
 // Packed FP32 path (fast.cu): one chunk of nb signals.
 m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, float* E, float* P, float* F,
                           cudaStream_t st, int lane = 0, const float2* g_pre = nullptr);
 // spread grids of nb signals (packed path) into g_out [nb][Kp][Lg]
 m2_status spread_fast(m2nufft_plan_s* p, const float* x, int nb, float2* g_out, cudaStream_t st);
-// Stage-batched executor of uneven batches of packed plans (hbatch.cu).
+// Stage-batched executor of uneven batches of packed plans (hbatch.cu).  CTA shapes of its stage
+// launches (every shape gives the same bits): spread tiles per CTA (1, 2, 4), row FFTs per CTA
+// (4, 8), epilogue tile height T1 (16, 32; tiles T1 x 16, one position per thread).
+struct HBConfig {
+    int spread_tiles = 2;
+    int row_warps = 8;
+    int epi_t1 = 32;
+};
 struct HBatch;
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                        void* const* Es, void* const* Ps, HBatch** out);
+                        void* const* Es, void* const* Ps, const HBConfig& cfg, HBatch** out);
 m2_status hbatch_run(HBatch* H, cudaStream_t st);
 int hbatch_launches(const HBatch* H);
 void hbatch_free(HBatch* H);
@@ -197,6 +206,10 @@ struct m2nufft_plan_s {
     // status word [abort, status, item] that a launch writes if a wait gives up
     std::map<int64_t, m2::PipeLaunch*> pipe_cache;
     int* pipe_status = nullptr;
+    // packed path: mapped pinned status word [flag, code, where, 0] that a stage kernel whose bounded
+    // wait gave up writes (d_stage_status is its device address); exec reports it once
+    int* stage_status = nullptr;
+    int* d_stage_status = nullptr;
     // autotuning at plan time: the candidate configurations and their measured ms per exec
     std::vector<m2_opts> tune_opts;
     std::vector<double> tune_ms;

@@ -524,6 +524,18 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     return M2_OK;
 }
 
+m2_status check_stage_status(m2nufft_plan_s* p) {
+    int* h = p->stage_status;
+    if (h && ((volatile int*)h)[0] != 0) {
+        const int where = ((volatile int*)h)[2];
+        h[0] = h[1] = h[2] = 0;
+        set_error("an earlier launch of a packed stage kernel gave up waiting for a bulk copy (row %d; "
+                  "M2_ERR_TIMEOUT)", where);
+        return M2_ERR_TIMEOUT;
+    }
+    return M2_OK;
+}
+
 struct DeviceGuard {
     int prev = -1;
     bool changed = false;
@@ -560,6 +572,7 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
         set_error("m2nufft_exec_ftest: the F-statistic is formed for full-band plans (real tapers, f_c0 = 0)");
         return M2_ERR_ARG;
     }
+    M2_TRY(check_stage_status(p));
     if (B > 0) {
         if (p->precision == 32) M2_TRY(exec_typed<float>(p, x, B, J, E, P, F, st));
         else M2_TRY(exec_typed<double>(p, x, B, J, E, P, F, st));
@@ -667,8 +680,18 @@ void drop_entry(GraphEntry& e) {
     if (e.hb) hbatch_free(e.hb);
 }
 
-// How all-packed batches run: 0 = stage-batched launches, 1 = one persistent-kernel launch.
+// How all-packed batches run: 0 = stage-batched launches, 1 = one persistent-kernel launch,
+// 2 = whichever form and stage-batched CTA shapes measured fastest for the batch (tuned on the
+// first call for the batch's signature, then cached with its graph).
 std::atomic<int> g_batch_mode{0};
+
+// The candidates and their measured times of the most recently tuned batch (guarded by g_batch_mu).
+struct BatchTuneRow {
+    int mode;
+    HBConfig cfg;
+    double ms;
+};
+std::vector<BatchTuneRow> g_batch_tuning;
 
 std::mutex g_batch_mu;
 BatchResources g_batch_res[64];
@@ -765,6 +788,88 @@ m2_status capture_packed_batch(PipeLaunch* L, HBatch* H, BatchResources& r, cuda
     return st;
 }
 
+// Tuning of an all-packed batch: every stage-batched CTA shape (spread tiles per CTA 1 / 2 / 4,
+// rows per CTA 8 / 4, epilogue tiles 32 x 16 / 16 x 16) and the persistent kernel are built,
+// captured and timed on `st` (one warm-up launch, then the mean of three, CUDA events); the
+// fastest is kept (its resources returned), the others freed.  Every candidate writes the same
+// bits.  Synchronous; not allowed while `st` is capturing.
+m2_status tune_packed_batch(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                            void* const* Es, void* const* Ps, BatchResources& r, cudaStream_t st,
+                            cudaGraphExec_t* out, PipeLaunch** out_pipe, HBatch** out_hb) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    M2_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("m2nufft_exec_batch: batch mode 2 tunes on the first call for a batch, which cannot be captured");
+        return M2_ERR_ARG;
+    }
+    std::vector<std::pair<int, HBConfig>> cands;
+    for (int nt : {1, 2, 4})
+        for (int rw : {8, 4})
+            for (int t1 : {32, 16}) cands.push_back({0, HBConfig{nt, rw, t1}});
+    cands.push_back({1, HBConfig{}});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    M2_CUDA_TRY(cudaEventCreate(&e0));
+    M2_CUDA_TRY(cudaEventCreate(&e1));
+    std::vector<BatchTuneRow> rows;
+    double best_ms = 1e300;
+    cudaGraphExec_t best = nullptr;
+    PipeLaunch* best_pipe = nullptr;
+    HBatch* best_hb = nullptr;
+    m2_status status = M2_OK;
+    for (const auto& c : cands) {
+        PipeLaunch* pipe = nullptr;
+        HBatch* hb = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        status = c.first == 1 ? pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe)
+                              : hbatch_create(plans, xs, nsig, Js, Es, Ps, c.second, &hb);
+        if (status == M2_OK) status = capture_packed_batch(pipe, hb, r, &ex);
+        float ms = 0.f;
+        cudaError_t e = cudaSuccess;
+        if (status == M2_OK) {
+            e = cudaGraphLaunch(ex, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                set_error("m2nufft_exec_batch tuning: %s", cudaGetErrorString(e));
+                status = M2_ERR_CUDA;
+            }
+            if (status == M2_OK && pipe) status = pipe_check(pipe);
+        }
+        const double t = ms / 3.0;
+        if (status == M2_OK) rows.push_back(BatchTuneRow{c.first, c.second, t});
+        if (status == M2_OK && t < best_ms) {
+            if (best) cudaGraphExecDestroy(best);
+            if (best_pipe) pipe_free(best_pipe);
+            if (best_hb) hbatch_free(best_hb);
+            best_ms = t;
+            best = ex;
+            best_pipe = pipe;
+            best_hb = hb;
+        } else {
+            if (ex) cudaGraphExecDestroy(ex);
+            if (pipe) pipe_free(pipe);
+            if (hb) hbatch_free(hb);
+        }
+        if (status != M2_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != M2_OK) {
+        if (best) cudaGraphExecDestroy(best);
+        if (best_pipe) pipe_free(best_pipe);
+        if (best_hb) hbatch_free(best_hb);
+        return status;
+    }
+    g_batch_tuning = rows;
+    *out = best;
+    *out_pipe = best_pipe;
+    *out_hb = best_hb;
+    return M2_OK;
+}
+
 }  // namespace
 
 // Drop cached batch graphs that reference plan p (called before p is freed).
@@ -837,9 +942,11 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     m2::HBatch* hb = nullptr;
     bool all_packed = plans[0]->precision == 32;
     for (int64_t s = 0; s < nsig && all_packed; ++s) all_packed = plans[s]->g.path >= 2;
-    if (all_packed) {
+    if (all_packed && mode == 2) {
+        M2_TRY(m2::tune_packed_batch(plans, xs, nsig, Js, Es, Ps, *res, st, &exec, &pipe, &hb));
+    } else if (all_packed) {
         if (mode == 1) M2_TRY(m2::pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
-        else M2_TRY(m2::hbatch_create(plans, xs, nsig, Js, Es, Ps, &hb));
+        else M2_TRY(m2::hbatch_create(plans, xs, nsig, Js, Es, Ps, m2::HBConfig{}, &hb));
         const m2_status cs = m2::capture_packed_batch(pipe, hb, *res, &exec);
         if (cs != M2_OK) {
             if (pipe) m2::pipe_free(pipe);
@@ -902,9 +1009,32 @@ extern "C" m2_status m2nufft_get_timing(m2nufft_plan_t p, double* ms, int64_t* l
 
 extern "C" int m2nufft_set_batch_mode(int mode) {
     m2::clear_error();
-    if (mode != 0 && mode != 1) {
-        m2::set_error("m2nufft_set_batch_mode: mode must be 0 or 1");
+    if (mode < 0 || mode > 2) {
+        m2::set_error("m2nufft_set_batch_mode: mode must be 0, 1 or 2");
         return -1;
     }
     return m2::g_batch_mode.exchange(mode);
+}
+
+extern "C" m2_status m2nufft_get_batch_tuning(int* n, int* config, double* ms) {
+    m2::clear_error();
+    if (!n || *n < 0) {
+        m2::set_error("m2nufft_get_batch_tuning: n must point to the capacity (>= 0)");
+        return M2_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(m2::g_batch_mu);
+    const int cnt = (int)m2::g_batch_tuning.size();
+    const int m = std::min(*n, cnt);
+    for (int i = 0; i < m; ++i) {
+        const auto& r = m2::g_batch_tuning[(size_t)i];
+        if (config) {
+            config[4 * i + 0] = r.mode;
+            config[4 * i + 1] = r.cfg.spread_tiles;
+            config[4 * i + 2] = r.cfg.row_warps;
+            config[4 * i + 3] = r.cfg.epi_t1;
+        }
+        if (ms) ms[i] = r.ms;
+    }
+    *n = cnt;
+    return M2_OK;
 }

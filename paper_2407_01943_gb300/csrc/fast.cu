@@ -82,6 +82,7 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     c.deconv = reinterpret_cast<const float2*>(p->d_deconv);
     c.wsum = reinterpret_cast<const float*>(p->d_wsum);
     c.wq = (float)p->wq;
+    c.status = p->d_stage_status;
     return c;
 }
 

@@ -30,10 +30,7 @@ using packed::Ctx;
 using packed::Tw32;
 using packed::kRowLen;
 
-constexpr int kEpiThreads = 256;  // one 32 x 16 epilogue tile per CTA
 constexpr int kColThreads = 128;  // 4 warps: one group of 4 warps, or 4 one-warp groups
-constexpr int kRowWarps = 8;
-constexpr int kSpreadTiles = 2;  // spread tiles per CTA
 
 struct __align__(16) HTask {
     const float* x;
@@ -57,9 +54,9 @@ __device__ __forceinline__ void load_task(const HTask* tasks, const Ctx* ctxs, i
     __syncthreads();
 }
 
-// map entry: (task, first tile, tiles); up to kSpreadTiles tiles per CTA amortise the
-// dependent loads (tile bounds, point records, samples) over more cells
-template <int KP>
+// map entry: (task, first tile, tiles); up to NT tiles per CTA amortise the dependent loads
+// (tile bounds, point records, samples) over more cells
+template <int KP, int NT>
 __global__ void __launch_bounds__(kSpreadTile) hb_spread_kernel(const int4* __restrict__ map, const HTask* tasks,
                                                                 const Ctx* ctxs, float2* ws) {
     __shared__ __align__(16) unsigned char smem[packed::spread_smem_bytes(KP)];
@@ -67,7 +64,7 @@ __global__ void __launch_bounds__(kSpreadTile) hb_spread_kernel(const int4* __re
     __shared__ __align__(16) HTask s_task;
     const int4 m = map[blockIdx.x];
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
-    packed::spread_tiles<KP, kSpreadTiles>(s_ctx, s_task.x, m.y, m.z, ws + s_task.g_off, smem);
+    packed::spread_tiles<KP, NT>(s_ctx, s_task.x, m.y, m.z, ws + s_task.g_off, smem);
 }
 
 // map entry: (task, pair, first column, warps per 32-column group); the CTA's 4 warps form
@@ -92,10 +89,10 @@ __global__ void __launch_bounds__(kColThreads) hb_cols_kernel(const int4* __rest
                           s_tw + c.n1 + (size_t)grp * packed::cols_group_f2(c.rows, F));
 }
 
-// map entry: (task, pair, first row, rows)
-__global__ void __launch_bounds__(32 * kRowWarps, 2) hb_rows_kernel(const int4* __restrict__ map,
-                                                                     const HTask* tasks, const Ctx* ctxs, Tw32 tw,
-                                                                     float2* ws) {
+// map entry: (task, pair, first row, rows); one warp per row, R rows per CTA
+template <int R>
+__global__ void __launch_bounds__(32 * R, 16 / R) hb_rows_kernel(const int4* __restrict__ map, const HTask* tasks,
+                                                                 const Ctx* ctxs, Tw32 tw, float2* ws) {
     extern __shared__ float2 smem_f2[];
     __shared__ __align__(16) Ctx s_ctx;
     __shared__ __align__(16) HTask s_task;
@@ -103,18 +100,19 @@ __global__ void __launch_bounds__(32 * kRowWarps, 2) hb_rows_kernel(const int4* 
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
     const Ctx& c = s_ctx;
     float2* Z = ws + s_task.z_off + (int64_t)m.y * c.n1 * kRowLen;
-    packed::rowfft_rows<kRowWarps, true>(c, tw, Z, m.z, m.w, smem_f2);
+    packed::rowfft_rows<R, true>(c, tw, Z, m.z, m.w, smem_f2);
 }
 
-// map entry: (task, epilogue tile)
-__global__ void __launch_bounds__(kEpiThreads) hb_epi_kernel(const int2* __restrict__ map, const HTask* tasks,
-                                                             const Ctx* ctxs, const float2* ws) {
+// map entry: (task, epilogue tile); one T1 x 16 tile per CTA, one position per thread
+template <int T1>
+__global__ void __launch_bounds__(16 * T1) hb_epi_kernel(const int2* __restrict__ map, const HTask* tasks,
+                                                         const Ctx* ctxs, const float2* ws) {
     __shared__ __align__(16) Ctx s_ctx;
     __shared__ __align__(16) HTask s_task;
-    __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(32) / sizeof(float2)];
+    __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(T1) / sizeof(float2)];
     const int2 m = map[blockIdx.x];
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
-    packed::epi_tile<32, kEpiThreads, true, false, true>(s_ctx, ws + s_task.z_off, m.y, s_task.J, s_task.E, s_task.P,
+    packed::epi_tile<T1, 16 * T1, true, false, true>(s_ctx, ws + s_task.z_off, m.y, s_task.J, s_task.E, s_task.P,
                                                      nullptr, smem);
 }
 
@@ -133,6 +131,7 @@ m2_status upload_vec(std::vector<void*>& owned, T** dst, const std::vector<T>& v
 // Resources of one uneven batch (owned by the cached batch graph).
 struct HBatch {
     int device = 0;
+    HBConfig cfg;
     std::vector<void*> owned;
     Ctx* d_ctxs = nullptr;
     HTask* d_tasks = nullptr;
@@ -159,7 +158,8 @@ void hbatch_free(HBatch* h) { delete h; }
 m2_status init_hbatch_kernels(int smem_optin) {
     const void* funcs[] = {(const void*)hb_cols_kernel<2>,  (const void*)hb_cols_kernel<4>,
                            (const void*)hb_cols_kernel<8>,  (const void*)hb_cols_kernel<16>,
-                           (const void*)hb_cols_kernel<32>, (const void*)hb_rows_kernel};
+                           (const void*)hb_cols_kernel<32>, (const void*)hb_rows_kernel<4>,
+                           (const void*)hb_rows_kernel<8>};
     for (const void* f : funcs) {
         cudaFuncAttributes fa;
         M2_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
@@ -181,8 +181,9 @@ struct Maps {
     int64_t ws_f2 = 0;  // workspace, float2 units
 };
 
-// Append task `task` of context c (geometry g) to the maps; its workspace goes at the end.
-void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
+// Append task `task` of context c (geometry g) to the maps, in the CTA shapes of cfg; its
+// workspace goes at the end.
+void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const HBConfig& cfg) {
     auto take = [&](int64_t n) {  // 256-byte aligned sections
         const int64_t o = m.ws_f2;
         m.ws_f2 += (n + 31) / 32 * 32;
@@ -190,10 +191,11 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
     };
     t.g_off = take((int64_t)c.Kp * c.Lg);
     t.z_off = take((int64_t)c.Kp * c.n1 * kRowLen);
-    // spread: kSpreadTiles tiles per CTA
+    // spread: cfg.spread_tiles tiles per CTA
     const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
-    for (int64_t tile = 0; tile < ntiles; tile += kSpreadTiles)
-        m.sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(kSpreadTiles, ntiles - tile), 0));
+    const int nt = cfg.spread_tiles;
+    for (int64_t tile = 0; tile < ntiles; tile += nt)
+        m.sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(nt, ntiles - tile), 0));
     // column DFTs: one coset per warp where the C = n1 / F cosets allow it (C = 1: four one-warp
     // groups per CTA, C = 2: two two-warp groups), else one four-warp group sharing the cosets
     const int C = c.n1 / c.F;
@@ -203,11 +205,12 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t) {
         for (int col = 0; col < kRowLen; col += 32 * (4 / gw)) m.co[lf].push_back(make_int4(task, j, col, gw));
     m.smem_cols[lf] = std::max(m.smem_cols[lf], sizeof(float2) * ((size_t)c.n1 + (size_t)(4 / gw) *
                                                                    packed::cols_group_f2(c.rows, c.F)));
-    // row FFTs: up to 8 rows per CTA
+    // row FFTs: up to cfg.row_warps rows per CTA
+    const int rw = cfg.row_warps;
     for (int j = 0; j < c.Kp; ++j)
-        for (int r0 = 0; r0 < c.n1; r0 += kRowWarps) m.ro.push_back(make_int4(task, j, r0, std::min(kRowWarps, c.n1 - r0)));
-    // epilogue: one 32 x 16 tile per CTA
-    const int ntile = packed::epi_tiles(c.n1, c.k2max, 32);
+        for (int r0 = 0; r0 < c.n1; r0 += rw) m.ro.push_back(make_int4(task, j, r0, std::min(rw, c.n1 - r0)));
+    // epilogue: one cfg.epi_t1 x 16 tile per CTA
+    const int ntile = packed::epi_tiles(c.n1, c.k2max, cfg.epi_t1);
     for (int e = 0; e < ntile; ++e) m.ep.push_back(make_int2(task, e));
 }
 
@@ -224,11 +227,18 @@ struct MapView {
     int n_ep = 0;
 };
 
+template <int NT>
+void launch_spread_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, float2* ws, cudaStream_t st) {
+    if (v.n_sp[0]) hb_spread_kernel<2, NT><<<v.n_sp[0], kSpreadTile, 0, st>>>(v.sp[0], tasks, ctxs, ws);
+    if (v.n_sp[1]) hb_spread_kernel<4, NT><<<v.n_sp[1], kSpreadTile, 0, st>>>(v.sp[1], tasks, ctxs, ws);
+    if (v.n_sp[2]) hb_spread_kernel<8, NT><<<v.n_sp[2], kSpreadTile, 0, st>>>(v.sp[2], tasks, ctxs, ws);
+}
+
 m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, const Tw32& tw, float2* ws,
-                      cudaStream_t st) {
-    if (v.n_sp[0]) hb_spread_kernel<2><<<v.n_sp[0], kSpreadTile, 0, st>>>(v.sp[0], tasks, ctxs, ws);
-    if (v.n_sp[1]) hb_spread_kernel<4><<<v.n_sp[1], kSpreadTile, 0, st>>>(v.sp[1], tasks, ctxs, ws);
-    if (v.n_sp[2]) hb_spread_kernel<8><<<v.n_sp[2], kSpreadTile, 0, st>>>(v.sp[2], tasks, ctxs, ws);
+                      const HBConfig& cfg, cudaStream_t st) {
+    if (cfg.spread_tiles == 1) launch_spread_maps<1>(v, tasks, ctxs, ws, st);
+    else if (cfg.spread_tiles == 4) launch_spread_maps<4>(v, tasks, ctxs, ws, st);
+    else launch_spread_maps<2>(v, tasks, ctxs, ws, st);
     M2_CUDA_TRY(cudaGetLastError());
     for (int k = 1; k < 6; ++k) {
         if (!v.n_co[k]) continue;
@@ -243,11 +253,14 @@ m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, con
         M2_CUDA_TRY(cudaGetLastError());
     }
     if (v.n_ro) {
-        hb_rows_kernel<<<v.n_ro, 32 * kRowWarps, packed::rowfft_smem_bytes(kRowWarps), st>>>(v.ro, tasks, ctxs, tw, ws);
+        if (cfg.row_warps == 4)
+            hb_rows_kernel<4><<<v.n_ro, 32 * 4, packed::rowfft_smem_bytes(4), st>>>(v.ro, tasks, ctxs, tw, ws);
+        else hb_rows_kernel<8><<<v.n_ro, 32 * 8, packed::rowfft_smem_bytes(8), st>>>(v.ro, tasks, ctxs, tw, ws);
         M2_CUDA_TRY(cudaGetLastError());
     }
     if (v.n_ep) {
-        hb_epi_kernel<<<v.n_ep, kEpiThreads, 0, st>>>(v.ep, tasks, ctxs, ws);
+        if (cfg.epi_t1 == 16) hb_epi_kernel<16><<<v.n_ep, 16 * 16, 0, st>>>(v.ep, tasks, ctxs, ws);
+        else hb_epi_kernel<32><<<v.n_ep, 16 * 32, 0, st>>>(v.ep, tasks, ctxs, ws);
         M2_CUDA_TRY(cudaGetLastError());
     }
     return M2_OK;
@@ -256,9 +269,15 @@ m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, con
 }  // namespace
 
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                        void* const* Es, void* const* Ps, HBatch** out) {
+                        void* const* Es, void* const* Ps, const HBConfig& cfg, HBatch** out) {
+    if (!(cfg.spread_tiles == 1 || cfg.spread_tiles == 2 || cfg.spread_tiles == 4) ||
+        !(cfg.row_warps == 4 || cfg.row_warps == 8) || !(cfg.epi_t1 == 16 || cfg.epi_t1 == 32)) {
+        set_error("internal: unsupported stage-batched CTA shapes");
+        return M2_ERR_ARG;
+    }
     std::unique_ptr<HBatch> H(new HBatch());
     H->device = plans[0]->device;
+    H->cfg = cfg;
     H->tw = packed::make_tw32();
     std::vector<Ctx> ctxs;
     std::map<const m2nufft_plan_s*, int> index;
@@ -278,7 +297,7 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
         t.P = Ps ? static_cast<float*>(Ps[s]) : nullptr;
         t.ctx = f->second;
         t.pad0 = t.pad1 = t.pad2 = 0;
-        add_task(m, (int)s, ctxs[(size_t)f->second], p->g.ntiles, t);
+        add_task(m, (int)s, ctxs[(size_t)f->second], p->g.ntiles, t, cfg);
     }
     const int64_t off = m.ws_f2;
     std::vector<int4>* sp = m.sp;
@@ -323,7 +342,7 @@ m2_status hbatch_run(HBatch* H, cudaStream_t st) {
     v.n_ro = H->n_rows;
     v.ep = H->d_epi;
     v.n_ep = H->n_epi;
-    return launch_maps(v, H->d_tasks, H->d_ctxs, H->tw, H->ws, st);
+    return launch_maps(v, H->d_tasks, H->d_ctxs, H->tw, H->ws, H->cfg, st);
 }
 
 int hbatch_launches(const HBatch* H) {
@@ -367,14 +386,14 @@ void hserve_free(HServe* H) { delete H; }
 size_t hserve_ws_bytes(const HServe* H, int plan) {
     Maps m;
     HTask t{};
-    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t);
+    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t, HBConfig{});
     return sizeof(float2) * (size_t)m.ws_f2;
 }
 
 size_t hserve_map_bytes(const HServe* H, int plan) {
     Maps m;
     HTask t{};
-    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t);
+    add_task(m, 0, H->ctxs[plan], H->ntiles[plan], t, HBConfig{});
     size_t b = sizeof(HTask);
     for (auto& v : m.sp) b += sizeof(int4) * v.size();
     for (auto& v : m.co) b += sizeof(int4) * v.size();
@@ -395,7 +414,7 @@ m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x
         t.P = P[r];
         t.ctx = plan[r];
         t.pad0 = t.pad1 = t.pad2 = 0;
-        add_task(m, r, H->ctxs[plan[r]], H->ntiles[plan[r]], t);
+        add_task(m, r, H->ctxs[plan[r]], H->ntiles[plan[r]], t, HBConfig{});
     }
     // staging layout: tasks, then the maps, each section 16-byte aligned
     size_t off = 0;
@@ -431,7 +450,7 @@ m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x
     v.n_ro = (int)m.ro.size();
     v.ep = reinterpret_cast<const int2*>(dstage + oep);
     v.n_ep = (int)m.ep.size();
-    return launch_maps(v, reinterpret_cast<const HTask*>(dstage + ot), H->d_ctxs, H->tw, ws, st);
+    return launch_maps(v, reinterpret_cast<const HTask*>(dstage + ot), H->d_ctxs, H->tw, ws, HBConfig{}, st);
 }
 
 }  // namespace m2

@@ -98,6 +98,7 @@ struct __align__(16) Ctx {
     const float2* deconv;  // [I]
     const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
     float wq;              // sum_k W_k^0(0)^2
+    int* status;           // mapped host word [flag, code, where, 0] set by a stage whose bounded wait gave up
 };
 
 // Drop a dead 128-byte line of an intermediate from L2 without writing it back (its contents
@@ -366,6 +367,68 @@ __device__ __forceinline__ void rowfft_row(const Ctx& c, const Tw32& tw, float2*
     for (int q = 0; q < 32; ++q) {
         const int k2 = lane + 32 * brev(q, 5);
         if (k2 < nlo || k2 >= kRowLen - nlo) __stcg(Zr + k2, v[q]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies into shared memory (cp.async.bulk, the 1-D form of the tensor memory
+// accelerator's copies), completed on an mbarrier, and the bounded waits on it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes the barrier initialisation visible to the asynchronous proxy that completes it
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier shared-memory accesses (generic proxy) before later bulk copies
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// L2 policy for data read once: evict first
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes a multiple of 16; the
+// transaction count of `bar` is raised by `bytes` first, so one call arms the barrier's phase
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ long long gtimer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr long long kStageWaitNs = 2000000000LL;  // 2 s: a copy that has not landed by then never will
+// Wait for the phase with this parity to complete; false if it has not within kStageWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = gtimer_ns();
+    while (!mbar_test(bar, parity))
+        if (gtimer_ns() - t0 > kStageWaitNs) return false;
+    return true;
+}
+// Record a stage that gave up waiting (the host reads the word at the plan's next exec).
+__device__ __forceinline__ void stage_timeout(int* status, int where) {
+    if (!status) return;
+    if (atomicExch(status, 1) == 0) {
+        status[1] = (int)M2_ERR_TIMEOUT;
+        status[2] = where;
+        __threadfence_system();
     }
 }
 

@@ -356,6 +356,7 @@ void free_plan(m2nufft_plan_s* p) {
         if (p->d_gall) cudaFree(p->d_gall);
         if (p->gall_ev) cudaEventDestroy(p->gall_ev);
         if (p->pipe_status) cudaFreeHost(p->pipe_status);
+        if (p->stage_status) cudaFreeHost(p->stage_status);
         if (p->d_pipe_prof) cudaFree(p->d_pipe_prof);
         for (void* d : p->allocations) cudaFree(d);
         for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -1105,6 +1106,9 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
             }
             M2_TRY_OR(upload_complex(pb, p->precision, &p->d_tw1024, t32));
         }
+        M2_CUDA_TRY_OR(cudaHostAlloc(reinterpret_cast<void**>(&p->stage_status), 4 * sizeof(int), cudaHostAllocMapped));
+        std::memset(p->stage_status, 0, 4 * sizeof(int));
+        M2_CUDA_TRY_OR(cudaHostGetDevicePointer(reinterpret_cast<void**>(&p->d_stage_status), p->stage_status, 0));
         int64_t F = 1;
         while (F < 32 && g.n1 % (F * 2) == 0) F *= 2;
         g.colF = (int)F;

@@ -5,8 +5,10 @@
 // and completion by event polling.  When every plan is a packed FP32 plan, a
 // launch runs all its requests, whatever their sampling patterns, through the
 // stage-batched kernels (one set of stage launches over the launch's requests,
-// work maps built per launch, workspace in the slot's arena); otherwise the
-// requests are grouped by pattern and each group is one m2nufft_exec.
+// work maps built per launch, workspace in the slot's arena) -- except a launch of
+// a single request, which runs its plan's own exec when that plan is not in use in
+// another slot; otherwise the requests are grouped by pattern and each group is one
+// m2nufft_exec.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -430,7 +432,11 @@ extern "C" m2_status m2serve_run_trace(m2serve_t s, int64_t nreq, const int32_t*
                 keep.pop_back();
             }
             if (!take.empty()) {
-                if (cross) M2_TRY(run.launch_cross(free_slot, take));
+                // a launch of one request goes through its plan's own exec (no work maps to stage
+                // and upload) unless that plan's workspace is busy in another slot; both forms give
+                // the same bits
+                if (cross && !(take.size() == 1 && run.pattern_slot[pattern[take[0]]] < 0))
+                    M2_TRY(run.launch_cross(free_slot, take));
                 else M2_TRY(run.launch(free_slot, take));
                 continue;
             }

@@ -903,7 +903,7 @@ def _uneven_subset(ws, n, seed):
     return sorted(pick | set(int(s) for s in rest[: n - len(pick)]))
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["stage_batched", "persistent"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["stage_batched", "persistent", "tuned"])
 def test_uneven_2048_batch_against_oracle(dev, mode):
     """The uneven-batch workload at its size: 2048 signals (grid length log-uniform in
     [1024, 16384], Markov gaps, K in {4, 6, 8}, I = 4G) planned with taper-shaped inputs and run as
@@ -929,8 +929,8 @@ def test_uneven_2048_batch_against_oracle(dev, mode):
         torch.cuda.synchronize()
         got = {s: {"J": Js[s].cpu().numpy()[None], "E": Es[s].cpu().numpy()[None], "P": Ps[s].cpu().numpy()[None]}
                for s in sub}
-        if mode == 1:
-            pkg.binding.set_batch_mode(1)
+        if mode in (1, 2):
+            pkg.binding.set_batch_mode(mode)
             for J in Js:
                 J.zero_()
             pkg.exec_batch(plans, xs, Js, Es, Ps)
@@ -938,6 +938,10 @@ def test_uneven_2048_batch_against_oracle(dev, mode):
             for s in sub:
                 assert np.array_equal(Js[s].cpu().numpy()[None], got[s]["J"]), s
                 assert np.array_equal(Ps[s].cpu().numpy()[None], got[s]["P"]), s
+        if mode == 2:
+            rep = pkg.binding.batch_tuning()
+            assert len(rep) == 13 and all(ms > 0 for _, ms in rep)
+            assert {c[0] for c, _ in rep} == {0, 1}
     finally:
         pkg.binding.set_batch_mode(prev)
     worst = {}
@@ -951,3 +955,40 @@ def test_uneven_2048_batch_against_oracle(dev, mode):
     assert set(worst) == {"J", "P", "E"}
     for p in plans:
         p.close()
+
+
+def test_exec_batch_tuned_mode_bitwise_and_report(dev):
+    """Batch mode 2: the first call times every stage-batched CTA shape and the persistent kernel
+    and keeps the fastest; the report lists the 13 candidates, and the tuned batch (first call and
+    replay) equals per-signal exec bit for bit."""
+    ws = synth.batched_uneven(9, seed=31, n_min=300, n_max=6000)
+    plans, xs, Js, Es, Ps = [], [], [], [], []
+    for s_, wl in enumerate(ws):
+        plans.append(pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                              tapers=seeded_tapers(wl.K, wl.N, 60 + s_)))
+        xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
+        Js.append(torch.empty((wl.K, wl.I), dtype=torch.complex64, device=dev))
+        Es.append(torch.empty((wl.K, wl.I), dtype=torch.float32, device=dev))
+        Ps.append(torch.empty((wl.I,), dtype=torch.float32, device=dev))
+    prev = pkg.binding.set_batch_mode(2)
+    try:
+        for rep in range(2):  # tune + keep the fastest, then replay the cached graph
+            for J in Js:
+                J.zero_()
+            pkg.exec_batch(plans, xs, Js, Es, Ps)
+            torch.cuda.synchronize()
+            for p, x, J, E, P in zip(plans, xs, Js, Es, Ps):
+                single = p.run(x[None, :], want=("J", "E", "P"))
+                torch.cuda.synchronize()
+                assert torch.equal(single["J"][0], J) and torch.equal(single["E"][0], E)
+                assert torch.equal(single["P"][0], P)
+        table = pkg.binding.batch_tuning()
+        assert len(table) == 13
+        cfgs = {c for c, _ in table}
+        assert (0, 2, 8, 32) in cfgs and (1, 2, 8, 32) in cfgs
+        assert {c[1] for c in cfgs if c[0] == 0} == {1, 2, 4}
+        assert all(0 < ms < 1e3 for _, ms in table)
+    finally:
+        pkg.binding.set_batch_mode(prev)
+    with pytest.raises(ValueError):
+        pkg.binding.set_batch_mode(3)
