@@ -24,6 +24,19 @@
 #include "common.cuh"
 
 namespace m2 {
+
+m2_status check_stage_status(m2nufft_plan_s* p) {
+    int* h = p->stage_status;
+    if (h && ((volatile int*)h)[0] != 0) {
+        const int where = ((volatile int*)h)[2];
+        h[0] = h[1] = h[2] = 0;
+        set_error("an earlier launch of a packed stage kernel gave up waiting for a bulk copy (row %d; "
+                  "M2_ERR_TIMEOUT)", where);
+        return M2_ERR_TIMEOUT;
+    }
+    return M2_OK;
+}
+
 namespace {
 
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
@@ -524,18 +537,6 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
     return M2_OK;
 }
 
-m2_status check_stage_status(m2nufft_plan_s* p) {
-    int* h = p->stage_status;
-    if (h && ((volatile int*)h)[0] != 0) {
-        const int where = ((volatile int*)h)[2];
-        h[0] = h[1] = h[2] = 0;
-        set_error("an earlier launch of a packed stage kernel gave up waiting for a bulk copy (row %d; "
-                  "M2_ERR_TIMEOUT)", where);
-        return M2_ERR_TIMEOUT;
-    }
-    return M2_OK;
-}
-
 struct DeviceGuard {
     int prev = -1;
     bool changed = false;
@@ -909,6 +910,7 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
             return M2_ERR_ARG;
         }
     }
+    for (int64_t s = 0; s < nsig; ++s) M2_TRY(m2::check_stage_status(plans[s]));
     const int dev = plans[0]->device;
     m2::DeviceGuard guard(dev);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -1015,6 +1015,10 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const int64_t ecta = opts.precision == 32 ? 8192 : 4096;
     g.cw = (int)std::max<int64_t>(1, std::min<int64_t>(g.n2, ecta / g.n1));
     g.rw = (int)std::max<int64_t>(1, std::min<int64_t>(g.n1, ecta / g.n2));
+    // small transforms: fewer columns / rows per CTA until one signal's pass has two CTAs per SM
+    // (each column and row is transformed on its own, so the shape does not change the result)
+    while (g.cw > 1 && (g.n2 / g.cw) * (int64_t)K < 2 * (int64_t)p->sm_count) g.cw /= 2;
+    while (g.rw > 1 && (g.n1 / g.rw) < 2 * (int64_t)p->sm_count) g.rw /= 2;
     const size_t csz = opts.precision == 32 ? 8 : 16;
     {
         // generic path: keep a chunk's workspace within L2.  Packed four-kernel path: 4 to 16
