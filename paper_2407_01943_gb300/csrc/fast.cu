@@ -83,6 +83,9 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     c.wsum = reinterpret_cast<const float*>(p->d_wsum);
     c.wq = (float)p->wq;
     c.status = p->d_stage_status;
+    c.tile_desc = p->d_tile_desc;
+    c.tile_blk = p->d_tile_blk;
+    c.ncap = p->spread_ncap;
     return c;
 }
 
@@ -106,6 +109,25 @@ __global__ void __launch_bounds__(kSpreadTile) spread_packed_kernel(Ctx c, const
                                       g + (int64_t)b0 * c.Kp * c.Lg, smem);
 }
 
+// the same with the tile's point block and sample runs copied in by cp.async.bulk (plans with tile
+// blocks); dynamic smem spread_bulk_smem_bytes(K, ncap, SB, 1)
+template <int KP, int SB>
+__global__ void __launch_bounds__(kSpreadTile) spread_bulk_kernel(Ctx c, const float* __restrict__ x, int nb,
+                                                                  float2* __restrict__ g) {
+    extern __shared__ __align__(16) unsigned char smem_sb[];
+    const int b0 = blockIdx.y * SB;
+    packed::spread_bulk<KP, SB, 1>(c, x + (int64_t)b0 * c.N, min(SB, nb - b0), blockIdx.x, 1,
+                                   g + (int64_t)b0 * c.Kp * c.Lg, smem_sb);
+}
+
+template <int KP, int SB>
+void launch_spread_sb(const Ctx& c, const float* x, int nb, float2* g, dim3 grid, cudaStream_t st) {
+    if (c.ncap > 0)
+        spread_bulk_kernel<KP, SB><<<grid, kSpreadTile, packed::spread_bulk_smem_bytes(c.K, c.ncap, SB, 1), st>>>(c, x,
+                                                                                                           nb, g);
+    else spread_packed_kernel<KP, SB><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
+}
+
 // Signals per CTA: the most (sharing the staging of a tile's points) that still give the launch
 // about two CTAs per SM; fewer when a chunk is small.
 template <int KP>
@@ -114,9 +136,9 @@ void launch_spread_packed(const Ctx& c, const float* x, int nb, float2* g, int s
     int sb = spread_signals(KP);
     while (sb > 1 && ntiles * ((nb + sb - 1) / sb) < 2 * (int64_t)sm_count) sb /= 2;
     dim3 grid((unsigned)ntiles, (unsigned)((nb + sb - 1) / sb));
-    if (sb >= 4) spread_packed_kernel<KP, spread_signals(KP) >= 4 ? 4 : 2><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
-    else if (sb == 2) spread_packed_kernel<KP, 2><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
-    else spread_packed_kernel<KP, 1><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
+    if (sb >= 4) launch_spread_sb<KP, spread_signals(KP) >= 4 ? 4 : 2>(c, x, nb, g, grid, st);
+    else if (sb == 2) launch_spread_sb<KP, 2>(c, x, nb, g, grid, st);
+    else launch_spread_sb<KP, 1>(c, x, nb, g, grid, st);
 }
 
 // grid (1024 / 32, Kp, nb): 32 columns of one taper pair per CTA of 4 warps
@@ -187,6 +209,17 @@ m2_status init_fast_kernels(int smem_optin) {
     };
     for (const void* f : funcs)
         M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+    const void* bulk[] = {
+        (const void*)spread_bulk_kernel<2, 1>, (const void*)spread_bulk_kernel<2, 2>, (const void*)spread_bulk_kernel<2, 4>,
+        (const void*)spread_bulk_kernel<4, 1>, (const void*)spread_bulk_kernel<4, 2>, (const void*)spread_bulk_kernel<4, 4>,
+        (const void*)spread_bulk_kernel<8, 1>, (const void*)spread_bulk_kernel<8, 2>,
+    };
+    for (const void* f : bulk) {
+        cudaFuncAttributes fa;
+        M2_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem_optin - (int)fa.sharedSizeBytes));
+    }
     return M2_OK;
 }
 

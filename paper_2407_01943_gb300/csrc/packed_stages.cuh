@@ -99,6 +99,13 @@ struct __align__(16) Ctx {
     const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
     float wq;              // sum_k W_k^0(0)^2
     int* status;           // mapped host word [flag, code, where, 0] set by a stage whose bounded wait gave up
+    // bulk-staged spreading: per tile a descriptor (first word of its block, points n, first sample,
+    // samples contiguous) and a 16-byte aligned block [cell | off | taper pairs | src]: n4 = n rounded
+    // up to 4 words per section (n4 <= ncap), each taper pair (2j, 2j + 1) interleaved over two
+    // sections (taper K of an odd K is 0); ncap = 0: not available
+    const int4* tile_desc;
+    const uint32_t* tile_blk;
+    int ncap;
 };
 
 // Drop a dead 128-byte line of an intermediate from L2 without writing it back (its contents
@@ -115,6 +122,80 @@ template <bool kStream>
 __device__ __forceinline__ float2 ld_inter(const float2* p) {
     if (kStream) return __ldcs(p);
     return __ldcg(p);
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies into shared memory (cp.async.bulk, the 1-D form of the tensor memory
+// accelerator's copies), completed on an mbarrier, and the bounded waits on it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes the barrier initialisation visible to the asynchronous proxy that completes it
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier shared-memory accesses (generic proxy) before later bulk copies
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// L2 policy for data read once: evict first
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes a multiple of 16, completed
+// on `bar` (whose transaction count the caller raised for it)
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ long long gtimer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr long long kStageWaitNs = 2000000000LL;  // 2 s: a copy that has not landed by then never will
+// Wait for the phase with this parity to complete; false if it has not within kStageWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = gtimer_ns();
+    while (!mbar_test(bar, parity))
+        if (gtimer_ns() - t0 > kStageWaitNs) return false;
+    return true;
+}
+// Record a stage that gave up waiting (the host reads the word at the plan's next exec).
+__device__ __forceinline__ void stage_timeout(int* status, int where) {
+    if (!status) return;
+    if (atomicExch(status, 1) == 0) {
+        status[1] = (int)M2_ERR_TIMEOUT;
+        status[2] = where;
+        __threadfence_system();
+    }
+}
+
+// Window value of a point at cell ci: off = (first cell of its window) - u_n, dcell = ci - first
+// cell; the exponential of semicircle phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)).  Every rounding
+// is spelled out so that all spreading variants compute the same bits.
+__device__ __forceinline__ float spread_phi(const Ctx& c, float off, int dcell) {
+    const float z = __fadd_rn(off, (float)dcell);
+    const float a = __fmul_rn(z, c.two_over_w);
+    return expf(__fmul_rn(c.beta, __fadd_rn(sqrtf(fmaxf(0.f, __fmaf_rn(-a, a, 1.f))), -1.f)));
+}
+// acc += (taper pair * sample) * phi, the tapered sample rounded first
+__device__ __forceinline__ void spread_mac(float2& acc, float2 tp, float xv, float phi) {
+    acc.x = __fmaf_rn(__fmul_rn(tp.x, xv), phi, acc.x);
+    acc.y = __fmaf_rn(__fmul_rn(tp.y, xv), phi, acc.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -149,8 +230,8 @@ __device__ __forceinline__ void spread_tiles(const Ctx& c, const float* __restri
 #pragma unroll
             for (int j = 0; j < KP; ++j) {
                 float2 v = make_float2(0.f, 0.f);
-                if (2 * j < c.K) v.x = c.taper[(int64_t)(2 * j) * c.P + p] * xv;
-                if (2 * j + 1 < c.K) v.y = c.taper[(int64_t)(2 * j + 1) * c.P + p] * xv;
+                if (2 * j < c.K) v.x = __fmul_rn(c.taper[(int64_t)(2 * j) * c.P + p], xv);
+                if (2 * j + 1 < c.K) v.y = __fmul_rn(c.taper[(int64_t)(2 * j + 1) * c.P + p], xv);
                 s_val[j * kSpreadChunk + t] = v;
             }
         }
@@ -166,14 +247,12 @@ __device__ __forceinline__ void spread_tiles(const Ctx& c, const float* __restri
                     if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
                 }
                 for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
-                    const float z = s_off[t] + (float)(ci - s_cell[t]);
-                    const float a = z * c.two_over_w;
-                    const float phi = expf(c.beta * (sqrtf(fmaxf(0.f, 1.f - a * a)) - 1.f));
+                    const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
 #pragma unroll
                     for (int j = 0; j < KP; ++j) {
-                        const float2 v = s_val[j * kSpreadChunk + t];
-                        acc[u][j].x += v.x * phi;
-                        acc[u][j].y += v.y * phi;
+                        const float2 v = s_val[j * kSpreadChunk + t];  // already the tapered sample
+                        acc[u][j].x = __fmaf_rn(v.x, phi, acc[u][j].x);
+                        acc[u][j].y = __fmaf_rn(v.y, phi, acc[u][j].y);
                     }
                 }
             }
@@ -250,19 +329,12 @@ __device__ __forceinline__ void spread_tile_multi(const Ctx& c, const float* __r
                 if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
             }
             for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
-                const float z = s_off[t] + (float)(ci - s_cell[t]);
-                const float a = z * c.two_over_w;
-                const float phi = expf(c.beta * (sqrtf(fmaxf(0.f, 1.f - a * a)) - 1.f));
+                const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
 #pragma unroll
                 for (int b = 0; b < SB; ++b) {
                     const float xv = s_x[b * kSpreadChunk + t];
 #pragma unroll
-                    for (int j = 0; j < KP; ++j) {
-                        const float2 tp = s_tap[j * kSpreadChunk + t];
-                        const float vx = tp.x * xv, vy = tp.y * xv;  // the tapered sample, rounded as when spread alone
-                        acc[b][j].x += vx * phi;
-                        acc[b][j].y += vy * phi;
-                    }
+                    for (int j = 0; j < KP; ++j) spread_mac(acc[b][j], s_tap[j * kSpreadChunk + t], xv, phi);
                 }
             }
         }
@@ -279,6 +351,151 @@ __device__ __forceinline__ void spread_tile_multi(const Ctx& c, const float* __r
 }
 
 __host__ __device__ constexpr size_t spread_smem_bytes(int KP) { return (size_t)8 * kSpreadChunk + (size_t)KP * kSpreadChunk * 8; }
+
+// ---------------------------------------------------------------------------
+// Bulk-staged spreading of tiles [tile0, tile0 + nt) (nt <= NT) for SB signals (b0 .. b0 + nsb - 1
+// of x, strided by N; grids strided by Kp * Lg), one cell per thread and tile.  Thread 0 reads the
+// tiles' descriptors and copies each tile's point block (cp.async.bulk, one copy per tile) and,
+// where a tile's points come from one contiguous run of samples, that run of each signal (one
+// copy per tile and signal, widened to 16-byte boundaries) into shared memory, all completed on
+// one mbarrier; tiles whose samples are not contiguous gather them after the copies land.  The
+// cells then add their points in ascending point order with the arithmetic of spread_tiles, so
+// the grids are bit-identical to it.  A copy that has not landed within 2 s is recorded in
+// c.status and the CTA writes nothing.
+// smem (16-byte aligned): spread_bulk_smem_bytes(K, ncap, SB, NT).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t spread_bulk_meta_bytes(int SB, int NT) {
+    return 16 + (size_t)16 * NT + ((size_t)4 * SB * NT + 15) / 16 * 16;
+}
+__host__ __device__ inline size_t spread_bulk_smem_bytes(int K, int ncap, int SB, int NT) {
+    return spread_bulk_meta_bytes(SB, NT) +
+           (size_t)4 * NT * ((size_t)(3 + 2 * ((K + 1) / 2)) * ncap + (size_t)SB * (ncap + 8));
+}
+
+template <int KP, int SB, int NT>
+__device__ __forceinline__ void spread_bulk(const Ctx& c, const float* __restrict__ x, int nsb, int tile0, int nt,
+                                            float2* __restrict__ g, unsigned char* smem) {
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int4* s_desc = reinterpret_cast<int4*>(smem + 16);                // [NT]
+    int* s_xoff = reinterpret_cast<int*>(smem + 16 + 16 * NT);       // [NT][SB] first sample's offset in its run
+    const int ncap = c.ncap;
+    const int nsec = 2 + 2 * c.Kp;  // cell, off, taper pairs (the src section follows)
+    const size_t blk_words = (size_t)(nsec + 1) * ncap;
+    uint32_t* s_blk = reinterpret_cast<uint32_t*>(smem + spread_bulk_meta_bytes(SB, NT));  // [NT][blk_words]
+    float* s_x = reinterpret_cast<float*>(s_blk + (size_t)NT * blk_words);                 // [NT][SB][ncap + 8]
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t pol = l2_evict_first_policy();
+        int4 d[NT];
+        unsigned total = 0;
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            d[u] = u < nt ? __ldg(c.tile_desc + tile0 + u) : make_int4(0, 0, 0, 1);
+            s_desc[u] = d[u];
+            const unsigned n4 = (unsigned)((d[u].y + 3) & ~3);
+            total += 4u * n4 * (unsigned)(nsec + (d[u].w ? 0 : 1));
+#pragma unroll
+            for (int b = 0; b < SB; ++b) {
+                s_xoff[u * SB + b] = 0;  // every entry is defined, also for signals b >= nsb
+                if (d[u].w && b < nsb && d[u].y > 0) {
+                    const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + d[u].z);
+                    const uintptr_t lo = a0 & ~(uintptr_t)15, hi = (a0 + 4u * (unsigned)d[u].y + 15) & ~(uintptr_t)15;
+                    s_xoff[u * SB + b] = (int)((a0 - lo) >> 2);
+                    total += (unsigned)(hi - lo);
+                }
+            }
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
+                     : "memory");
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            const unsigned n4 = (unsigned)((d[u].y + 3) & ~3);
+            if (n4 == 0) continue;
+            // the block keeps its layout (sections n4 words apart): one copy, without the src section
+            // when the samples are one run
+            bulk_copy(s_blk + u * blk_words, c.tile_blk + d[u].x, 4u * n4 * (unsigned)(nsec + (d[u].w ? 0 : 1)), bar,
+                      pol);
+#pragma unroll
+            for (int b = 0; b < SB; ++b) {
+                if (d[u].w && b < nsb) {
+                    const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + d[u].z);
+                    const uintptr_t lo = a0 & ~(uintptr_t)15, hi = (a0 + 4u * (unsigned)d[u].y + 15) & ~(uintptr_t)15;
+                    bulk_copy(s_x + ((size_t)u * SB + b) * (ncap + 8), reinterpret_cast<const void*>(lo),
+                              (unsigned)(hi - lo), bar, pol);
+                }
+            }
+        }
+    }
+    const bool late = !mbar_wait(bar, 0);
+    if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) stage_timeout(c.status, tile0);
+        return;
+    }
+    // tiles whose samples are not one run: gather them by the src section
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        const int4 d = s_desc[u];
+        if (d.w || d.y == 0) continue;
+        const int n4 = (d.y + 3) & ~3;
+        const int32_t* s_src = reinterpret_cast<const int32_t*>(s_blk + u * blk_words + (size_t)nsec * n4);
+        for (int t = threadIdx.x; t < d.y; t += blockDim.x) {
+            const int src = s_src[t];
+#pragma unroll
+            for (int b = 0; b < SB; ++b)
+                s_x[((size_t)u * SB + b) * (ncap + 8) + t] = b < nsb ? __ldg(x + (int64_t)b * c.N + src) : 0.f;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NT; ++u) {
+        const int64_t cell = (int64_t)(tile0 + u) * kSpreadTile + threadIdx.x;
+        if (u >= nt || cell >= c.Lg) continue;
+        const int4 d = s_desc[u];
+        const int n = d.y, n4 = (n + 3) & ~3;
+        const int32_t* s_cell = reinterpret_cast<const int32_t*>(s_blk + u * blk_words);
+        const float* s_off = reinterpret_cast<const float*>(s_blk + u * blk_words + n4);
+        const float2* s_tap = reinterpret_cast<const float2*>(s_blk + u * blk_words + 2 * (size_t)n4);  // [Kp][n4]
+        const float* s_xu = s_x + (size_t)u * SB * (ncap + 8);
+        int xo[SB];
+#pragma unroll
+        for (int b = 0; b < SB; ++b) xo[b] = d.w && b < nsb ? s_xoff[u * SB + b] : 0;
+        float2 acc[SB][KP];
+#pragma unroll
+        for (int b = 0; b < SB; ++b)
+#pragma unroll
+            for (int j = 0; j < KP; ++j) acc[b][j] = make_float2(0.f, 0.f);
+        const int ci = (int)cell;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
+        }
+        for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
+            const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
+            float2 tp[KP];
+#pragma unroll
+            for (int j = 0; j < KP; ++j) tp[j] = j < c.Kp ? s_tap[(size_t)j * n4 + t] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < SB; ++b) {
+                if (b >= nsb) break;
+                const float xv = s_xu[(size_t)b * (ncap + 8) + xo[b] + t];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) spread_mac(acc[b][j], tp[j], xv, phi);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < SB; ++b)
+            if (b < nsb) {
+#pragma unroll
+                for (int j = 0; j < KP; ++j)
+                    if (j < c.Kp) g[((int64_t)b * c.Kp + j) * c.Lg + cell] = acc[b][j];
+            }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // column pass for 32 columns starting at colbase, done by a group of gw warps
@@ -367,68 +584,6 @@ __device__ __forceinline__ void rowfft_row(const Ctx& c, const Tw32& tw, float2*
     for (int q = 0; q < 32; ++q) {
         const int k2 = lane + 32 * brev(q, 5);
         if (k2 < nlo || k2 >= kRowLen - nlo) __stcg(Zr + k2, v[q]);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Asynchronous bulk copies into shared memory (cp.async.bulk, the 1-D form of the tensor memory
-// accelerator's copies), completed on an mbarrier, and the bounded waits on it.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-// makes the barrier initialisation visible to the asynchronous proxy that completes it
-__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-// orders this thread's earlier shared-memory accesses (generic proxy) before later bulk copies
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// L2 policy for data read once: evict first
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes a multiple of 16; the
-// transaction count of `bar` is raised by `bytes` first, so one call arms the barrier's phase
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ long long gtimer_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-constexpr long long kStageWaitNs = 2000000000LL;  // 2 s: a copy that has not landed by then never will
-// Wait for the phase with this parity to complete; false if it has not within kStageWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    if (mbar_test(bar, parity)) return true;
-    const long long t0 = gtimer_ns();
-    while (!mbar_test(bar, parity))
-        if (gtimer_ns() - t0 > kStageWaitNs) return false;
-    return true;
-}
-// Record a stage that gave up waiting (the host reads the word at the plan's next exec).
-__device__ __forceinline__ void stage_timeout(int* status, int where) {
-    if (!status) return;
-    if (atomicExch(status, 1) == 0) {
-        status[1] = (int)M2_ERR_TIMEOUT;
-        status[2] = where;
-        __threadfence_system();
     }
 }
 

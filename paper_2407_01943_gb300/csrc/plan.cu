@@ -1090,6 +1090,46 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         }
         M2_TRY_OR(pb.upload(&p->d_tile_pb, tpb));
         M2_TRY_OR(pb.upload(&p->d_tile_pe, tpe));
+
+        if (g.path >= 2) {
+            // tile blocks for bulk-staged spreading: each tile's point records, tapers and sample
+            // indices as one 16-byte aligned block (sections of n4 = n rounded up to 4 words), and
+            // whether its samples are one contiguous run of x (then the kernel copies that run)
+            std::vector<int4> desc((size_t)g.ntiles);
+            std::vector<uint32_t> blk;
+            int ncap = 0;
+            for (int64_t j = 0; j < g.ntiles; ++j) {
+                const int b0 = tpb[j], n = tpe[j] - tpb[j], n4 = (n + 3) & ~3;
+                bool contig = true;
+                for (int q = 1; q < n && contig; ++q) contig = src[b0 + q] == src[b0] + q;
+                desc[(size_t)j] = make_int4((int)blk.size(), n, n > 0 ? src[b0] : 0, contig ? 1 : 0);
+                const size_t base = blk.size();
+                const int kp = (K + 1) / 2;
+                blk.resize(base + (size_t)(3 + 2 * kp) * n4, 0u);
+                for (int q = 0; q < n; ++q) {
+                    const int64_t pp = b0 + q;
+                    const float fo = (float)off[pp];
+                    std::memcpy(&blk[base + q], &cell[pp], 4);
+                    std::memcpy(&blk[base + n4 + q], &fo, 4);
+                    for (int k = 0; k < K; ++k) {  // taper pairs (2j, 2j + 1) interleaved, taper K = 0
+                        const float ft = (float)tap[(size_t)k * g.P + pp];
+                        std::memcpy(&blk[base + (size_t)(2 + 2 * (k / 2)) * n4 + 2 * q + (k & 1)], &ft, 4);
+                    }
+                    std::memcpy(&blk[base + (size_t)(2 + 2 * kp) * n4 + q], &src[pp], 4);
+                }
+                ncap = std::max(ncap, n4);
+            }
+            // staged in shared memory only while a CTA's share stays modest (about 64 KB)
+            if (ncap > 0 && (size_t)4 * ((size_t)(3 + 2 * ((K + 1) / 2)) * ncap + (size_t)4 * (ncap + 8)) <=
+                                (size_t(64) << 10)) {
+                if (blk.size() > (size_t)INT32_MAX) blk.clear();
+                if (!blk.empty()) {
+                    M2_TRY_OR(pb.upload(&p->d_tile_desc, desc));
+                    M2_TRY_OR(pb.upload(&p->d_tile_blk, blk));
+                    p->spread_ncap = ncap;
+                }
+            }
+        }
     }
 
     // ---- twiddles ----
