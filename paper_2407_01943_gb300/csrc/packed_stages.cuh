@@ -502,57 +502,72 @@ __device__ __forceinline__ void spread_bulk(const Ctx& c, const float* __restric
 // (gwarp = this warp's index in the group); every warp of the CTA calls this
 // once per pass, so the CTA-wide barriers line up:
 //   Z[k1][l2] = W_nf^{l2 k1} sum_{l1 < rows} g[l1][l2] W_n1^{l1 k1}
-// The group's warps share the C = n1 / F cosets.  s_tw: [n1] twiddles W_n1^q,
-// filled by the caller before the call (the first barrier inside publishes
-// them).  smem: this group's [rows][32] + [F][32].
+// The group's warps share the C = n1 / F cosets k1 = r + C q.  s_fw: the fold
+// twiddles [C][rows], s_fw[r][l1] = W_n1^{(l1 r) mod n1}, filled by all threads
+// of the CTA with fill_fold_twiddles before the call (the first barrier inside
+// publishes them).  smem: this group's [rows][32] inputs, [F][32] output
+// twiddles W_nf^{l2 C q} and [C][32] coset factors W_nf^{l2 r}, all staged
+// before the barrier, so the coset loop reads only shared memory.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int cols_cosets(int n1, int F) { return n1 / F; }
+// fold-twiddle table, float2 units
+__host__ __device__ inline size_t cols_fold_f2(int n1, int rows, int F) { return (size_t)cols_cosets(n1, F) * rows; }
+__device__ __forceinline__ void fill_fold_twiddles(const Ctx& c, int F, float2* s_fw) {
+    const int C = cols_cosets(c.n1, F), rows = c.rows;
+    for (int e = threadIdx.x; e < C * rows; e += blockDim.x) {
+        const int r = e / rows, l1 = e - r * rows;
+        s_fw[e] = __ldg(c.tw_n1 + (int)(((int64_t)l1 * r) % c.n1));
+    }
+}
+
 template <int F>
 __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const float2* __restrict__ gj,
                                            float2* __restrict__ Zj, int colbase, int gwarp, int gw,
-                                           const float2* s_tw, float2* smem) {
-    float2* s_in = smem;                // [rows][32]
-    float2* s_T = s_in + c.rows * 32;   // [F][32]
+                                           const float2* s_fw, float2* smem) {
     const int lane = threadIdx.x & 31;
     const int l2 = colbase + lane;
     const int n1 = c.n1, rows = c.rows;
     const int C = n1 / F;
+    float2* s_in = smem;                // [rows][32]
+    float2* s_T = s_in + rows * 32;     // [F][32]
+    float2* s_B = s_T + F * 32;         // [C][32]
     for (int l1 = gwarp; l1 < rows; l1 += gw) s_in[l1 * 32 + lane] = __ldcg(gj + (int64_t)l1 * kRowLen + l2);
     for (int q = gwarp; q < F; q += gw) s_T[q * 32 + lane] = __ldg(c.colT + q * kRowLen + l2);
+    for (int r = gwarp; r < C; r += gw) s_B[r * 32 + lane] = __ldg(c.colB + (int64_t)r * kRowLen + l2);
     __syncthreads();
     const int nfold = (rows + F - 1) / F;
     for (int r = gwarp; r < C; r += gw) {
-        const float2 base = __ldg(c.colB + (int64_t)r * kRowLen + l2);
+        const float2 base = s_B[r * 32 + lane];
+        const float2* fw = s_fw + r * rows;
         float2 v[F];
 #pragma unroll
         for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
-        int tix = 0;  // (l1 * r) mod n1, advanced incrementally
         for (int f = 0; f < nfold; ++f) {
 #pragma unroll
             for (int q = 0; q < F; ++q) {
                 const int l1 = f * F + q;
                 if (l1 < rows) {
-                    const float2 a = s_in[l1 * 32 + lane];
-                    const float2 t = s_tw[tix];
-                    v[q].x += a.x * t.x - a.y * t.y;
-                    v[q].y += a.x * t.y + a.y * t.x;
+                    const float2 p = cmulf(s_in[l1 * 32 + lane], fw[l1]);
+                    v[q].x += p.x;
+                    v[q].y += p.y;
                 }
-                tix += r;
-                if (tix >= n1) tix -= n1;
             }
         }
         fft_reg<F>(v, tw);
+        float2* Zr = Zj + (int64_t)r * kRowLen + l2;
 #pragma unroll
         for (int q = 0; q < F; ++q) {
-            const int k1 = r + C * q;
             const float2 t = cmulf(base, s_T[q * 32 + lane]);
-            Zj[(int64_t)k1 * kRowLen + l2] = cmulf(v[brev(q, ilog2c(F))], t);
+            Zr[(int64_t)(C * q) * kRowLen] = cmulf(v[brev(q, ilog2c(F))], t);
         }
     }
     __syncthreads();  // smem reuse
 }
 
-// shared memory of one column group (float2 units, excluding the [n1] twiddles)
-__host__ __device__ inline size_t cols_group_f2(int rows, int F) { return (size_t)rows * 32 + (size_t)F * 32; }
+// shared memory of one column group (float2 units, excluding the fold twiddles)
+__host__ __device__ inline size_t cols_group_f2(int rows, int F, int n1) {
+    return (size_t)rows * 32 + (size_t)F * 32 + (size_t)cols_cosets(n1, F) * 32;
+}
 
 // One 1024-point row FFT by one warp, in place: the in-band transforms
 //   Y[k2] = sum_{l2} Zr[l2] W_1024^{l2 k2},   k2 <= k2max or k2 >= 1023 - k2max,
