@@ -154,9 +154,11 @@ __global__ void __launch_bounds__(32 * kColWarps) cols_fast_kernel(Ctx c, Tw32 t
                           threadIdx.x >> 5, kColWarps, s_fw, s_fw + packed::cols_fold_f2(c.n1, c.rows, F));
 }
 
-// grid (n1 / R, Kp, nb): R consecutive rows of one taper pair per CTA, one warp per row, in place
+// grid (n1 / R, Kp, nb): R consecutive rows of one taper pair per CTA, one warp per row, in place;
+// R = 4 at five CTAs per SM (at most 102 registers: 20 warps per SM) measured faster than R = 8 at
+// two (128 registers, 16 warps)
 template <int R>
-__global__ void __launch_bounds__(32 * R, (R <= 8 ? 2 : 1)) rowfft_kernel(Ctx c, Tw32 tw, float2* __restrict__ Z) {
+__global__ void __launch_bounds__(32 * R, (R <= 4 ? 5 : 2)) rowfft_kernel(Ctx c, Tw32 tw, float2* __restrict__ Z) {
     extern __shared__ float2 smem_f2[];
     const int64_t base = ((int64_t)blockIdx.z * c.Kp + blockIdx.y) * (int64_t)c.n1 * kRowLen;
     packed::rowfft_rows<R, true>(c, tw, Z + base, blockIdx.x * R, R, smem_f2);
@@ -205,7 +207,7 @@ m2_status init_fast_kernels(int smem_optin) {
     const void* funcs[] = {
         (const void*)cols_fast_kernel<2>,  (const void*)cols_fast_kernel<4>, (const void*)cols_fast_kernel<8>,
         (const void*)cols_fast_kernel<16>, (const void*)cols_fast_kernel<32>, (const void*)rowfft_kernel<2>,
-        (const void*)rowfft_kernel<4>,     (const void*)rowfft_kernel<8>,
+        (const void*)rowfft_kernel<4>,
     };
     for (const void* f : funcs)
         M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
@@ -266,10 +268,9 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
 
     mark(p, 2, 0, st);
     {
-        int R = 1;  // rows per CTA: largest power of two <= 8 dividing n1
-        while (R < 8 && g.n1 % (R * 2) == 0) R *= 2;
-        if (R == 8) M2_TRY(launch_rowfft<8>(c, tw, dZ, nb, st));
-        else if (R == 4) M2_TRY(launch_rowfft<4>(c, tw, dZ, nb, st));
+        int R = 1;  // rows per CTA: largest power of two <= 4 dividing n1
+        while (R < 4 && g.n1 % (R * 2) == 0) R *= 2;
+        if (R == 4) M2_TRY(launch_rowfft<4>(c, tw, dZ, nb, st));
         else M2_TRY(launch_rowfft<2>(c, tw, dZ, nb, st));
     }
     mark(p, 2, 1, st);
