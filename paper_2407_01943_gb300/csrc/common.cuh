@@ -189,6 +189,7 @@ struct m2nufft_plan_s {
     void* d_tw1024 = nullptr;      // packed path: [32][32] C, [cc][l] = exp(-i 2 pi cc l / 1024)
     void* d_colT = nullptr;        // packed path: [F][1024] C, exp(-i 2 pi l2 C q / nf) (column-FFT output twiddle)
     void* d_colB = nullptr;        // packed path: [C][1024] C, exp(-i 2 pi l2 r / nf) (per-coset factor)
+    void* d_colFw = nullptr;       // packed path: [C][rows] C, exp(-i 2 pi ((l1 r) mod n1) / n1) (fold twiddles)
     void* d_wsum = nullptr;        // [K] R: W_k^0(0) = sum_n w_k(t_n) (F-statistic)
     double wq = 0.0;               // sum_k W_k^0(0)^2
     void* d_Jscratch = nullptr;    // generic path: J of one chunk when F is wanted without J

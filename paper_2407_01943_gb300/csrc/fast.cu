@@ -64,8 +64,8 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
         const size_t budget = packed::rowfft_smem_bytes(8);
         int gw = 4;
         for (int cand : {1, 2}) {
-            const size_t sm = sizeof(float2) * (packed::cols_fold_f2((int)g.n1, (int)g.rows, g.colF) + (size_t)(8 / cand) *
-                                                packed::cols_group_f2((int)g.rows, g.colF, (int)g.n1));
+            const size_t sm = sizeof(float2) * (packed::cols_tw_f2(false, (int)g.n1, (int)g.rows, g.colF) +
+                                                (size_t)(8 / cand) * packed::cols_group_f2(false, (int)g.rows, g.colF, (int)g.n1));
             if ((C + cand - 1) / cand <= 3 && sm <= budget) {
                 gw = cand;
                 break;
@@ -78,6 +78,7 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     c.tw_n1 = reinterpret_cast<const float2*>(p->d_twn1);
     c.colT = reinterpret_cast<const float2*>(p->d_colT);
     c.colB = reinterpret_cast<const float2*>(p->d_colB);
+    c.colFw = reinterpret_cast<const float2*>(p->d_colFw);
     c.tw1024 = reinterpret_cast<const float2*>(p->d_tw1024);
     c.deconv = reinterpret_cast<const float2*>(p->d_deconv);
     c.wsum = reinterpret_cast<const float*>(p->d_wsum);
@@ -150,8 +151,8 @@ __global__ void __launch_bounds__(32 * kColWarps) cols_fast_kernel(Ctx c, Tw32 t
     const int j = blockIdx.y, b = blockIdx.z;
     packed::fill_fold_twiddles(c, F, s_fw);
     const int64_t pair = (int64_t)b * c.Kp + j;
-    packed::cols_group<F>(c, tw, g + pair * c.Lg, Z + pair * (int64_t)c.n1 * kRowLen, blockIdx.x * 32,
-                          threadIdx.x >> 5, kColWarps, s_fw, s_fw + packed::cols_fold_f2(c.n1, c.rows, F));
+    packed::cols_group<F, true>(c, tw, g + pair * c.Lg, Z + pair * (int64_t)c.n1 * kRowLen, blockIdx.x * 32,
+                                threadIdx.x >> 5, kColWarps, s_fw, s_fw + packed::cols_tw_f2(true, c.n1, c.rows, F));
 }
 
 // grid (n1 / R, Kp, nb): R consecutive rows of one taper pair per CTA, one warp per row, in place;
@@ -186,7 +187,8 @@ __global__ void __launch_bounds__(epi_threads(kF), kF ? 4 : kEpiMinBlocks) epi_k
 
 template <int F>
 m2_status launch_cols_fast(const Ctx& c, const Tw32& tw, const float2* g, float2* Z, int nb, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (packed::cols_fold_f2(c.n1, c.rows, F) + packed::cols_group_f2(c.rows, F, c.n1));
+    const size_t smem = sizeof(float2) * (packed::cols_tw_f2(true, c.n1, c.rows, F) +
+                                          packed::cols_group_f2(true, c.rows, F, c.n1));
     dim3 grid((unsigned)(kRowLen / 32), (unsigned)c.Kp, (unsigned)nb);
     cols_fast_kernel<F><<<grid, 32 * kColWarps, smem, st>>>(c, tw, g, Z);
     M2_CUDA_TRY(cudaGetLastError());

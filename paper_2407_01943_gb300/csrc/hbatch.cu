@@ -94,12 +94,12 @@ __global__ void __launch_bounds__(kColThreads) hb_cols_kernel(const int4* __rest
     const int gw = m.w;
     const int warp = threadIdx.x >> 5;
     const int grp = warp / gw, gwarp = warp - grp * gw;
-    float2* s_fw = smem_f2;  // [C][rows] fold twiddles
-    packed::fill_fold_twiddles(c, F, s_fw);
+    float2* s_tw = smem_f2;  // [n1]
+    packed::fill_n1_twiddles(c, s_tw);
     float2* ws_g = ws + s_task.g_off + (int64_t)m.y * c.Lg;
     float2* ws_z = ws + s_task.z_off + (int64_t)m.y * c.n1 * kRowLen;
-    packed::cols_group<F>(c, tw, ws_g, ws_z, m.z + grp * 32, gwarp, gw, s_fw,
-                          s_fw + packed::cols_fold_f2(c.n1, c.rows, F) + (size_t)grp * packed::cols_group_f2(c.rows, F, c.n1));
+    packed::cols_group<F, false>(c, tw, ws_g, ws_z, m.z + grp * 32, gwarp, gw, s_tw,
+                                 s_tw + c.n1 + (size_t)grp * packed::cols_group_f2(false, c.rows, F, c.n1));
 }
 
 // map entry: (task, pair, first row, rows); one warp per row, R rows per CTA
@@ -243,8 +243,8 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const H
     const int lf = packed::ilog2c(c.F);
     for (int j = 0; j < c.Kp; ++j)
         for (int col = 0; col < kRowLen; col += 32 * (4 / gw)) m.co[lf].push_back(make_int4(task, j, col, gw));
-    m.smem_cols[lf] = std::max(m.smem_cols[lf], sizeof(float2) * (packed::cols_fold_f2(c.n1, c.rows, c.F) + (size_t)(4 / gw) *
-                                                                   packed::cols_group_f2(c.rows, c.F, c.n1)));
+    m.smem_cols[lf] = std::max(m.smem_cols[lf], sizeof(float2) * (packed::cols_tw_f2(false, c.n1, c.rows, c.F) +
+                                                                   (size_t)(4 / gw) * packed::cols_group_f2(false, c.rows, c.F, c.n1)));
     // row FFTs: up to cfg.row_warps rows per CTA
     const int rw = cfg.row_warps;
     for (int j = 0; j < c.Kp; ++j)

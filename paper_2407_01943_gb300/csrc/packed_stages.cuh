@@ -94,6 +94,7 @@ struct __align__(16) Ctx {
     const float2* tw_n1;   // [n1]
     const float2* colT;    // [F][1024]
     const float2* colB;    // [C][1024]
+    const float2* colFw;   // [C][rows] fold twiddles W_n1^{(l1 r) mod n1}
     const float2* tw1024;  // [32][32]: [cc][l] = W_1024^{cc l}
     const float2* deconv;  // [I]
     const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
@@ -502,54 +503,69 @@ __device__ __forceinline__ void spread_bulk(const Ctx& c, const float* __restric
 // (gwarp = this warp's index in the group); every warp of the CTA calls this
 // once per pass, so the CTA-wide barriers line up:
 //   Z[k1][l2] = W_nf^{l2 k1} sum_{l1 < rows} g[l1][l2] W_n1^{l1 k1}
-// The group's warps share the C = n1 / F cosets k1 = r + C q.  s_fw: the fold
-// twiddles [C][rows], s_fw[r][l1] = W_n1^{(l1 r) mod n1}, filled by all threads
-// of the CTA with fill_fold_twiddles before the call (the first barrier inside
-// publishes them).  smem: this group's [rows][32] inputs, [F][32] output
-// twiddles W_nf^{l2 C q} and [C][32] coset factors W_nf^{l2 r}, all staged
-// before the barrier, so the coset loop reads only shared memory.
+// The group's warps share the C = n1 / F cosets k1 = r + C q.  Two forms with the
+// same arithmetic (every product rounded as cmulf does, the fold adds in row
+// order), so they write the same bits:
+//   kStaged: s_tw is the fold-twiddle table [C][rows], s_tw[r][l1] =
+//     W_n1^{(l1 r) mod n1} (fill_fold_twiddles), and the group's [C][32] coset
+//     factors W_nf^{l2 r} are staged with its inputs, so the coset loop reads only
+//     shared memory -- for CTAs with several cosets per warp;
+//   otherwise: s_tw is the [n1] table W_n1^q (fill_n1_twiddles), the twiddle
+//     index (l1 r) mod n1 advances by r per row and the coset factor is read in
+//     the loop -- a shorter prologue, for CTAs with one coset per warp.
+// The tables are filled by all threads of the CTA before the call (the first
+// barrier inside publishes them).  smem: this group's [rows][32] inputs, [F][32]
+// output twiddles W_nf^{l2 C q} (and with kStaged the [C][32] coset factors).
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int cols_cosets(int n1, int F) { return n1 / F; }
-// fold-twiddle table, float2 units
-__host__ __device__ inline size_t cols_fold_f2(int n1, int rows, int F) { return (size_t)cols_cosets(n1, F) * rows; }
-__device__ __forceinline__ void fill_fold_twiddles(const Ctx& c, int F, float2* s_fw) {
-    const int C = cols_cosets(c.n1, F), rows = c.rows;
-    for (int e = threadIdx.x; e < C * rows; e += blockDim.x) {
-        const int r = e / rows, l1 = e - r * rows;
-        s_fw[e] = __ldg(c.tw_n1 + (int)(((int64_t)l1 * r) % c.n1));
-    }
+// twiddle table of the CTA, float2 units
+__host__ __device__ inline size_t cols_tw_f2(bool staged, int n1, int rows, int F) {
+    return staged ? (size_t)cols_cosets(n1, F) * rows : (size_t)n1;
+}
+__device__ __forceinline__ void fill_fold_twiddles(const Ctx& c, int F, float2* s_tw) {
+    const int n = cols_cosets(c.n1, F) * c.rows;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) s_tw[e] = __ldg(c.colFw + e);
+}
+__device__ __forceinline__ void fill_n1_twiddles(const Ctx& c, float2* s_tw) {
+    for (int q = threadIdx.x; q < c.n1; q += blockDim.x) s_tw[q] = __ldg(c.tw_n1 + q);
 }
 
-template <int F>
+template <int F, bool kStaged>
 __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const float2* __restrict__ gj,
                                            float2* __restrict__ Zj, int colbase, int gwarp, int gw,
-                                           const float2* s_fw, float2* smem) {
+                                           const float2* s_tw, float2* smem) {
     const int lane = threadIdx.x & 31;
     const int l2 = colbase + lane;
     const int n1 = c.n1, rows = c.rows;
     const int C = n1 / F;
     float2* s_in = smem;                // [rows][32]
     float2* s_T = s_in + rows * 32;     // [F][32]
-    float2* s_B = s_T + F * 32;         // [C][32]
+    float2* s_B = s_T + F * 32;         // kStaged: [C][32]
     for (int l1 = gwarp; l1 < rows; l1 += gw) s_in[l1 * 32 + lane] = __ldcg(gj + (int64_t)l1 * kRowLen + l2);
     for (int q = gwarp; q < F; q += gw) s_T[q * 32 + lane] = __ldg(c.colT + q * kRowLen + l2);
-    for (int r = gwarp; r < C; r += gw) s_B[r * 32 + lane] = __ldg(c.colB + (int64_t)r * kRowLen + l2);
+    if (kStaged)
+        for (int r = gwarp; r < C; r += gw) s_B[r * 32 + lane] = __ldg(c.colB + (int64_t)r * kRowLen + l2);
     __syncthreads();
     const int nfold = (rows + F - 1) / F;
     for (int r = gwarp; r < C; r += gw) {
-        const float2 base = s_B[r * 32 + lane];
-        const float2* fw = s_fw + r * rows;
+        const float2 base = kStaged ? s_B[r * 32 + lane] : __ldg(c.colB + (int64_t)r * kRowLen + l2);
         float2 v[F];
 #pragma unroll
         for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
+        int tix = 0;  // (l1 * r) mod n1, advanced incrementally (the [n1]-table form)
         for (int f = 0; f < nfold; ++f) {
 #pragma unroll
             for (int q = 0; q < F; ++q) {
                 const int l1 = f * F + q;
                 if (l1 < rows) {
-                    const float2 p = cmulf(s_in[l1 * 32 + lane], fw[l1]);
+                    const float2 t = kStaged ? s_tw[r * rows + l1] : s_tw[tix];
+                    const float2 p = cmulf(s_in[l1 * 32 + lane], t);
                     v[q].x += p.x;
                     v[q].y += p.y;
+                }
+                if (!kStaged) {
+                    tix += r;
+                    if (tix >= n1) tix -= n1;
                 }
             }
         }
@@ -564,9 +580,9 @@ __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const f
     __syncthreads();  // smem reuse
 }
 
-// shared memory of one column group (float2 units, excluding the fold twiddles)
-__host__ __device__ inline size_t cols_group_f2(int rows, int F, int n1) {
-    return (size_t)rows * 32 + (size_t)F * 32 + (size_t)cols_cosets(n1, F) * 32;
+// shared memory of one column group (float2 units, excluding the CTA's twiddle table)
+__host__ __device__ inline size_t cols_group_f2(bool staged, int rows, int F, int n1) {
+    return (size_t)rows * 32 + (size_t)F * 32 + (staged ? (size_t)cols_cosets(n1, F) * 32 : 0);
 }
 
 // One 1024-point row FFT by one warp, in place: the in-band transforms

@@ -141,16 +141,16 @@ __device__ __forceinline__ void run_cols(const Ctx& c, const Tw32& tw, const flo
     const int gw = c.cgw, ngroups = 8 / gw;
     const int per_pair = 4 * gw / c.cm;
     const int j = idx / per_pair, cb = idx - j * per_pair;
-    float2* s_fw = smem;  // [C][rows] fold twiddles
+    float2* s_tw = smem;  // [n1]
     const int warp = threadIdx.x >> 5;
     const int grp = warp / gw, gwarp = warp - grp * gw;
-    float2* s_grp = smem + packed::cols_fold_f2(c.n1, c.rows, F) + (size_t)grp * packed::cols_group_f2(c.rows, F, c.n1);
-    packed::fill_fold_twiddles(c, F, s_fw);
+    float2* s_grp = smem + c.n1 + (size_t)grp * packed::cols_group_f2(false, c.rows, F, c.n1);
+    packed::fill_n1_twiddles(c, s_tw);
     const float2* gj = gb + (int64_t)j * c.Lg;
     float2* Zj = Zb + (int64_t)j * c.n1 * kRowLen;
     for (int m = 0; m < c.cm; ++m) {
         const int colbase = ((cb * c.cm + m) * ngroups + grp) * 32;
-        packed::cols_group<F>(c, tw, gj, Zj, colbase, gwarp, gw, s_fw, s_grp);
+        packed::cols_group<F, false>(c, tw, gj, Zj, colbase, gwarp, gw, s_tw, s_grp);
     }
 }
 
@@ -294,8 +294,8 @@ StageCounts stage_counts(const Ctx& c, int ntiles) {
 
 size_t pipe_smem_bytes(const Ctx& c) {
     const size_t spread = packed::spread_smem_bytes(8);
-    const size_t cols = sizeof(float2) * (packed::cols_fold_f2(c.n1, c.rows, c.F) +
-                                          (size_t)(8 / c.cgw) * packed::cols_group_f2(c.rows, c.F, c.n1));
+    const size_t cols = sizeof(float2) * (packed::cols_tw_f2(false, c.n1, c.rows, c.F) +
+                                          (size_t)(8 / c.cgw) * packed::cols_group_f2(false, c.rows, c.F, c.n1));
     const size_t rows = packed::rowfft_smem_bytes(kRowsPerItem);
     return std::max(spread, std::max(cols, rows));
 }

@@ -1175,6 +1175,17 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
             }
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_colT, tT));
         M2_TRY_OR(upload_complex(pb, p->precision, &p->d_colB, tB));
+        // fold twiddles of the column pass: colFw[r][l1] = W_n1^{(l1 r) mod n1}, the entries of the
+        // [n1] table that coset r reads for input row l1
+        const std::vector<double> tn1 = unit_roots(g.n1, g.n1, 1);
+        std::vector<double> tF(2 * C * g.rows);
+        for (int64_t r = 0; r < C; ++r)
+            for (int64_t l1 = 0; l1 < g.rows; ++l1) {
+                const int64_t e = (l1 * r) % g.n1;
+                tF[2 * (r * g.rows + l1)] = tn1[2 * e];
+                tF[2 * (r * g.rows + l1) + 1] = tn1[2 * e + 1];
+            }
+        M2_TRY_OR(upload_complex(pb, p->precision, &p->d_colFw, tF));
     }
 
     // ---- deconvolution / re-phasing factors ----
