@@ -237,6 +237,12 @@ def hbm_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: str = "JE
     out = I * rsz + (K * I * csz if "J" in outputs else 0) + (K * I * rsz if "E" in outputs else 0) + \
         (I * rsz if "F" in outputs else 0)
     if kernel == "spread":
+        if info.get("spread_entries", 0) > 0:
+            # packed paths: x, the cell-major spreading matrix (per entry a sample index and
+            # ceil(K/2) complex weights; read once per launch), slice and tile descriptors
+            ents = info["spread_entries"]
+            return nb * N * rsz + ents * (4 + (K + 1) // 2 * csz) + (info["rows"] * info["n2"] // 32) * 8 + \
+                (info["rows"] * info["n2"] // 256 + 1) * 16
         return nb * N * rsz + N * (8 + rsz) + K * N * taper
     if kernel == "cols":
         return 0.0
@@ -426,8 +432,10 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
     pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)  # first call: build + capture + instantiate
     torch.cuda.synchronize()
     t_capture = time.perf_counter() - t0
-    ms_batch = timed_ms(torch, stream, dev, lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream),
-                        steps, warmup)
+    # the argument arrays (5 x nsig pointers) are marshalled once, so the timed region holds the
+    # library call (cached-graph lookup and launch), not the Python list building
+    call = pkg.BatchCall(plans, xs, Js, Es, Ps)
+    ms_batch = timed_ms(torch, stream, dev, lambda: call(stream), steps, warmup)
     def coset_len(n1):
         f = 1
         while f < 32 and n1 % (2 * f) == 0:
@@ -443,8 +451,7 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
         pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream)
         torch.cuda.synchronize()
         pkg.binding.batch_pipe_profile()  # reset the stage accounting
-        ms_pipe = timed_ms(torch, stream, dev, lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream),
-                           steps, warmup)
+        ms_pipe = timed_ms(torch, stream, dev, lambda: call(stream), steps, warmup)
         pkg.binding.set_batch_mode(prev)
         busy, waitms, nitems = pkg.binding.batch_pipe_profile()
         tot = max(float(busy.sum()), 1e-12)
@@ -460,8 +467,7 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t0
     table = pkg.binding.batch_tuning()
-    ms_tuned = timed_ms(torch, stream, dev, lambda: pkg.exec_batch(plans, xs, Js, Es, Ps, stream=stream),
-                        steps, warmup)
+    ms_tuned = timed_ms(torch, stream, dev, lambda: call(stream), steps, warmup)
     pkg.binding.set_batch_mode(prev)
     best = min(table, key=lambda r: r[1]) if table else None
 
@@ -472,6 +478,25 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
     wall0 = time.perf_counter()
     ms_plain = timed_ms(torch, stream, dev, plain, steps, warmup)
     wall_plain = time.perf_counter() - wall0
+    # the same per-signal execs captured once in a CUDA graph: the plain path's device time
+    # without the per-call host overhead
+    ms_plain_graph, plain_graph_note = None, None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            for p, x, J, E, P in zip(plans, xs, Js, Es, Ps):
+                p.exec(x[None, :], J[None], E[None], P[None])
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=cap):
+            for p, x, J, E, P in zip(plans, xs, Js, Es, Ps):
+                p.exec(x[None, :], J[None], E[None], P[None])
+        torch.cuda.synchronize()
+        ms_plain_graph = timed_ms(torch, stream, dev, graph.replay, steps, warmup)
+        del graph
+    except Exception as e:  # reported, not hidden: the line says why there is no number
+        plain_graph_note = f"capture failed: {type(e).__name__}: {e}"[:200]
     out = {
         "workload": f"uneven batch: {nsig} signals, grid length log-uniform in [1024, 16384], Markov gaps 15%, "
                     f"K in {{4,6,8}}, I = 4G; outputs J, |J|^2, P-hat",
@@ -482,7 +507,12 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
         "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain, "host_wall_s": wall_plain,
                              "gpu_launches": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
                                                  for p in plans)},
+        "plain_per_signal_graph": None if ms_plain_graph is None else {
+            "value": units / (ms_plain_graph * 1e-3), "ms_per_step": ms_plain_graph,
+            "form": "the per-signal m2nufft_exec calls captured once in one CUDA graph and replayed"},
+        "plain_per_signal_graph_note": plain_graph_note,
         "batched_over_plain": ms_plain / ms_batch,
+        "batched_over_plain_graph": None if ms_plain_graph is None else ms_plain_graph / ms_batch,
         "tuned": {"value": units / (ms_tuned * 1e-3), "ms_per_step": ms_tuned, "tune_seconds": t_tune,
                   "choice": None if best is None else {
                       "batch_mode": best[0][0], "spread_tiles_per_cta": best[0][1], "rows_per_cta": best[0][2],

@@ -138,6 +138,9 @@ typedef struct {
                             3 = packed FP32 (persistent pipelined kernel) */
     size_t device_bytes; /* device memory held by the plan */
     double gep_seconds;  /* wall time of the GEP during planning (0 if tapers were given) */
+    int64_t spread_entries; /* packed paths: entries of the cell-major spreading matrix (each a
+                               sample index and ceil(K/2) complex FP32 weights), padding
+                               included; 0 on the generic path */
 } m2_info;
 
 /*

@@ -11,7 +11,7 @@ The compute lives in libm2nufft.so (csrc/, C ABI in include/m2nufft.h);
 `binding` marshals arguments to it.
 """
 from ._build_lib import build as build_library  # noqa: F401
-from .binding import M2Error, Plan, exec_batch, load, lib_path, version  # noqa: F401
+from .binding import BatchCall, M2Error, Plan, exec_batch, load, lib_path, version  # noqa: F401
 
 
 def build(force: bool = False) -> str:

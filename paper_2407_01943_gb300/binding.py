@@ -48,7 +48,8 @@ class m2_info(ctypes.Structure):
                 ("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("rows", ctypes.c_int64), ("wrap", ctypes.c_int),
                 ("real_taper", ctypes.c_int), ("integer_grid", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("path", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("gep_seconds", ctypes.c_double)]
+                ("device_bytes", ctypes.c_size_t), ("gep_seconds", ctypes.c_double),
+                ("spread_entries", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) of every exported entry point of include/m2nufft.h
@@ -354,17 +355,31 @@ class Plan:
         self.close()
 
 
+class BatchCall:
+    """m2nufft_exec_batch with its argument arrays marshalled once: for a batch that is run
+    repeatedly on the same plans and buffers, each call then only launches (the library replays
+    its cached graph for the same plans and pointers).  The tensors must stay alive and in place
+    while the object is used."""
+
+    def __init__(self, plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None):
+        n = len(plans)
+        arr = lambda vals: (_VP * n)(*vals)
+        self._keep = (list(plans), xs, Js, Es, Ps)
+        self.n = n
+        self.hp = arr([p.handle.value for p in plans])
+        self.hx = arr([_tptr(x) for x in xs])
+        self.hJ = arr([_tptr(j) for j in Js]) if Js is not None else None
+        self.hE = arr([_tptr(e) for e in Es]) if Es is not None else None
+        self.hP = arr([_tptr(q) for q in Ps]) if Ps is not None else None
+
+    def __call__(self, stream=None):
+        st = load().m2nufft_exec_batch(self.hp, self.hx, self.n, self.hJ, self.hE, self.hP, _stream_handle(stream))
+        _check(st, "m2nufft_exec_batch")
+
+
 def exec_batch(plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, stream=None):
     """Uneven batch: one signal per entry, each with its own plan."""
-    n = len(plans)
-    arr = lambda vals: (_VP * n)(*vals)
-    hp = arr([p.handle.value for p in plans])
-    hx = arr([_tptr(x) for x in xs])
-    hJ = arr([_tptr(j) for j in Js]) if Js is not None else None
-    hE = arr([_tptr(e) for e in Es]) if Es is not None else None
-    hP = arr([_tptr(q) for q in Ps]) if Ps is not None else None
-    st = load().m2nufft_exec_batch(hp, hx, n, hJ, hE, hP, _stream_handle(stream))
-    _check(st, "m2nufft_exec_batch")
+    BatchCall(plans, xs, Js, Es, Ps)(stream)
 
 
 def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: int, Lhat, Ehat, stream=None):

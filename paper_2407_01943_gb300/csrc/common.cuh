@@ -174,12 +174,15 @@ struct m2nufft_plan_s {
     void* d_taper = nullptr;       // [K][P] R (real taper) or C (modulated taper)
     int32_t* d_tile_pb = nullptr;  // [ntiles] first point of each spread tile
     int32_t* d_tile_pe = nullptr;  // [ntiles] one past the last point
-    // packed path, bulk-staged spreading: per tile {first word of its block, points, first sample,
-    // samples contiguous} and the blocks [cell | off | taper pairs | src] (n4 words per section, two
-    // sections per interleaved taper pair)
-    int4* d_tile_desc = nullptr;
-    uint32_t* d_tile_blk = nullptr;
-    int spread_ncap = 0;  // largest n4 of a tile (0: bulk staging not used)
+    // packed path: cell-major spreading matrix (sliced ELL, 32-cell slices; the layout is described
+    // at packed::spread_ell)
+    int2* d_ell_slice = nullptr;  // per slice {first entry, entries per cell}
+    uint2* d_ell_e = nullptr;     // per entry {point word, window value bits}
+    int4* d_ell_tile = nullptr;   // per tile {first entry, entries, first point, points}
+    int4* d_ell_run = nullptr;    // per tile {first sample, samples, staged, 0}
+    float* d_tap2 = nullptr;      // [P][Kp] taper pairs, point-major (FP32 complex)
+    int ell_ecap = 0, ell_pcap = 0, ell_ncap = 0;  // largest staged tile (multiples of 4)
+    int64_t ell_entries = 0;      // entries including padding
     void* d_deconv = nullptr;      // [I] C: exp(-i 2 pi m df t_ref) / phihat(m)
     void* d_tw1 = nullptr;         // [n1/2] C: exp(-i 2 pi q / n1)
     void* d_tw2 = nullptr;         // [n2/2] C: exp(-i 2 pi q / n2)

@@ -30,7 +30,7 @@ m2_status check_stage_status(m2nufft_plan_s* p) {
     if (h && ((volatile int*)h)[0] != 0) {
         const int where = ((volatile int*)h)[2];
         h[0] = h[1] = h[2] = 0;
-        set_error("an earlier launch of a packed stage kernel gave up waiting for a bulk copy (row %d; "
+        set_error("an earlier launch of a packed stage kernel gave up waiting for a bulk copy (spread tile %d; "
                   "M2_ERR_TIMEOUT)", where);
         return M2_ERR_TIMEOUT;
     }

@@ -35,19 +35,18 @@ int packed_k2max(const Geometry& g) {
 packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     const Geometry& g = p->g;
     packed::Ctx c;
+    c.ell_slice = p->d_ell_slice;
+    c.ell_e = p->d_ell_e;
+    c.ell_tile = p->d_ell_tile;
+    c.ell_run = p->d_ell_run;
+    c.tap2 = reinterpret_cast<const float2*>(p->d_tap2);
     c.pt_src = p->d_pt_src;
-    c.pt_cell = p->d_pt_cell;
-    c.pt_off = reinterpret_cast<const float*>(p->d_pt_off);
-    c.taper = reinterpret_cast<const float*>(p->d_taper);
-    c.P = g.P;
-    c.tile_pb = p->d_tile_pb;
-    c.tile_pe = p->d_tile_pe;
+    c.ecap = p->ell_ecap;
+    c.pcap = p->ell_pcap;
+    c.ncap = p->ell_ncap;
     c.N = (int)g.N;
     c.K = g.K;
     c.Kp = g.kp;
-    c.w = g.width;
-    c.two_over_w = (float)(2.0 / g.width);
-    c.beta = (float)g.beta;
     c.Lg = g.Lg;
     c.rows = (int)g.rows;
     c.n1 = (int)g.n1;
@@ -84,9 +83,6 @@ packed::Ctx packed_ctx(const m2nufft_plan_s* p) {
     c.wsum = reinterpret_cast<const float*>(p->d_wsum);
     c.wq = (float)p->wq;
     c.status = p->d_stage_status;
-    c.tile_desc = p->d_tile_desc;
-    c.tile_blk = p->d_tile_blk;
-    c.ncap = p->spread_ncap;
     return c;
 }
 
@@ -97,49 +93,33 @@ using packed::Tw32;
 using packed::kColWarps;
 using packed::kRowLen;
 
-// grid (ntiles, ceil(nb / SB)): one 256-cell tile of up to SB signals per CTA (SB <= 4, or <= 2
-// for five or more taper pairs, which keeps the accumulators in registers); the tile's points are
-// staged once for its SB signals
+// grid (ntiles, ceil(nb / NS)): one 256-cell tile of up to NS signals per CTA, whose entries, tapers
+// and sample runs are staged once; the signals are spread SB at a time (SB <= 4, or <= 2 for five
+// or more taper pairs, which keeps the accumulators in registers).  Dynamic smem
+// spread_ell_smem_bytes(Kp, NS, ecap, pcap, ncap).
 __host__ __device__ constexpr int spread_signals(int KP) { return KP <= 4 ? 4 : 2; }
-template <int KP, int SB>
-__global__ void __launch_bounds__(kSpreadTile) spread_packed_kernel(Ctx c, const float* __restrict__ x, int nb,
+template <int KP>
+__global__ void __launch_bounds__(kSpreadTile, 3) spread_ell_kernel(Ctx c, const float* __restrict__ x, int nb, int ns,
                                                                     float2* __restrict__ g) {
-    __shared__ __align__(16) unsigned char smem[packed::spread_multi_smem_bytes(KP, SB)];
-    const int b0 = blockIdx.y * SB;
-    packed::spread_tile_multi<KP, SB>(c, x + (int64_t)b0 * c.N, min(SB, nb - b0), blockIdx.x,
-                                      g + (int64_t)b0 * c.Kp * c.Lg, smem);
+    extern __shared__ __align__(16) unsigned char smem_sp[];
+    const int b0 = blockIdx.y * ns;
+    packed::spread_ell<KP, spread_signals(KP)>(c, x + (int64_t)b0 * c.N, min(ns, nb - b0), blockIdx.x,
+                                               g + (int64_t)b0 * c.Kp * c.Lg, smem_sp);
 }
 
-// the same with the tile's point block and sample runs copied in by cp.async.bulk (plans with tile
-// blocks); dynamic smem spread_bulk_smem_bytes(K, ncap, SB, 1)
-template <int KP, int SB>
-__global__ void __launch_bounds__(kSpreadTile) spread_bulk_kernel(Ctx c, const float* __restrict__ x, int nb,
-                                                                  float2* __restrict__ g) {
-    extern __shared__ __align__(16) unsigned char smem_sb[];
-    const int b0 = blockIdx.y * SB;
-    packed::spread_bulk<KP, SB, 1>(c, x + (int64_t)b0 * c.N, min(SB, nb - b0), blockIdx.x, 1,
-                                   g + (int64_t)b0 * c.Kp * c.Lg, smem_sb);
-}
-
-template <int KP, int SB>
-void launch_spread_sb(const Ctx& c, const float* x, int nb, float2* g, dim3 grid, cudaStream_t st) {
-    if (c.ncap > 0)
-        spread_bulk_kernel<KP, SB><<<grid, kSpreadTile, packed::spread_bulk_smem_bytes(c.K, c.ncap, SB, 1), st>>>(c, x,
-                                                                                                           nb, g);
-    else spread_packed_kernel<KP, SB><<<grid, kSpreadTile, 0, st>>>(c, x, nb, g);
-}
-
-// Signals per CTA: the most (sharing the staging of a tile's points) that still give the launch
-// about two CTAs per SM; fewer when a chunk is small.
+// Signals per CTA: as many as keep at least two CTAs per SM (and the staging within 96 KB), so a
+// tile's entries and tapers are staged once for as many signals as possible (32 jitter16k signals:
+// 8 per CTA, 14.3 us; one or four CTAs per SM measured 18.5 / 16.3 us).
 template <int KP>
 void launch_spread_packed(const Ctx& c, const float* x, int nb, float2* g, int sm_count, cudaStream_t st) {
     const int64_t ntiles = (c.Lg + kSpreadTile - 1) / kSpreadTile;
-    int sb = spread_signals(KP);
-    while (sb > 1 && ntiles * ((nb + sb - 1) / sb) < 2 * (int64_t)sm_count) sb /= 2;
-    dim3 grid((unsigned)ntiles, (unsigned)((nb + sb - 1) / sb));
-    if (sb >= 4) launch_spread_sb<KP, spread_signals(KP) >= 4 ? 4 : 2>(c, x, nb, g, grid, st);
-    else if (sb == 2) launch_spread_sb<KP, 2>(c, x, nb, g, grid, st);
-    else launch_spread_sb<KP, 1>(c, x, nb, g, grid, st);
+    int ns = std::max(1, nb);
+    while (ns > 1 && (ntiles * ((nb + ns - 1) / ns) < 2 * (int64_t)sm_count ||
+                      packed::spread_ell_smem_bytes(c.Kp, ns, c.ecap, c.pcap, c.ncap) > (size_t(96) << 10)))
+        ns = (ns + 1) / 2;
+    dim3 grid((unsigned)ntiles, (unsigned)((nb + ns - 1) / ns));
+    spread_ell_kernel<KP><<<grid, kSpreadTile, packed::spread_ell_smem_bytes(c.Kp, ns, c.ecap, c.pcap, c.ncap), st>>>(
+        c, x, nb, ns, g);
 }
 
 // grid (1024 / 32, Kp, nb): 32 columns of one taper pair per CTA of 4 warps
@@ -206,6 +186,10 @@ m2_status launch_rowfft(const Ctx& c, const Tw32& tw, float2* Z, int nb, cudaStr
 }  // namespace
 
 m2_status init_fast_kernels(int smem_optin) {
+    const void* spread[] = {(const void*)spread_ell_kernel<2>, (const void*)spread_ell_kernel<4>,
+                            (const void*)spread_ell_kernel<8>};
+    for (const void* f : spread)
+        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
     const void* funcs[] = {
         (const void*)cols_fast_kernel<2>,  (const void*)cols_fast_kernel<4>, (const void*)cols_fast_kernel<8>,
         (const void*)cols_fast_kernel<16>, (const void*)cols_fast_kernel<32>, (const void*)rowfft_kernel<2>,
@@ -213,17 +197,6 @@ m2_status init_fast_kernels(int smem_optin) {
     };
     for (const void* f : funcs)
         M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
-    const void* bulk[] = {
-        (const void*)spread_bulk_kernel<2, 1>, (const void*)spread_bulk_kernel<2, 2>, (const void*)spread_bulk_kernel<2, 4>,
-        (const void*)spread_bulk_kernel<4, 1>, (const void*)spread_bulk_kernel<4, 2>, (const void*)spread_bulk_kernel<4, 4>,
-        (const void*)spread_bulk_kernel<8, 1>, (const void*)spread_bulk_kernel<8, 2>,
-    };
-    for (const void* f : bulk) {
-        cudaFuncAttributes fa;
-        M2_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
-        M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_optin - (int)fa.sharedSizeBytes));
-    }
     return M2_OK;
 }
 

@@ -54,30 +54,19 @@ __device__ __forceinline__ void load_task(const HTask* tasks, const Ctx* ctxs, i
     __syncthreads();
 }
 
-// map entry: (task, first tile, tiles); up to NT tiles per CTA amortise the dependent loads
-// (tile bounds, point records, samples) over more cells
+// map entry: (task, first tile, tiles); up to NT tiles per CTA, one after the other (the task
+// prologue is amortised over them).  Dynamic smem: the largest spread_ell_smem_bytes(Kp, 1, ...) of the batch.
 template <int KP, int NT>
 __global__ void __launch_bounds__(kSpreadTile) hb_spread_kernel(const int4* __restrict__ map, const HTask* tasks,
                                                                 const Ctx* ctxs, float2* ws) {
-    __shared__ __align__(16) unsigned char smem[packed::spread_smem_bytes(KP)];
-    __shared__ __align__(16) Ctx s_ctx;
-    __shared__ __align__(16) HTask s_task;
-    const int4 m = map[blockIdx.x];
-    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
-    packed::spread_tiles<KP, NT>(s_ctx, s_task.x, m.y, m.z, ws + s_task.g_off, smem);
-}
-
-// the same with each tile's point block and sample run copied in by cp.async.bulk (every plan of
-// the batch has tile blocks); dynamic smem spread_bulk_smem_bytes(Kmax, ncap_max, 1, NT)
-template <int KP, int NT>
-__global__ void __launch_bounds__(kSpreadTile) hb_spread_bulk_kernel(const int4* __restrict__ map, const HTask* tasks,
-                                                                     const Ctx* ctxs, float2* ws) {
     extern __shared__ __align__(16) unsigned char smem_hb[];
     __shared__ __align__(16) Ctx s_ctx;
     __shared__ __align__(16) HTask s_task;
     const int4 m = map[blockIdx.x];
     load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
-    packed::spread_bulk<KP, 1, NT>(s_ctx, s_task.x, 1, m.y, m.z, ws + s_task.g_off, smem_hb);
+#pragma unroll 1
+    for (int u = 0; u < NT && u < m.z; ++u)
+        packed::spread_ell<KP, 1>(s_ctx, s_task.x, 1, m.y + u, ws + s_task.g_off, smem_hb);
 }
 
 // map entry: (task, pair, first column, warps per 32-column group); the CTA's 4 warps form
@@ -174,14 +163,12 @@ m2_status init_hbatch_kernels(int smem_optin) {
                            (const void*)hb_cols_kernel<8>,  (const void*)hb_cols_kernel<16>,
                            (const void*)hb_cols_kernel<32>, (const void*)hb_rows_kernel<4>,
                            (const void*)hb_rows_kernel<8>};
-    const void* bulk[] = {
-        (const void*)hb_spread_bulk_kernel<2, 1>, (const void*)hb_spread_bulk_kernel<2, 2>,
-        (const void*)hb_spread_bulk_kernel<2, 4>, (const void*)hb_spread_bulk_kernel<4, 1>,
-        (const void*)hb_spread_bulk_kernel<4, 2>, (const void*)hb_spread_bulk_kernel<4, 4>,
-        (const void*)hb_spread_bulk_kernel<8, 1>, (const void*)hb_spread_bulk_kernel<8, 2>,
-        (const void*)hb_spread_bulk_kernel<8, 4>,
+    const void* spread[] = {
+        (const void*)hb_spread_kernel<2, 1>, (const void*)hb_spread_kernel<2, 2>, (const void*)hb_spread_kernel<2, 4>,
+        (const void*)hb_spread_kernel<4, 1>, (const void*)hb_spread_kernel<4, 2>, (const void*)hb_spread_kernel<4, 4>,
+        (const void*)hb_spread_kernel<8, 1>, (const void*)hb_spread_kernel<8, 2>, (const void*)hb_spread_kernel<8, 4>,
     };
-    for (const void* f : bulk) {
+    for (const void* f : spread) {
         cudaFuncAttributes fa;
         M2_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
         M2_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -206,15 +193,8 @@ struct Maps {
     std::vector<int4> ro;
     std::vector<int2> ep;
     int64_t ws_f2 = 0;  // workspace, float2 units
-    // bulk-staged spreading when every task's plan has tile blocks: the largest K and block size
-    bool bulk = true;
-    int bulk_k = 0, bulk_ncap = 0;
-    int spread_nt = 1;
-    size_t spread_smem() const {
-        if (!bulk || bulk_ncap == 0) return 0;
-        const size_t b = packed::spread_bulk_smem_bytes(bulk_k, bulk_ncap, 1, spread_nt);
-        return b <= (size_t(160) << 10) ? b : 0;
-    }
+    size_t spread_smem_max = 16;  // largest shared memory a task's spread tiles need
+    size_t spread_smem() const { return spread_smem_max; }
 };
 
 // Append task `task` of context c (geometry g) to the maps, in the CTA shapes of cfg; its
@@ -230,10 +210,7 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const H
     // spread: cfg.spread_tiles tiles per CTA
     const int kpc = c.Kp <= 2 ? 0 : (c.Kp <= 4 ? 1 : 2);
     const int nt = cfg.spread_tiles;
-    m.spread_nt = nt;
-    if (c.ncap == 0) m.bulk = false;
-    m.bulk_k = std::max(m.bulk_k, c.K);
-    m.bulk_ncap = std::max(m.bulk_ncap, c.ncap);
+    m.spread_smem_max = std::max(m.spread_smem_max, packed::spread_ell_smem_bytes(c.Kp, 1, c.ecap, c.pcap, c.ncap));
     for (int64_t tile = 0; tile < ntiles; tile += nt)
         m.sp[kpc].push_back(make_int4(task, (int)tile, (int)std::min<int64_t>(nt, ntiles - tile), 0));
     // column DFTs: one coset per warp where the C = n1 / F cosets allow it (C = 1: four one-warp
@@ -258,7 +235,7 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const H
 struct MapView {
     const int4* sp[3] = {};
     int n_sp[3] = {};
-    size_t spread_smem = 0;  // > 0: bulk-staged spreading with this dynamic shared memory
+    size_t spread_smem = 0;  // dynamic shared memory of the spread launches
     const int4* co[6] = {};
     int n_co[6] = {};
     size_t smem_cols[6] = {};
@@ -270,16 +247,10 @@ struct MapView {
 
 template <int NT>
 void launch_spread_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, float2* ws, cudaStream_t st) {
-    if (v.spread_smem > 0) {
-        const size_t sm = v.spread_smem;
-        if (v.n_sp[0]) hb_spread_bulk_kernel<2, NT><<<v.n_sp[0], kSpreadTile, sm, st>>>(v.sp[0], tasks, ctxs, ws);
-        if (v.n_sp[1]) hb_spread_bulk_kernel<4, NT><<<v.n_sp[1], kSpreadTile, sm, st>>>(v.sp[1], tasks, ctxs, ws);
-        if (v.n_sp[2]) hb_spread_bulk_kernel<8, NT><<<v.n_sp[2], kSpreadTile, sm, st>>>(v.sp[2], tasks, ctxs, ws);
-        return;
-    }
-    if (v.n_sp[0]) hb_spread_kernel<2, NT><<<v.n_sp[0], kSpreadTile, 0, st>>>(v.sp[0], tasks, ctxs, ws);
-    if (v.n_sp[1]) hb_spread_kernel<4, NT><<<v.n_sp[1], kSpreadTile, 0, st>>>(v.sp[1], tasks, ctxs, ws);
-    if (v.n_sp[2]) hb_spread_kernel<8, NT><<<v.n_sp[2], kSpreadTile, 0, st>>>(v.sp[2], tasks, ctxs, ws);
+    const size_t sm = v.spread_smem;
+    if (v.n_sp[0]) hb_spread_kernel<2, NT><<<v.n_sp[0], kSpreadTile, sm, st>>>(v.sp[0], tasks, ctxs, ws);
+    if (v.n_sp[1]) hb_spread_kernel<4, NT><<<v.n_sp[1], kSpreadTile, sm, st>>>(v.sp[1], tasks, ctxs, ws);
+    if (v.n_sp[2]) hb_spread_kernel<8, NT><<<v.n_sp[2], kSpreadTile, sm, st>>>(v.sp[2], tasks, ctxs, ws);
 }
 
 m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, const Tw32& tw, float2* ws,

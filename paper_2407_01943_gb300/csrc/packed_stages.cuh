@@ -76,15 +76,17 @@ __device__ __forceinline__ void fft_reg(float2 (&v)[N], const Tw32& tw) {
 
 // Plan data the stages read (one plan; device pointers).
 struct __align__(16) Ctx {
-    const int32_t* pt_src;
-    const int32_t* pt_cell;
-    const float* pt_off;
-    const float* taper;  // [K][P] real
-    int64_t P;
-    const int32_t* tile_pb;
-    const int32_t* tile_pe;
-    int N, K, Kp, w;
-    float two_over_w, beta;
+    // cell-major spreading matrix (sliced ELL, see spread_ell): per 32-cell slice {first entry,
+    // entries per cell}; per entry {point word, window value}; per 256-cell tile its entry and point
+    // ranges and its sample run; taper pairs point-major and the points' sample indices
+    const int2* ell_slice;
+    const uint2* ell_e;
+    const int4* ell_tile;
+    const int4* ell_run;
+    const float2* tap2;    // [P][Kp]
+    const int32_t* pt_src; // [P]
+    int ecap, pcap, ncap;  // largest staged tile: entries, points, samples (multiples of 4)
+    int N, K, Kp;
     int64_t Lg;          // spread cells per pair = rows * 1024
     int rows, n1;
     int I, i_c, nf, k2max;
@@ -100,13 +102,6 @@ struct __align__(16) Ctx {
     const float* wsum;     // [K] W_k^0(0) = sum_n w_k(t_n) (F-statistic), or NULL
     float wq;              // sum_k W_k^0(0)^2
     int* status;           // mapped host word [flag, code, where, 0] set by a stage whose bounded wait gave up
-    // bulk-staged spreading: per tile a descriptor (first word of its block, points n, first sample,
-    // samples contiguous) and a 16-byte aligned block [cell | off | taper pairs | src]: n4 = n rounded
-    // up to 4 words per section (n4 <= ncap), each taper pair (2j, 2j + 1) interleaved over two
-    // sections (taper K of an odd K is 0); ncap = 0: not available
-    const int4* tile_desc;
-    const uint32_t* tile_blk;
-    int ncap;
 };
 
 // Drop a dead 128-byte line of an intermediate from L2 without writing it back (its contents
@@ -185,315 +180,182 @@ __device__ __forceinline__ void stage_timeout(int* status, int where) {
     }
 }
 
-// Window value of a point at cell ci: off = (first cell of its window) - u_n, dcell = ci - first
-// cell; the exponential of semicircle phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)).  Every rounding
-// is spelled out so that all spreading variants compute the same bits.
-__device__ __forceinline__ float spread_phi(const Ctx& c, float off, int dcell) {
-    const float z = __fadd_rn(off, (float)dcell);
-    const float a = __fmul_rn(z, c.two_over_w);
-    return expf(__fmul_rn(c.beta, __fadd_rn(sqrtf(fmaxf(0.f, __fmaf_rn(-a, a, 1.f))), -1.f)));
+// ---------------------------------------------------------------------------
+// Spreading by the plan's cell-major spreading matrix (sliced ELL, slices of 32 cells):
+//   g[j][c] = sum over the points p whose window covers cell c (ascending p) of
+//             ((u_{2j}[p] + i u_{2j+1}[p]) * phi_p(c)) x[src(p)]
+// with phi_p(c) = phi(c - u_p) the exponential-of-semicircle window.  The window values depend only
+// on the sampling pattern, so the plan evaluates them once (FP64, rounded to FP32) and stores them
+// per (cell, point) entry; spreading a signal is then a streaming sparse product with no
+// transcendental functions.  Entry e of cell 32 s + l (slice s) is ell_e[sl.x + 32 e + l]
+// (sl = ell_slice[s] = {first entry, entries per cell}): {point word, phi bits}, point word
+// 0xffffffff = padding.  Per 256-cell tile, ell_tile = {first entry, entries, first point,
+// points} (its slices' entries and its points are contiguous) and ell_run = {first sample,
+// samples, staged, 0}.  Staged tiles (staged != 0): the point word is (p - first point) |
+// (src(p) - first sample) << 16, and thread 0 copies the tile's entries, its points' taper pairs
+// (tap2 [P][Kp], point-major) and the run of samples of each of the SB signals into shared memory
+// with cp.async.bulk, completed on one mbarrier; the cells then read only shared memory.  Other
+// tiles: the point word is p, and entries, tapers (tap2) and samples (src = pt_src[p]) are read
+// from global memory.  A warp spreads one slice (lane l: cell 32 s + l), a 256-thread CTA one tile
+// for nsb signals (x and g strided by N and Kp * Lg), SB at a time; each product is rounded as
+//   w = phi * u (per component), acc = fma(w, x, acc)   in ascending entry order,
+// so every executor writes the same bits.  A copy that has not landed within 2 s is recorded in
+// c.status and the CTA writes nothing.  Called by all 256 threads of the CTA.
+// smem (16-byte aligned): spread_ell_smem_bytes(Kp, nsb, ecap, pcap, ncap).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t spread_ell_tap_off(int ecap) { return 16 + (size_t)8 * ecap; }
+__host__ __device__ constexpr size_t spread_ell_x_off(int Kp, int ecap, int pcap) {
+    return spread_ell_tap_off(ecap) + (((size_t)8 * ((size_t)pcap * Kp + 2) + 15) & ~(size_t)15);
 }
-// acc += (taper pair * sample) * phi, the tapered sample rounded first
-__device__ __forceinline__ void spread_mac(float2& acc, float2 tp, float xv, float phi) {
-    acc.x = __fmaf_rn(__fmul_rn(tp.x, xv), phi, acc.x);
-    acc.y = __fmaf_rn(__fmul_rn(tp.y, xv), phi, acc.y);
+__host__ __device__ constexpr size_t spread_ell_smem_bytes(int Kp, int SB, int ecap, int pcap, int ncap) {
+    return spread_ell_x_off(Kp, ecap, pcap) + (size_t)4 * SB * (ncap > 0 ? ncap + 8 : 0);
 }
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+constexpr unsigned kEllPad = 0xffffffffu;
 
-// ---------------------------------------------------------------------------
-// spread tiles [tile0, tile0 + nt) (256 cells each, nt <= NT) of one signal:
-//   g[j][c] = sum_n (u_{2j}[n] + i u_{2j+1}[n]) x[n] phi(c - u_n)
-// Thread = cell tile0 * 256 + 256 u + threadIdx.x for u < nt.  The points whose
-// windows meet the tiles are staged in chunks; every cell adds its points in
-// ascending point order, so the result does not depend on NT.
-// blockDim = kSpreadTile; smem >= spread_smem_bytes(KP).
-// ---------------------------------------------------------------------------
-template <int KP, int NT>
-__device__ __forceinline__ void spread_tiles(const Ctx& c, const float* __restrict__ xb, int tile0, int nt,
-                                             float2* __restrict__ gb, unsigned char* smem) {
-    int32_t* s_cell = reinterpret_cast<int32_t*>(smem);
-    float* s_off = reinterpret_cast<float*>(smem + 4 * kSpreadChunk);
-    float2* s_val = reinterpret_cast<float2*>(smem + 8 * kSpreadChunk);  // [KP][chunk]
-    const int64_t cell0 = (int64_t)tile0 * kSpreadTile + threadIdx.x;
-    const int pb = c.tile_pb[tile0], pe = c.tile_pe[tile0 + nt - 1];
-    float2 acc[NT][KP];
+// the products of one entry for SB signals: w_j = phi * u_j, acc[b][j] += w_j * x_b
+template <int KP, int SB>
+__device__ __forceinline__ void spread_ell_mac(float2 (&acc)[SB][KP], const float2 (&u)[KP], float phi,
+                                               const float (&xv)[SB], int nsb) {
 #pragma unroll
-    for (int u = 0; u < NT; ++u)
+    for (int j = 0; j < KP; ++j) {
+        const float2 wj = make_float2(__fmul_rn(phi, u[j].x), __fmul_rn(phi, u[j].y));
 #pragma unroll
-        for (int j = 0; j < KP; ++j) acc[u][j] = make_float2(0.f, 0.f);
-    for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
-        const int n = min(kSpreadChunk, pe - q0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int p = q0 + t;
-            s_cell[t] = c.pt_cell[p];
-            s_off[t] = c.pt_off[p];
-            const float xv = xb[c.pt_src[p]];
-#pragma unroll
-            for (int j = 0; j < KP; ++j) {
-                float2 v = make_float2(0.f, 0.f);
-                if (2 * j < c.K) v.x = __fmul_rn(c.taper[(int64_t)(2 * j) * c.P + p], xv);
-                if (2 * j + 1 < c.K) v.y = __fmul_rn(c.taper[(int64_t)(2 * j + 1) * c.P + p], xv);
-                s_val[j * kSpreadChunk + t] = v;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            const int64_t cell = cell0 + (int64_t)u * kSpreadTile;
-            if (u < nt && cell < c.Lg) {
-                const int ci = (int)cell;
-                int lo = 0, hi = n;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
-                }
-                for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
-                    const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
-#pragma unroll
-                    for (int j = 0; j < KP; ++j) {
-                        const float2 v = s_val[j * kSpreadChunk + t];  // already the tapered sample
-                        acc[u][j].x = __fmaf_rn(v.x, phi, acc[u][j].x);
-                        acc[u][j].y = __fmaf_rn(v.y, phi, acc[u][j].y);
-                    }
-                }
+        for (int b = 0; b < SB; ++b) {
+            if (b < nsb) {
+                acc[b][j].x = __fmaf_rn(wj.x, xv[b], acc[b][j].x);
+                acc[b][j].y = __fmaf_rn(wj.y, xv[b], acc[b][j].y);
             }
         }
     }
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        const int64_t cell = cell0 + (int64_t)u * kSpreadTile;
-        if (u < nt && cell < c.Lg) {
-#pragma unroll
-            for (int j = 0; j < KP; ++j)
-                if (j < c.Kp) gb[(int64_t)j * c.Lg + cell] = acc[u][j];
-        }
-    }
-    __syncthreads();  // smem reuse by the next stage of this CTA
-}
-
-template <int KP>
-__device__ __forceinline__ void spread_tile(const Ctx& c, const float* __restrict__ xb, int tile,
-                                            float2* __restrict__ gb, unsigned char* smem) {
-    spread_tiles<KP, 1>(c, xb, tile, 1, gb, smem);
-}
-
-// ---------------------------------------------------------------------------
-// spread one tile for SB signals of one plan at once (signals b0 .. b0 + nsb - 1,
-// x and g strided by N and Kp * Lg): the point records, tapers and window
-// searches are shared by all signals of a plan, so they are staged once per
-// tile; per signal the arithmetic and its order are those of spread_tiles, so
-// each signal's grid is bit-identical to spreading it alone.
-// smem >= spread_multi_smem_bytes(KP, SB).
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr size_t spread_multi_smem_bytes(int KP, int SB) {
-    return (size_t)8 * kSpreadChunk + (size_t)KP * kSpreadChunk * 8 + (size_t)SB * kSpreadChunk * 4;
 }
 
 template <int KP, int SB>
-__device__ __forceinline__ void spread_tile_multi(const Ctx& c, const float* __restrict__ x, int nsb, int tile,
-                                                  float2* __restrict__ g, unsigned char* smem) {
-    int32_t* s_cell = reinterpret_cast<int32_t*>(smem);
-    float* s_off = reinterpret_cast<float*>(smem + 4 * kSpreadChunk);
-    float2* s_tap = reinterpret_cast<float2*>(smem + 8 * kSpreadChunk);                      // [KP][chunk]
-    float* s_x = reinterpret_cast<float*>(smem + 8 * kSpreadChunk + KP * kSpreadChunk * 8);  // [SB][chunk]
-    const int64_t cell = (int64_t)tile * kSpreadTile + threadIdx.x;
-    const int pb = c.tile_pb[tile], pe = c.tile_pe[tile];
-    float2 acc[SB][KP];
-#pragma unroll
-    for (int b = 0; b < SB; ++b)
-#pragma unroll
-        for (int j = 0; j < KP; ++j) acc[b][j] = make_float2(0.f, 0.f);
-    for (int q0 = pb; q0 < pe; q0 += kSpreadChunk) {
-        const int n = min(kSpreadChunk, pe - q0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < n; t += blockDim.x) {
-            const int p = q0 + t;
-            s_cell[t] = c.pt_cell[p];
-            s_off[t] = c.pt_off[p];
-            const int src = c.pt_src[p];
-#pragma unroll
-            for (int b = 0; b < SB; ++b) s_x[b * kSpreadChunk + t] = b < nsb ? x[(int64_t)b * c.N + src] : 0.f;
-#pragma unroll
-            for (int j = 0; j < KP; ++j) {
-                float2 v = make_float2(0.f, 0.f);
-                if (2 * j < c.K) v.x = c.taper[(int64_t)(2 * j) * c.P + p];
-                if (2 * j + 1 < c.K) v.y = c.taper[(int64_t)(2 * j + 1) * c.P + p];
-                s_tap[j * kSpreadChunk + t] = v;
-            }
-        }
-        __syncthreads();
-        if (cell < c.Lg) {
-            const int ci = (int)cell;
-            int lo = 0, hi = n;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
-            }
-            for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
-                const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
-#pragma unroll
-                for (int b = 0; b < SB; ++b) {
-                    const float xv = s_x[b * kSpreadChunk + t];
-#pragma unroll
-                    for (int j = 0; j < KP; ++j) spread_mac(acc[b][j], s_tap[j * kSpreadChunk + t], xv, phi);
-                }
-            }
-        }
-    }
-    if (cell < c.Lg) {
-#pragma unroll
-        for (int b = 0; b < SB; ++b)
-            if (b < nsb) {
-#pragma unroll
-                for (int j = 0; j < KP; ++j)
-                    if (j < c.Kp) g[((int64_t)b * c.Kp + j) * c.Lg + cell] = acc[b][j];
-            }
-    }
-}
-
-__host__ __device__ constexpr size_t spread_smem_bytes(int KP) { return (size_t)8 * kSpreadChunk + (size_t)KP * kSpreadChunk * 8; }
-
-// ---------------------------------------------------------------------------
-// Bulk-staged spreading of tiles [tile0, tile0 + nt) (nt <= NT) for SB signals (b0 .. b0 + nsb - 1
-// of x, strided by N; grids strided by Kp * Lg), one cell per thread and tile.  Thread 0 reads the
-// tiles' descriptors and copies each tile's point block (cp.async.bulk, one copy per tile) and,
-// where a tile's points come from one contiguous run of samples, that run of each signal (one
-// copy per tile and signal, widened to 16-byte boundaries) into shared memory, all completed on
-// one mbarrier; tiles whose samples are not contiguous gather them after the copies land.  The
-// cells then add their points in ascending point order with the arithmetic of spread_tiles, so
-// the grids are bit-identical to it.  A copy that has not landed within 2 s is recorded in
-// c.status and the CTA writes nothing.
-// smem (16-byte aligned): spread_bulk_smem_bytes(K, ncap, SB, NT).
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr size_t spread_bulk_meta_bytes(int SB, int NT) {
-    return 16 + (size_t)16 * NT + ((size_t)4 * SB * NT + 15) / 16 * 16;
-}
-__host__ __device__ inline size_t spread_bulk_smem_bytes(int K, int ncap, int SB, int NT) {
-    return spread_bulk_meta_bytes(SB, NT) +
-           (size_t)4 * NT * ((size_t)(3 + 2 * ((K + 1) / 2)) * ncap + (size_t)SB * (ncap + 8));
-}
-
-template <int KP, int SB, int NT>
-__device__ __forceinline__ void spread_bulk(const Ctx& c, const float* __restrict__ x, int nsb, int tile0, int nt,
-                                            float2* __restrict__ g, unsigned char* smem) {
+__device__ __forceinline__ void spread_ell(const Ctx& c, const float* __restrict__ x, int nsb, int tile,
+                                           float2* __restrict__ g, unsigned char* smem) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    int4* s_desc = reinterpret_cast<int4*>(smem + 16);                // [NT]
-    int* s_xoff = reinterpret_cast<int*>(smem + 16 + 16 * NT);       // [NT][SB] first sample's offset in its run
-    const int ncap = c.ncap;
-    const int nsec = 2 + 2 * c.Kp;  // cell, off, taper pairs (the src section follows)
-    const size_t blk_words = (size_t)(nsec + 1) * ncap;
-    uint32_t* s_blk = reinterpret_cast<uint32_t*>(smem + spread_bulk_meta_bytes(SB, NT));  // [NT][blk_words]
-    float* s_x = reinterpret_cast<float*>(s_blk + (size_t)NT * blk_words);                 // [NT][SB][ncap + 8]
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint64_t pol = l2_evict_first_policy();
-        int4 d[NT];
-        unsigned total = 0;
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            d[u] = u < nt ? __ldg(c.tile_desc + tile0 + u) : make_int4(0, 0, 0, 1);
-            s_desc[u] = d[u];
-            const unsigned n4 = (unsigned)((d[u].y + 3) & ~3);
-            total += 4u * n4 * (unsigned)(nsec + (d[u].w ? 0 : 1));
-#pragma unroll
-            for (int b = 0; b < SB; ++b) {
-                s_xoff[u * SB + b] = 0;  // every entry is defined, also for signals b >= nsb
-                if (d[u].w && b < nsb && d[u].y > 0) {
-                    const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + d[u].z);
-                    const uintptr_t lo = a0 & ~(uintptr_t)15, hi = (a0 + 4u * (unsigned)d[u].y + 15) & ~(uintptr_t)15;
-                    s_xoff[u * SB + b] = (int)((a0 - lo) >> 2);
-                    total += (unsigned)(hi - lo);
-                }
+    const uint2* s_e = reinterpret_cast<const uint2*>(smem + 16);
+    const int4 tb = __ldg(c.ell_tile + tile);  // {first entry, entries, first point, points}
+    const int4 tr = __ldg(c.ell_run + tile);   // {first sample, samples, staged, 0}
+    const bool staged = tr.z != 0;             // uniform over the CTA
+    const int Kp = c.Kp;
+    const int ldx = c.ncap + 8;
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)tile * (kSpreadTile / 32) + (threadIdx.x >> 5);
+    const int64_t cell = s * 32 + lane;
+    const int2 sl = cell < c.Lg ? __ldg(c.ell_slice + s) : make_int2(0, 0);  // loaded while the copies fly
+    const float2* s_tap = reinterpret_cast<const float2*>(smem + spread_ell_tap_off(c.ecap));
+    const float* s_x = reinterpret_cast<const float*>(smem + spread_ell_x_off(Kp, c.ecap, c.pcap));
+    int to = 0;  // staged: position of point tb.z's taper pairs in s_tap (float2 units)
+    // staged: position of sample tr.x of signal b in s_x[b] (the copy starts on the 16-byte boundary
+    // at or below it)
+    auto xoff = [&](int b) { return (int)((reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + tr.x) & 15u) >> 2); };
+    if (staged) {
+        fence_async_smem();  // earlier reads of this shared memory before the copies overwrite it
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        const uintptr_t ta = reinterpret_cast<uintptr_t>(c.tap2 + (int64_t)tb.z * Kp);
+        const uintptr_t tlo = ta & ~(uintptr_t)15, thi = (ta + (uintptr_t)8 * tb.w * Kp + 15) & ~(uintptr_t)15;
+        to = (int)((ta - tlo) >> 3);
+        if (threadIdx.x == 0) {
+            unsigned total = 8u * (unsigned)tb.y + (unsigned)(thi - tlo);
+            for (int b = 0; b < nsb; ++b) {
+                const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + tr.x);
+                total += (unsigned)(((a0 + 4u * (unsigned)tr.y + 15) & ~(uintptr_t)15) - (a0 & ~(uintptr_t)15));
+            }
+            const uint64_t pol = l2_evict_first_policy();
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
+                         : "memory");
+            if (tb.y > 0) bulk_copy(smem + 16, c.ell_e + tb.x, 8u * (unsigned)tb.y, bar, pol);
+            if (thi > tlo)
+                bulk_copy(smem + spread_ell_tap_off(c.ecap), reinterpret_cast<const void*>(tlo), (unsigned)(thi - tlo),
+                          bar, pol);
+            for (int b = 0; b < nsb; ++b) {
+                const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + tr.x);
+                const uintptr_t lo = a0 & ~(uintptr_t)15, hi = (a0 + 4u * (unsigned)tr.y + 15) & ~(uintptr_t)15;
+                bulk_copy(const_cast<float*>(s_x) + b * ldx, reinterpret_cast<const void*>(lo), (unsigned)(hi - lo),
+                          bar, pol);
             }
         }
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(total)
-                     : "memory");
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            const unsigned n4 = (unsigned)((d[u].y + 3) & ~3);
-            if (n4 == 0) continue;
-            // the block keeps its layout (sections n4 words apart): one copy, without the src section
-            // when the samples are one run
-            bulk_copy(s_blk + u * blk_words, c.tile_blk + d[u].x, 4u * n4 * (unsigned)(nsec + (d[u].w ? 0 : 1)), bar,
-                      pol);
-#pragma unroll
-            for (int b = 0; b < SB; ++b) {
-                if (d[u].w && b < nsb) {
-                    const uintptr_t a0 = reinterpret_cast<uintptr_t>(x + (int64_t)b * c.N + d[u].z);
-                    const uintptr_t lo = a0 & ~(uintptr_t)15, hi = (a0 + 4u * (unsigned)d[u].y + 15) & ~(uintptr_t)15;
-                    bulk_copy(s_x + ((size_t)u * SB + b) * (ncap + 8), reinterpret_cast<const void*>(lo),
-                              (unsigned)(hi - lo), bar, pol);
-                }
-            }
+        // one thread waits on the barrier (the others hold at the CTA barrier, taking no issue slots);
+        // the CTA barrier then makes the copied data visible to every thread
+        const bool late = threadIdx.x == 0 && !mbar_wait(bar, 0);
+        const bool any_late = __syncthreads_or(late);
+        if (threadIdx.x == 0 && !any_late) mbar_inval(bar);
+        if (any_late) {
+            if (threadIdx.x == 0) stage_timeout(c.status, tile);
+            return;
         }
     }
-    const bool late = !mbar_wait(bar, 0);
-    if (__syncthreads_or(late)) {
-        if (threadIdx.x == 0) stage_timeout(c.status, tile0);
-        return;
-    }
-    // tiles whose samples are not one run: gather them by the src section
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        const int4 d = s_desc[u];
-        if (d.w || d.y == 0) continue;
-        const int n4 = (d.y + 3) & ~3;
-        const int32_t* s_src = reinterpret_cast<const int32_t*>(s_blk + u * blk_words + (size_t)nsec * n4);
-        for (int t = threadIdx.x; t < d.y; t += blockDim.x) {
-            const int src = s_src[t];
-#pragma unroll
-            for (int b = 0; b < SB; ++b)
-                s_x[((size_t)u * SB + b) * (ncap + 8) + t] = b < nsb ? __ldg(x + (int64_t)b * c.N + src) : 0.f;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < NT; ++u) {
-        const int64_t cell = (int64_t)(tile0 + u) * kSpreadTile + threadIdx.x;
-        if (u >= nt || cell >= c.Lg) continue;
-        const int4 d = s_desc[u];
-        const int n = d.y, n4 = (n + 3) & ~3;
-        const int32_t* s_cell = reinterpret_cast<const int32_t*>(s_blk + u * blk_words);
-        const float* s_off = reinterpret_cast<const float*>(s_blk + u * blk_words + n4);
-        const float2* s_tap = reinterpret_cast<const float2*>(s_blk + u * blk_words + 2 * (size_t)n4);  // [Kp][n4]
-        const float* s_xu = s_x + (size_t)u * SB * (ncap + 8);
-        int xo[SB];
-#pragma unroll
-        for (int b = 0; b < SB; ++b) xo[b] = d.w && b < nsb ? s_xoff[u * SB + b] : 0;
+    if (cell >= c.Lg) return;  // no barrier follows
+    // with Kp == KP even, the tapers of a point are 16-byte aligned in s_tap (the copy starts on a
+    // 16-byte boundary and to = 0): read them two pairs at a time
+    const bool vec = (KP % 2 == 0) && Kp == KP;
+    // the signals in groups of SB, each group's accumulators in registers
+    for (int b0 = 0; b0 < nsb; b0 += SB) {
+        const int ng = min(SB, nsb - b0);
         float2 acc[SB][KP];
 #pragma unroll
         for (int b = 0; b < SB; ++b)
 #pragma unroll
             for (int j = 0; j < KP; ++j) acc[b][j] = make_float2(0.f, 0.f);
-        const int ci = (int)cell;
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (s_cell[mid] + c.w <= ci) lo = mid + 1; else hi = mid;
-        }
-        for (int t = lo; t < n && s_cell[t] <= ci; ++t) {
-            const float phi = spread_phi(c, s_off[t], ci - s_cell[t]);
-            float2 tp[KP];
+        if (staged) {
+            const uint2* es = s_e + (sl.x - tb.x) + lane;
+            int xo[SB];
 #pragma unroll
-            for (int j = 0; j < KP; ++j) tp[j] = j < c.Kp ? s_tap[(size_t)j * n4 + t] : make_float2(0.f, 0.f);
+            for (int b = 0; b < SB; ++b) xo[b] = (b0 + b) * ldx + (b < ng ? xoff(b0 + b) : 0);
+#pragma unroll 4
+            for (int e = 0; e < sl.y; ++e) {
+                const uint2 en = es[32 * e];
+                if (en.x == kEllPad) continue;
+                const int pl = (int)(en.x & 0xffffu), xl = (int)(en.x >> 16);
+                float2 u[KP];
+                if (vec) {
+                    const float4* t4 = reinterpret_cast<const float4*>(s_tap + to + pl * KP);
 #pragma unroll
-            for (int b = 0; b < SB; ++b) {
-                if (b >= nsb) break;
-                const float xv = s_xu[(size_t)b * (ncap + 8) + xo[b] + t];
+                    for (int j = 0; j < KP / 2; ++j) {
+                        const float4 v = t4[j];
+                        u[2 * j] = make_float2(v.x, v.y);
+                        u[2 * j + 1] = make_float2(v.z, v.w);
+                    }
+                } else {
 #pragma unroll
-                for (int j = 0; j < KP; ++j) spread_mac(acc[b][j], tp[j], xv, phi);
+                    for (int j = 0; j < KP; ++j) u[j] = j < Kp ? s_tap[to + pl * Kp + j] : make_float2(0.f, 0.f);
+                }
+                float xv[SB];
+#pragma unroll
+                for (int b = 0; b < SB; ++b) xv[b] = b < ng ? s_x[xo[b] + xl] : 0.f;
+                spread_ell_mac<KP, SB>(acc, u, __uint_as_float(en.y), xv, ng);
+            }
+        } else {
+            const uint2* eg = c.ell_e + sl.x + lane;
+            const float* xg = x + (int64_t)b0 * c.N;
+#pragma unroll 2
+            for (int e = 0; e < sl.y; ++e) {
+                const uint2 en = __ldg(eg + 32 * e);
+                if (en.x == kEllPad) continue;
+                const int p = (int)en.x;
+                const int q = __ldg(c.pt_src + p);
+                float2 u[KP];
+#pragma unroll
+                for (int j = 0; j < KP; ++j) u[j] = j < Kp ? __ldg(c.tap2 + (int64_t)p * Kp + j) : make_float2(0.f, 0.f);
+                float xv[SB];
+#pragma unroll
+                for (int b = 0; b < SB; ++b) xv[b] = b < ng ? __ldg(xg + (int64_t)b * c.N + q) : 0.f;
+                spread_ell_mac<KP, SB>(acc, u, __uint_as_float(en.y), xv, ng);
             }
         }
 #pragma unroll
         for (int b = 0; b < SB; ++b)
-            if (b < nsb) {
+            if (b < ng) {
 #pragma unroll
                 for (int j = 0; j < KP; ++j)
-                    if (j < c.Kp) g[((int64_t)b * c.Kp + j) * c.Lg + cell] = acc[b][j];
+                    if (j < Kp) g[((int64_t)(b0 + b) * Kp + j) * c.Lg + cell] = acc[b][j];
             }
     }
 }

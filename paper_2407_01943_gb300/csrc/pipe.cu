@@ -155,9 +155,9 @@ __device__ __forceinline__ void run_cols(const Ctx& c, const Tw32& tw, const flo
 }
 
 __device__ __forceinline__ void stage_spread(const Ctx& c, const float* x, int idx, float2* gb, unsigned char* smem) {
-    if (c.Kp <= 2) packed::spread_tile<2>(c, x, idx, gb, smem);
-    else if (c.Kp <= 4) packed::spread_tile<4>(c, x, idx, gb, smem);
-    else packed::spread_tile<8>(c, x, idx, gb, smem);
+    if (c.Kp <= 2) packed::spread_ell<2, 1>(c, x, 1, idx, gb, smem);
+    else if (c.Kp <= 4) packed::spread_ell<4, 1>(c, x, 1, idx, gb, smem);
+    else packed::spread_ell<8, 1>(c, x, 1, idx, gb, smem);
 }
 
 __device__ __forceinline__ void stage_cols(const Ctx& c, const Tw32& tw, const float2* gb, float2* Zb, int idx,
@@ -293,7 +293,7 @@ StageCounts stage_counts(const Ctx& c, int ntiles) {
 }
 
 size_t pipe_smem_bytes(const Ctx& c) {
-    const size_t spread = packed::spread_smem_bytes(8);
+    const size_t spread = packed::spread_ell_smem_bytes(c.Kp, 1, c.ecap, c.pcap, c.ncap);
     const size_t cols = sizeof(float2) * (packed::cols_tw_f2(false, c.n1, c.rows, c.F) +
                                           (size_t)(8 / c.cgw) * packed::cols_group_f2(false, c.rows, c.F, c.n1));
     const size_t rows = packed::rowfft_smem_bytes(kRowsPerItem);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "packed_stages.cuh"
 
 namespace m2 {
 
@@ -1092,43 +1093,113 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
         M2_TRY_OR(pb.upload(&p->d_tile_pe, tpe));
 
         if (g.path >= 2) {
-            // tile blocks for bulk-staged spreading: each tile's point records, tapers and sample
-            // indices as one 16-byte aligned block (sections of n4 = n rounded up to 4 words), and
-            // whether its samples are one contiguous run of x (then the kernel copies that run)
-            std::vector<int4> desc((size_t)g.ntiles);
-            std::vector<uint32_t> blk;
-            int ncap = 0;
-            for (int64_t j = 0; j < g.ntiles; ++j) {
-                const int b0 = tpb[j], n = tpe[j] - tpb[j], n4 = (n + 3) & ~3;
-                bool contig = true;
-                for (int q = 1; q < n && contig; ++q) contig = src[b0 + q] == src[b0] + q;
-                desc[(size_t)j] = make_int4((int)blk.size(), n, n > 0 ? src[b0] : 0, contig ? 1 : 0);
-                const size_t base = blk.size();
-                const int kp = (K + 1) / 2;
-                blk.resize(base + (size_t)(3 + 2 * kp) * n4, 0u);
-                for (int q = 0; q < n; ++q) {
-                    const int64_t pp = b0 + q;
-                    const float fo = (float)off[pp];
-                    std::memcpy(&blk[base + q], &cell[pp], 4);
-                    std::memcpy(&blk[base + n4 + q], &fo, 4);
-                    for (int k = 0; k < K; ++k) {  // taper pairs (2j, 2j + 1) interleaved, taper K = 0
-                        const float ft = (float)tap[(size_t)k * g.P + pp];
-                        std::memcpy(&blk[base + (size_t)(2 + 2 * (k / 2)) * n4 + 2 * q + (k & 1)], &ft, 4);
+            // cell-major spreading matrix (sliced ELL, slices of 32 cells): entry e of cell c is the
+            // e-th point p (ascending) whose window covers c, with the window value phi(c - u_p)
+            // evaluated in FP64 and rounded once to FP32; every cell of a slice has the slice's
+            // largest count of entries (padding entries are skipped)
+            const int Kp = (K + 1) / 2;
+            const int64_t nsl = (g.Lg + 31) / 32;
+            const int spt = kSpreadTile / 32;  // slices per tile
+            std::vector<int32_t> cnt((size_t)g.Lg, 0);
+            for (int64_t q = 0; q < g.P; ++q)
+                for (int d = 0; d < g.width; ++d) {
+                    const int64_t cc = (int64_t)cell[q] + d;
+                    if (cc >= 0 && cc < g.Lg) ++cnt[(size_t)cc];
+                }
+            std::vector<int2> sl((size_t)nsl);
+            int64_t ne = 0;
+            for (int64_t s = 0; s < nsl; ++s) {
+                int e = 0;
+                for (int64_t cc = 32 * s; cc < std::min<int64_t>(32 * s + 32, g.Lg); ++cc) e = std::max(e, cnt[(size_t)cc]);
+                sl[(size_t)s] = make_int2((int)ne, e);
+                ne += 32 * (int64_t)e;
+                if (ne > (int64_t)INT32_MAX) {
+                    set_error("internal: spreading matrix exceeds 2^31 entries");
+                    return bail(M2_ERR_ARG);
+                }
+            }
+            std::vector<int32_t> ep((size_t)ne, -1);  // point of each entry (-1: padding)
+            std::vector<float> ephi((size_t)ne, 0.f);
+            std::fill(cnt.begin(), cnt.end(), 0);  // now the fill cursor of each cell
+            const double two_over_w = 2.0 / g.width;
+            for (int64_t q = 0; q < g.P; ++q)
+                for (int d = 0; d < g.width; ++d) {
+                    const int64_t cc = (int64_t)cell[q] + d;
+                    if (cc < 0 || cc >= g.Lg) continue;
+                    const int64_t idx = sl[(size_t)(cc >> 5)].x + 32 * (int64_t)cnt[(size_t)cc]++ + (cc & 31);
+                    ep[(size_t)idx] = (int32_t)q;
+                    const double a = (off[q] + (double)d) * two_over_w;
+                    ephi[(size_t)idx] = (float)std::exp(g.beta * (std::sqrt(std::max(0.0, 1.0 - a * a)) - 1.0));
+                }
+            // per tile: its entries (contiguous: its slices), its points (contiguous: points are in
+            // cell order) and the run of samples they read; staged in shared memory when the run
+            // spans at most kMaxStagedRun samples and the caps of all staged tiles fit the budget
+            constexpr int kMaxStagedRun = 1024;
+            constexpr size_t kStageBudget = size_t(96) << 10;  // at 4 signals per CTA
+            std::vector<int4> tb((size_t)g.ntiles), tr((size_t)g.ntiles);
+            std::vector<char> staged((size_t)g.ntiles, 0);
+            for (int64_t t = 0; t < g.ntiles; ++t) {
+                const int64_t s0 = t * spt, s1 = std::min<int64_t>(s0 + spt, nsl);
+                const int64_t e0 = sl[(size_t)s0].x, e1 = s1 < nsl ? sl[(size_t)s1].x : ne;
+                int pmin = INT32_MAX, pmax = -1;
+                for (int64_t e = e0; e < e1; ++e)
+                    if (ep[(size_t)e] >= 0) {
+                        pmin = std::min(pmin, ep[(size_t)e]);
+                        pmax = std::max(pmax, ep[(size_t)e]);
                     }
-                    std::memcpy(&blk[base + (size_t)(2 + 2 * kp) * n4 + q], &src[pp], 4);
+                int smin = INT32_MAX, smax = -1;
+                for (int q = pmin; q <= pmax && pmax >= 0; ++q) {
+                    smin = std::min(smin, src[q]);
+                    smax = std::max(smax, src[q]);
                 }
-                ncap = std::max(ncap, n4);
+                const int np = pmax >= 0 ? pmax - pmin + 1 : 0;
+                const int run = smax >= smin ? smax - smin + 1 : 0;
+                tb[(size_t)t] = make_int4((int)e0, (int)(e1 - e0), np > 0 ? pmin : 0, np);
+                tr[(size_t)t] = make_int4(run > 0 ? smin : 0, run, 0, 0);
+                staged[(size_t)t] = np > 0 && np <= 65535 && run <= kMaxStagedRun;
             }
-            // staged in shared memory only while a CTA's share stays modest (about 64 KB)
-            if (ncap > 0 && (size_t)4 * ((size_t)(3 + 2 * ((K + 1) / 2)) * ncap + (size_t)4 * (ncap + 8)) <=
-                                (size_t(64) << 10)) {
-                if (blk.size() > (size_t)INT32_MAX) blk.clear();
-                if (!blk.empty()) {
-                    M2_TRY_OR(pb.upload(&p->d_tile_desc, desc));
-                    M2_TRY_OR(pb.upload(&p->d_tile_blk, blk));
-                    p->spread_ncap = ncap;
+            int ecap = 0, pcap = 0, ncap = 0;
+            for (;;) {
+                ecap = pcap = ncap = 0;
+                int64_t big = -1;
+                for (int64_t t = 0; t < g.ntiles; ++t)
+                    if (staged[(size_t)t]) {
+                        ecap = std::max(ecap, (tb[(size_t)t].y + 3) & ~3);
+                        pcap = std::max(pcap, (tb[(size_t)t].w + 3) & ~3);
+                        ncap = std::max(ncap, (tr[(size_t)t].y + 3) & ~3);
+                        if (big < 0 || tb[(size_t)t].y > tb[(size_t)big].y) big = t;
+                    }
+                if (big < 0 || packed::spread_ell_smem_bytes(Kp, 4, ecap, pcap, ncap) <= kStageBudget) break;
+                staged[(size_t)big] = 0;
+            }
+            std::vector<uint2> ee((size_t)ne);
+            for (int64_t t = 0; t < g.ntiles; ++t) {
+                tr[(size_t)t].z = staged[(size_t)t] ? 1 : 0;
+                for (int64_t e = tb[(size_t)t].x; e < (int64_t)tb[(size_t)t].x + tb[(size_t)t].y; ++e) {
+                    const int q = ep[(size_t)e];
+                    uint32_t word = 0xffffffffu;
+                    if (q >= 0)
+                        word = staged[(size_t)t] ? (uint32_t)(q - tb[(size_t)t].z) |
+                                                       ((uint32_t)(src[q] - tr[(size_t)t].x) << 16)
+                                                 : (uint32_t)q;
+                    uint32_t phib;
+                    std::memcpy(&phib, &ephi[(size_t)e], 4);
+                    ee[(size_t)e] = make_uint2(word, phib);
                 }
             }
+            // taper pairs point-major: tap2[q][j] = (u_{2j}[q], u_{2j+1}[q]) (u_K = 0 for odd K)
+            std::vector<float> t2((size_t)g.P * 2 * Kp, 0.f);
+            for (int64_t q = 0; q < g.P; ++q)
+                for (int k = 0; k < K; ++k) t2[(size_t)q * 2 * Kp + k] = (float)tap[(size_t)k * g.P + q];
+            M2_TRY_OR(pb.upload(&p->d_ell_slice, sl));
+            M2_TRY_OR(pb.upload(&p->d_ell_e, ee));
+            M2_TRY_OR(pb.upload(&p->d_ell_tile, tb));
+            M2_TRY_OR(pb.upload(&p->d_ell_run, tr));
+            M2_TRY_OR(pb.upload(&p->d_tap2, t2));
+            p->ell_ecap = ecap;
+            p->ell_pcap = pcap;
+            p->ell_ncap = ncap;
+            p->ell_entries = ne;
         }
     }
 
@@ -1565,6 +1636,7 @@ extern "C" m2_status m2nufft_get_info(m2nufft_plan_t p, m2_info* info) {
     info->path = g.path;
     info->device_bytes = p->device_bytes;
     info->gep_seconds = p->gep_seconds;
+    info->spread_entries = p->ell_entries;
     return M2_OK;
 }
 

@@ -59,3 +59,23 @@ def test_server_header_exports():
     lib = ctypes.CDLL(pkg.build())
     for n in names:
         assert hasattr(lib, n), n
+
+
+def test_info_layout_matches_c_compiler(tmp_path):
+    """m2_info as the C compiler lays it out from the header equals the binding's ctypes mirror."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "info.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "m2nufft.h"\n'
+                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(m2_info), offsetof(m2_info, gep_seconds),'
+                   ' offsetof(m2_info, spread_entries)); return 0; }\n')
+    exe = tmp_path / "info"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    size, gep, ent = (int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                      check=True).stdout.split())
+    assert ctypes.sizeof(binding.m2_info) == size
+    assert binding.m2_info.gep_seconds.offset == gep
+    assert binding.m2_info.spread_entries.offset == ent
