@@ -112,7 +112,9 @@ typedef struct {
                            the GPU; eigenvalues = the concentrations w^T R(A0) w / w^T R(B) w) */
     double sigma;       /* minimum oversampling nf / I: 0 = automatic (1.5 on the packed path with
                            the width ceil(1.25 log10(1/tol)) + 1; 2 on the generic path); at 2 or
-                           more the width is ceil(log10(1/tol)) + 1; accepted range [1.5, 8] */
+                           more the width is ceil(log10(1/tol)) + 1; packed plans below 1.5 (nf
+                           may then be 5 * 2^a) take ceil(ln(1/tol) / (pi sqrt(1 - 1/sigma))) + 1;
+                           accepted range [1.25, 8] */
     int tune;           /* 1 = autotune at plan time (m2nufft_plan / _with_tapers, packed FP32 plans):
                            candidate configurations -- sigma 1.5 or 2, 4, 8 or 16 signals per
                            chunk, the four-kernel or the persistent path -- are built from the

@@ -147,9 +147,11 @@ __global__ void __launch_bounds__(32 * R, (R <= 4 ? 5 : 2)) rowfft_kernel(Ctx c,
 
 // grid (epi_tiles(n1, k2max, T1), nb): one T1 x 16 tile of positions per CTA (and its partners);
 // kF adds the F-statistic output (16 x 16 tiles, 256 threads, one position each: every J_k of
-// the position stays in registers; 256 threads at <= 64 registers keep four CTAs per SM)
+// the position stays in registers; 256 threads at <= 64 registers keep four CTAs per SM).  Without
+// F: three 512-thread CTAs per SM (40 registers, room for the next pair's tile values loaded while
+// the current pair is computed; at four CTAs per SM the 32-register cap spills)
 constexpr int kEpiT1 = 32;
-constexpr int kEpiMinBlocks = 4;
+constexpr int kEpiMinBlocks = 3;
 __host__ __device__ constexpr int epi_t1(bool kF) { return kF ? 16 : kEpiT1; }
 __host__ __device__ constexpr int epi_threads(bool kF) { return 16 * epi_t1(kF); }  // one position per thread
 template <bool kF>

@@ -499,7 +499,8 @@ inline size_t rowfft_smem_bytes(int R) { return sizeof(float2) * (size_t)R * kRo
 // (n1 - k1, 1023 - k2), or (0, 1024 - k2) for k1 = 0, in the row transforms Y[j][k1][k2] of the
 // taper pairs j.  A tile is k1 in [k1a, k1a + T1) x k2 in [k2a, k2a + 16): per pair, its T1 row
 // segments and their partners' (one 128-byte line each) are staged in shared memory with
-// coalesced loads, then each thread unpacks, deconvolves and writes J and |J|^2 at m and -m for
+// coalesced loads (issued while the previous pair is computed, so their latency is hidden), then
+// each thread unpacks, deconvolves and writes J and |J|^2 at m and -m for
 // its positions -- consecutive threads take consecutive k1, so consecutive bands.  P-hat (and
 // with kF Thomson's F-statistic) accumulates over the pairs in registers.
 // Every in-band entry of Y is read by one position only (lower columns k2 <= k2max < 512 by
@@ -566,22 +567,48 @@ __device__ __forceinline__ void epi_tile(const Ctx& c, const float2* __restrict_
     float2 jk[kMaxPairs][2];  // kF: J of every taper at this position, for the residual of the line fit
     float2 csum = make_float2(0.f, 0.f);
 
+    // the tile entries this thread stages (16 threads per 128-byte row segment, so the loads are
+    // coalesced), their offsets within a plane, and the values of the next pair, loaded while the
+    // current pair is computed
+    bool lv[PPT];
+    int la[PPT], lb[PPT];  // within a plane (n1 * 1024 < 2^31)
+    float2 ra[PPT], rb[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+        const int e = threadIdx.x + u * NT;
+        const int lr = e / kEpiT2, lc = e % kEpiT2;
+        const int k1 = k1a + lr, k2 = k2a + lc;
+        lv[u] = k1 < n1 && k2 < nlo;
+        const int pk1 = k1 == 0 ? 0 : n1 - k1;
+        const int pk2 = k1 == 0 ? (kRowLen - k2) & (kRowLen - 1) : kRowLen - 1 - k2;
+        la[u] = k1 * kRowLen + k2;
+        lb[u] = pk1 * kRowLen + pk2;
+        ra[u] = rb[u] = make_float2(0.f, 0.f);
+    }
+    auto fetch = [&](int j) {
+        const float2* Yj = Yb + (int64_t)j * plane;
+#pragma unroll
+        for (int u = 0; u < PPT; ++u)
+            if (lv[u]) {
+                ra[u] = ld_inter<kStream>(Yj + la[u]);
+                rb[u] = ld_inter<kStream>(Yj + lb[u]);
+            }
+    };
+    fetch(0);
+
     auto pair = [&](int j) {
         const float2* Yj = Yb + (int64_t)j * plane;
         __syncthreads();  // the previous pair's reads of the tile are done
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
             const int e = threadIdx.x + u * NT;
-            const int lr = e / kEpiT2, lc = e % kEpiT2;  // 16 threads per 128-byte row segment
-            const int k1 = k1a + lr, k2 = k2a + lc;
-            if (k1 < n1 && k2 < nlo) {
-                sA[lr * LD + lc] = ld_inter<kStream>(Yj + (int64_t)k1 * kRowLen + k2);
-                const int pk1 = k1 == 0 ? 0 : n1 - k1;
-                const int pk2 = k1 == 0 ? (kRowLen - k2) & (kRowLen - 1) : kRowLen - 1 - k2;
-                sB[lr * LD + lc] = ld_inter<kStream>(Yj + (int64_t)pk1 * kRowLen + pk2);
+            if (lv[u]) {
+                sA[(e / kEpiT2) * LD + e % kEpiT2] = ra[u];
+                sB[(e / kEpiT2) * LD + e % kEpiT2] = rb[u];
             }
         }
         __syncthreads();
+        if (j + 1 < Kp) fetch(j + 1);
         if (kDiscard) {
             const int t = threadIdx.x;
             if (t < kEpiT1) {

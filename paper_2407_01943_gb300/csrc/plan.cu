@@ -893,8 +893,11 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     g.real_taper = !cplx && (std::fabs(g.fmid_hi) + std::fabs(g.fmid_lo)) * tmax_abs < real_thresh ? 1 : 0;
     // ---- exec path, fine-grid length and spreading kernel ----
     // generic path: nf = power of two >= 2 I (sigma in [2, 4)), w = ceil(log10(1/tol)) + 1, beta = 2.30 w.
-    // packed FP32 path: nf = smallest 2^a or 3 * 2^a >= 1.5 I (sigma in [1.5, 2)), w = ceil(1.25 log10(1/tol)) + 1,
-    // beta = 0.97 pi (1 - 1/(2 sigma)) w (exponential-of-semicircle kernel, Barnett et al. 2019).
+    // packed FP32 path: nf = smallest 2^a or 3 * 2^a >= 1.5 I (sigma in [1.5, 2)), w = ceil(1.25 log10(1/tol))
+    // + 1; with opts.sigma in [1.25, 1.5) also nf = 5 * 2^a, and below sigma 1.5
+    // w = ceil(ln(1/tol) / (pi sqrt(1 - 1/sigma))) + 1 (11 at sigma 1.25, tol 1e-6; the same rule gives
+    // the 9 of the first one at 1.5); beta = 0.97 pi (1 - 1/(2 sigma)) w (exponential-of-semicircle
+    // kernel, Barnett et al. 2019).
     if (opts.path < 0 || opts.path > 3) {
         set_error("opts.path must be 0, 1, 2 or 3");
         return bail(M2_ERR_ARG);
@@ -902,21 +905,29 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
     const double span_t = ts.back() - ts.front();
     bool packed_ok = false;
     int64_t nf_packed = 0;
-    if (!(opts.sigma == 0.0 || (opts.sigma >= 1.5 && opts.sigma <= 8.0))) {
-        set_error("opts.sigma must be 0 (automatic) or in [1.5, 8]");
+    if (!(opts.sigma == 0.0 || (opts.sigma >= 1.25 && opts.sigma <= 8.0))) {
+        set_error("opts.sigma must be 0 (automatic) or in [1.25, 8]");
         return bail(M2_ERR_ARG);
     }
-    int w_packed = std::min(16, std::max(2, (int)std::ceil(1.25 * std::log10(1.0 / p->tol)) + 1));
+    int w_packed = 0;
     if (opts.precision == 32 && g.real_taper && opts.path != 1) {
-        // nf >= sigma I with sigma = 1.5 unless asked for more; at sigma >= 2 the kernel needs the
+        // nf >= sigma I with sigma = 1.5 unless asked otherwise; at sigma >= 2 the kernel needs the
         // narrower width of the generic rule
         const double target = std::max((opts.sigma > 0 ? opts.sigma : 1.5) * (double)g.I, 2048.0);
-        int64_t a2 = 2048, a3 = 3 * 2048;  // nf = 1024 * n1 with n1 even
+        int64_t a2 = 2048, a3 = 3 * 2048, a5 = 5 * 2048;  // nf = 1024 * n1 with n1 even
         while ((double)a2 < target) a2 <<= 1;
         while ((double)a3 < target) a3 <<= 1;
+        while ((double)a5 < target) a5 <<= 1;
         nf_packed = std::min(a2, a3);
-        if ((double)nf_packed >= 2.0 * (double)g.I)
+        if (opts.sigma > 0 && opts.sigma < 1.5) nf_packed = std::min(nf_packed, a5);
+        const double sig = (double)nf_packed / (double)g.I;
+        if (sig >= 2.0)
             w_packed = std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / p->tol)) + 1));
+        else if (sig >= 1.5)
+            w_packed = std::min(16, std::max(2, (int)std::ceil(1.25 * std::log10(1.0 / p->tol)) + 1));
+        else
+            w_packed = std::min(16, std::max(2, (int)std::ceil(std::log(1.0 / p->tol) /
+                                                               (kPi * std::sqrt(1.0 - 1.0 / sig))) + 1));
         const double span = span_t * (double)nf_packed * g.df;
         const bool wrap_p = span + w_packed + 2.0 >= (double)nf_packed;
         const int64_t rows_p = wrap_p ? nf_packed / 1024 : (int64_t)std::ceil((span + w_packed + 2.0) / 1024.0);

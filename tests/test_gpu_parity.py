@@ -824,6 +824,30 @@ def test_sigma_option_parity(dev, prec, path, sigma):
     check(out, Jr, Pr, w, wl.x, prec, idx)
 
 
+@pytest.mark.parametrize("path", [2, 3])
+def test_sigma_125_parity(dev, path):
+    """Oversampling 1.25 on the packed path: nf = 5 * 2^a (n1 = 320 for I = 2^18, ten cosets of 32),
+    the wider kernel of the sigma < 1.5 rule, results within the parity bar at the full-size
+    special positions, and the stage-batched executor bit-identical to the plan's own exec."""
+    wl = synth.workload("jitter16k", batch=2)
+    w = seeded_tapers(wl.K, wl.N, 5)
+    args = (wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I)
+    base = pkg.Plan(*args, precision=32, tapers=w, path=path)
+    plan = pkg.Plan(*args, precision=32, tapers=w, path=path, sigma=1.25)
+    assert plan.info["path"] == path
+    assert plan.info["nf"] == 5 * 65536 and plan.info["n1"] == 320
+    assert plan.info["width"] > base.info["width"]
+    out = run_plan(plan, wl.x, dev)
+    idx = full_size_bands(wl.I, plan.info["n1"], 256, 2)
+    Jr, Pr = oracle_cached(f"jitter16k/b2/w5/n1={plan.info['n1']}", wl.t, wl.x, w, wl.f_lo, wl.df, wl.I, idx)
+    check(out, Jr, Pr, w, wl.x, 32, idx)
+    Ps = [torch.empty((wl.I,), dtype=torch.float32, device=dev) for _ in range(2)]
+    xs = [torch.from_numpy(wl.x[b].astype(np.float32)).to(dev) for b in range(2)]
+    pkg.exec_batch([plan, plan], xs, None, None, Ps)
+    torch.cuda.synchronize()
+    assert all(np.array_equal(Ps[b].cpu().numpy(), out["P"][b]) for b in range(2))
+
+
 def test_sigma_option_rejects_out_of_range(dev):
     wl = synth.workload("jitter16k")
     w = seeded_tapers(wl.K, wl.N, 5)
