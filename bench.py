@@ -238,11 +238,12 @@ def hbm_bytes(info, kernel: str, nb: int, csz: int, rsz: int, outputs: str = "JE
         (I * rsz if "F" in outputs else 0)
     if kernel == "spread":
         if info.get("spread_entries", 0) > 0:
-            # packed paths: x, the cell-major spreading matrix (per entry a sample index and
-            # ceil(K/2) complex weights; read once per launch), slice and tile descriptors
+            # packed paths: x, the cell-major spreading matrix (8 bytes per entry: point word and
+            # window value), the taper pairs (ceil(K/2) complex per point), slice and tile
+            # descriptors -- the plan data read once per launch
             ents = info["spread_entries"]
-            return nb * N * rsz + ents * (4 + (K + 1) // 2 * csz) + (info["rows"] * info["n2"] // 32) * 8 + \
-                (info["rows"] * info["n2"] // 256 + 1) * 16
+            return nb * N * rsz + ents * 8 + N * ((K + 1) // 2) * csz + (info["rows"] * info["n2"] // 32) * 8 + \
+                (info["rows"] * info["n2"] // 256 + 1) * 32
         return nb * N * rsz + N * (8 + rsz) + K * N * taper
     if kernel == "cols":
         return 0.0
