@@ -205,6 +205,11 @@ m2_status m2nufft_plan_subband(const double* t, int64_t N, double fs, double f_w
 
 /*
  * Run the per-signal path for B signals that share the plan's sampling times.
+ * Output buffers (J, E, P, Lhat, Ehat here and in every exec entry point) may be
+ * device memory or page-locked host memory that the device addresses directly
+ * (cudaHostAlloc, or pinned memory under unified addressing): the kernels then
+ * write the results straight into host memory over the host link, with no
+ * separate copy.
  *   x      device [B][N] real (plan precision), each row in the order of t
  *   B      number of signals, >= 0 (0 is a no-op)
  *   J      device [B][K][I] complex, or NULL

@@ -144,6 +144,18 @@ def _tptr(x) -> Optional[int]:
     return x.data_ptr()
 
 
+def _optr(x) -> Optional[int]:
+    """Pointer of an output tensor: device memory, or page-locked host memory that the device
+    addresses directly (the kernels then write the results straight to host memory)."""
+    if x is None:
+        return None
+    if not (x.is_cuda or x.is_pinned()):
+        raise ValueError("expected a CUDA tensor or a pinned host tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
 def _stream_handle(stream) -> Optional[int]:
     if stream is None:
         import torch
@@ -263,12 +275,12 @@ class Plan:
         if F is not None:
             if Lhat is not None or Ehat is not None:
                 raise ValueError("exec with F does not copy L-hat/E-hat; call leakage() or a second exec")
-            st = load().m2nufft_exec_ftest(self._h, _tptr(x), B, _tptr(J), _tptr(E), _tptr(P), _tptr(F),
+            st = load().m2nufft_exec_ftest(self._h, _tptr(x), B, _optr(J), _optr(E), _optr(P), _optr(F),
                                            _stream_handle(stream))
             _check(st, "m2nufft_exec_ftest")
             return
-        st = load().m2nufft_exec(self._h, _tptr(x), B, _tptr(J), _tptr(E), _tptr(P), _tptr(Lhat),
-                                 _tptr(Ehat), _stream_handle(stream))
+        st = load().m2nufft_exec(self._h, _tptr(x), B, _optr(J), _optr(E), _optr(P), _optr(Lhat),
+                                 _optr(Ehat), _stream_handle(stream))
         _check(st, "m2nufft_exec")
 
     def run(self, x, want=("J", "E", "P"), stream=None):
@@ -368,9 +380,9 @@ class BatchCall:
         self.n = n
         self.hp = arr([p.handle.value for p in plans])
         self.hx = arr([_tptr(x) for x in xs])
-        self.hJ = arr([_tptr(j) for j in Js]) if Js is not None else None
-        self.hE = arr([_tptr(e) for e in Es]) if Es is not None else None
-        self.hP = arr([_tptr(q) for q in Ps]) if Ps is not None else None
+        self.hJ = arr([_optr(j) for j in Js]) if Js is not None else None
+        self.hE = arr([_optr(e) for e in Es]) if Es is not None else None
+        self.hP = arr([_optr(q) for q in Ps]) if Ps is not None else None
 
     def __call__(self, stream=None):
         st = load().m2nufft_exec_batch(self.hp, self.hx, self.n, self.hJ, self.hE, self.hP, _stream_handle(stream))

@@ -580,9 +580,9 @@ m2_status exec_one(m2nufft_plan_s* p, const void* x, int64_t B, void* J, void* E
     }
     const Geometry& g = p->g;
     if (Lhat)
-        M2_CUDA_TRY(cudaMemcpyAsync(Lhat, p->d_Lhat, sizeof(double) * g.K * g.I, cudaMemcpyDeviceToDevice, st));
+        M2_CUDA_TRY(cudaMemcpyAsync(Lhat, p->d_Lhat, sizeof(double) * g.K * g.I, cudaMemcpyDefault, st));
     if (Ehat)
-        M2_CUDA_TRY(cudaMemcpyAsync(Ehat, p->d_Ehat, sizeof(double) * g.I, cudaMemcpyDeviceToDevice, st));
+        M2_CUDA_TRY(cudaMemcpyAsync(Ehat, p->d_Ehat, sizeof(double) * g.I, cudaMemcpyDefault, st));
     return M2_OK;
 }
 

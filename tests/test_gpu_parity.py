@@ -1044,3 +1044,32 @@ def test_permuted_sample_order_bitwise(dev, path):
     assert np.array_equal(Ps[0].cpu().numpy(), a["P"][0]) and np.array_equal(Ps[1].cpu().numpy(), a["P"][0])
     Jr, Pr = oracle_all(t, X, w, -0.5, 1.0 / I, I)
     check(b, Jr, Pr, w, X, 32)
+
+
+def test_outputs_in_pinned_host_memory_bitwise(dev):
+    """Output buffers in page-locked host memory: the kernels write J, |J|^2, P-hat (and L-hat / E-hat
+    are copied) straight into host memory, bit-identical to device outputs -- for a multi-chunk exec
+    on the four-kernel path and for the stage-batched executor."""
+    wl = synth.workload("grid1024", batch=12)
+    w, lam = ogpss.nominal_tapers(wl.t, wl.fs, wl.f_w, wl.K)
+    plan = pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32, tapers=w, lam=lam, max_batch=4)
+    assert plan.info["path"] == 2
+    x = torch.from_numpy(wl.x.astype(np.float32)).to(dev)
+    B, K, I = x.shape[0], wl.K, wl.I
+    ref = plan.run(x, want=("J", "E", "P", "Lhat", "Ehat"))
+    Jh = torch.empty((B, K, I), dtype=torch.complex64).pin_memory()
+    Eh = torch.empty((B, K, I), dtype=torch.float32).pin_memory()
+    Ph = torch.empty((B, I), dtype=torch.float32).pin_memory()
+    Lh = torch.empty((K, I), dtype=torch.float64).pin_memory()
+    Ah = torch.empty((I,), dtype=torch.float64).pin_memory()
+    plan.exec(x, Jh, Eh, Ph, Lh, Ah)
+    torch.cuda.synchronize()
+    for got, want in ((Jh, ref["J"]), (Eh, ref["E"]), (Ph, ref["P"]), (Lh, ref["Lhat"]), (Ah, ref["Ehat"])):
+        assert torch.equal(got, want.cpu())
+    Pb = [torch.empty((I,), dtype=torch.float32).pin_memory() for _ in range(3)]
+    pkg.exec_batch([plan] * 3, [x[b] for b in range(3)], None, None, Pb)
+    torch.cuda.synchronize()
+    assert all(torch.equal(Pb[b], ref["P"][b].cpu()) for b in range(3))
+    with pytest.raises(ValueError):
+        plan.exec(x, None, None, torch.empty((B, I), dtype=torch.float32))  # pageable host memory
+    plan.close()
