@@ -442,9 +442,20 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
         while f < 32 and n1 % (2 * f) == 0:
             f *= 2
         return f
-    # one spread launch per taper-pair class, one column launch per coset length, the row FFTs, the epilogue
+    def epi_height(n1, cap=32):  # the stage-batched epilogue's tile height for a plan's n1
+        best, t1 = None, 8
+        for cand in (8, 16, 32):
+            if cand > cap:
+                break
+            waste = -(-n1 // cand) * cand - n1
+            if best is None or waste <= best:
+                best, t1 = waste, cand
+        return t1
+    # one spread launch per taper-pair class, one column launch per coset length, the row FFTs, one
+    # epilogue launch per tile height
     kp_classes = {0 if (p.info["K"] + 1) // 2 <= 2 else (1 if (p.info["K"] + 1) // 2 <= 4 else 2) for p in plans}
-    hb_launches = (len(kp_classes) + len({coset_len(p.info["n1"]) for p in plans}) + 2) if all_packed else None
+    hb_launches = (len(kp_classes) + len({coset_len(p.info["n1"]) for p in plans}) + 1 +
+                   len({epi_height(p.info["n1"]) for p in plans})) if all_packed else None
     stage_split, ms_pipe = None, None
     if all_packed and persistent:
         # the same batch as one persistent pipelined kernel (batch mode 1), for comparison

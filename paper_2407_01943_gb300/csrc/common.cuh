@@ -107,7 +107,8 @@ m2_status exec_fast_chunk(m2nufft_plan_s* p, const float* x, int nb, float2* J, 
 m2_status spread_fast(m2nufft_plan_s* p, const float* x, int nb, float2* g_out, cudaStream_t st);
 // Stage-batched executor of uneven batches of packed plans (hbatch.cu).  CTA shapes of its stage
 // launches (every shape gives the same bits): spread tiles per CTA (1, 2, 4), row FFTs per CTA
-// (4, 8), epilogue tile height T1 (16, 32; tiles T1 x 16, one position per thread).
+// (4, 8), largest epilogue tile height T1 (16, 32; tiles T1 x 16, one position per thread; each task
+// takes the height of 8, 16 or 32 up to it that leaves the fewest idle rows of its n1).
 struct HBConfig {
     int spread_tiles = 2;
     int row_warps = 8;

@@ -146,8 +146,8 @@ struct HBatch {
     size_t smem_cols[6] = {};
     int4* d_rows = nullptr;
     int n_rows = 0;
-    int2* d_epi = nullptr;
-    int n_epi = 0;
+    int2* d_epi[3] = {};  // epilogue tile heights 8, 16, 32
+    int n_epi[3] = {};
     size_t ws_bytes = 0;
     size_t spread_smem = 0;
 
@@ -191,7 +191,7 @@ struct Maps {
     std::vector<int4> co[6];
     size_t smem_cols[6] = {};
     std::vector<int4> ro;
-    std::vector<int2> ep;
+    std::vector<int2> ep[3];  // by epilogue tile height 8, 16, 32
     int64_t ws_f2 = 0;  // workspace, float2 units
     size_t spread_smem_max = 16;  // largest shared memory a task's spread tiles need
     size_t spread_smem() const { return spread_smem_max; }
@@ -226,9 +226,21 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const H
     const int rw = cfg.row_warps;
     for (int j = 0; j < c.Kp; ++j)
         for (int r0 = 0; r0 < c.n1; r0 += rw) m.ro.push_back(make_int4(task, j, r0, std::min(rw, c.n1 - r0)));
-    // epilogue: one cfg.epi_t1 x 16 tile per CTA
-    const int ntile = packed::epi_tiles(c.n1, c.k2max, cfg.epi_t1);
-    for (int e = 0; e < ntile; ++e) m.ep.push_back(make_int2(task, e));
+    // epilogue: one T1 x 16 tile per CTA, T1 <= cfg.epi_t1 the height of 8, 16 or 32 rows that leaves
+    // the fewest idle rows in the task's n1 rows (the largest on a tie): small signals (n1 = 6, 12, 24)
+    // do not run 32-row tiles that are mostly empty
+    int t1 = 8, best = -1;
+    for (int cand : {8, 16, 32}) {
+        if (cand > cfg.epi_t1) break;
+        const int waste = (c.n1 + cand - 1) / cand * cand - c.n1;
+        if (best < 0 || waste <= best) {
+            best = waste;
+            t1 = cand;
+        }
+    }
+    const int cls = t1 == 8 ? 0 : (t1 == 16 ? 1 : 2);
+    const int ntile = packed::epi_tiles(c.n1, c.k2max, t1);
+    for (int e = 0; e < ntile; ++e) m.ep[cls].push_back(make_int2(task, e));
 }
 
 // Device work-map pointers and counts of one launch.
@@ -241,8 +253,8 @@ struct MapView {
     size_t smem_cols[6] = {};
     const int4* ro = nullptr;
     int n_ro = 0;
-    const int2* ep = nullptr;
-    int n_ep = 0;
+    const int2* ep[3] = {};
+    int n_ep[3] = {};
 };
 
 template <int NT>
@@ -277,11 +289,10 @@ m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, con
         else hb_rows_kernel<8><<<v.n_ro, 32 * 8, packed::rowfft_smem_bytes(8), st>>>(v.ro, tasks, ctxs, tw, ws);
         M2_CUDA_TRY(cudaGetLastError());
     }
-    if (v.n_ep) {
-        if (cfg.epi_t1 == 16) hb_epi_kernel<16><<<v.n_ep, 16 * 16, 0, st>>>(v.ep, tasks, ctxs, ws);
-        else hb_epi_kernel<32><<<v.n_ep, 16 * 32, 0, st>>>(v.ep, tasks, ctxs, ws);
-        M2_CUDA_TRY(cudaGetLastError());
-    }
+    if (v.n_ep[0]) hb_epi_kernel<8><<<v.n_ep[0], 16 * 8, 0, st>>>(v.ep[0], tasks, ctxs, ws);
+    if (v.n_ep[1]) hb_epi_kernel<16><<<v.n_ep[1], 16 * 16, 0, st>>>(v.ep[1], tasks, ctxs, ws);
+    if (v.n_ep[2]) hb_epi_kernel<32><<<v.n_ep[2], 16 * 32, 0, st>>>(v.ep[2], tasks, ctxs, ws);
+    M2_CUDA_TRY(cudaGetLastError());
     return M2_OK;
 }
 
@@ -322,7 +333,6 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
     std::vector<int4>* sp = m.sp;
     std::vector<int4>* co = m.co;
     std::vector<int4>& ro = m.ro;
-    std::vector<int2>& ep = m.ep;
     for (int k = 0; k < 6; ++k) H->smem_cols[k] = m.smem_cols[k];
     H->spread_smem = m.spread_smem();
     H->ws_bytes = (size_t)off * sizeof(float2);
@@ -340,8 +350,10 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
     }
     M2_TRY(upload_vec(H->owned, &H->d_rows, ro));
     H->n_rows = (int)ro.size();
-    M2_TRY(upload_vec(H->owned, &H->d_epi, ep));
-    H->n_epi = (int)ep.size();
+    for (int k = 0; k < 3; ++k) {
+        M2_TRY(upload_vec(H->owned, &H->d_epi[k], m.ep[k]));
+        H->n_epi[k] = (int)m.ep[k].size();
+    }
     *out = H.release();
     return M2_OK;
 }
@@ -361,13 +373,16 @@ m2_status hbatch_run(HBatch* H, cudaStream_t st) {
     }
     v.ro = H->d_rows;
     v.n_ro = H->n_rows;
-    v.ep = H->d_epi;
-    v.n_ep = H->n_epi;
+    for (int k = 0; k < 3; ++k) {
+        v.ep[k] = H->d_epi[k];
+        v.n_ep[k] = H->n_epi[k];
+    }
     return launch_maps(v, H->d_tasks, H->d_ctxs, H->tw, H->ws, H->cfg, st);
 }
 
 int hbatch_launches(const HBatch* H) {
-    int n = (H->n_rows ? 1 : 0) + (H->n_epi ? 1 : 0);
+    int n = H->n_rows ? 1 : 0;
+    for (int k = 0; k < 3; ++k) n += H->n_epi[k] ? 1 : 0;
     for (int k = 0; k < 3; ++k) n += H->n_spread[k] ? 1 : 0;
     for (int k = 0; k < 6; ++k) n += H->n_cols[k] ? 1 : 0;
     return n;
@@ -418,8 +433,9 @@ size_t hserve_map_bytes(const HServe* H, int plan) {
     size_t b = sizeof(HTask);
     for (auto& v : m.sp) b += sizeof(int4) * v.size();
     for (auto& v : m.co) b += sizeof(int4) * v.size();
-    b += sizeof(int4) * m.ro.size() + sizeof(int2) * m.ep.size();
-    return b + 16 * 12;  // per-section alignment
+    b += sizeof(int4) * m.ro.size();
+    for (auto& v : m.ep) b += sizeof(int2) * v.size();
+    return b + 16 * 14;  // per-section alignment
 }
 
 m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x, float2* const* J,
@@ -452,7 +468,8 @@ m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x
     for (int k = 0; k < 3; ++k) osp[k] = put(m.sp[k].data(), sizeof(int4) * m.sp[k].size());
     for (int k = 0; k < 6; ++k) oco[k] = put(m.co[k].data(), sizeof(int4) * m.co[k].size());
     const size_t oro = put(m.ro.data(), sizeof(int4) * m.ro.size());
-    const size_t oep = put(m.ep.data(), sizeof(int2) * m.ep.size());
+    size_t oep[3];
+    for (int k = 0; k < 3; ++k) oep[k] = put(m.ep[k].data(), sizeof(int2) * m.ep[k].size());
     if (off > stage_cap) {
         set_error("internal: serving work maps (%zu bytes) exceed the staging buffer (%zu)", off, stage_cap);
         return M2_ERR_ARG;
@@ -470,8 +487,10 @@ m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x
     }
     v.ro = reinterpret_cast<const int4*>(dstage + oro);
     v.n_ro = (int)m.ro.size();
-    v.ep = reinterpret_cast<const int2*>(dstage + oep);
-    v.n_ep = (int)m.ep.size();
+    for (int k = 0; k < 3; ++k) {
+        v.ep[k] = reinterpret_cast<const int2*>(dstage + oep[k]);
+        v.n_ep[k] = (int)m.ep[k].size();
+    }
     return launch_maps(v, reinterpret_cast<const HTask*>(dstage + ot), H->d_ctxs, H->tw, ws, HBConfig{}, st);
 }
 
