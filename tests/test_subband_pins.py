@@ -9,7 +9,11 @@ Eq. gep_at_A0 with f_c0 != 0).
     D = diag(e^{i 2 pi f_c0 t_n}), so the sub-band tapers are the DPSS modulated to f_c0 (with the
     same eigenvalues) -- catches a conjugated or missing modulation;
   * reduction: f_c0 = 0, f_min = 0, f_max = fs/2 gives the full-band (real) tapers;
-  * the Hermitian GEP's invariants: w^H R(B^q) w = 2 f_w, R(B^q)-orthogonality, 0 < lambda < 1.
+  * the Hermitian GEP's invariants: w^H R(B^q) w = 2 f_w, R(B^q)-orthogonality, 0 < lambda < 1;
+  * leakage estimate of sub-band tapers (App. B with R(B^q)): D equals the integral of the shifted
+    taper spectrum |W(f - df)|^2 over f_min <= |f| <= f_max (quadrature; catches a conjugated phase
+    or a dropped half of the band), it reduces to the full-band estimate for f_min = 0,
+    f_max = fs/2 and real tapers, and it vanishes at the nominal centre (D = w^H R(B^q) w = 2 f_w).
 """
 import numpy as np
 import pytest
@@ -18,6 +22,7 @@ import synth
 from oracle import dpss as odpss
 from oracle import estimator as oest
 from oracle import gpss as ogpss
+from oracle import leakage as oleak
 
 integrate = pytest.importorskip("scipy.integrate")
 
@@ -87,3 +92,43 @@ def test_shifted_eigencoefficient_of_a_line_at_the_nominal_centre():
     x = np.exp(2j * np.pi * f_c0 * t)
     J = oest.eigencoefficients(t, x, w, 0.0, 1.0, 1)  # delta f = 0 only
     assert J[0, 0].real > 0 and abs(J[0, 0].imag) < 1e-12 * abs(J[0, 0])
+
+
+def test_subband_leakage_denominator_is_the_band_integral():
+    t = synth.jittered(60, 0.4, 9)
+    rng = np.random.default_rng(4)
+    w = rng.standard_normal((2, 60)) + 1j * rng.standard_normal((2, 60))
+    f_min, f_max = 0.12, 0.33
+    dfs = np.array([-0.07, 0.0, 0.045])
+    D = oleak.leakage_denominator_subband(t, w, f_min, f_max, dfs)
+    tc = t - t.mean()
+    xg, wg = np.polynomial.legendre.leggauss(400)
+    for j, df in enumerate(dfs):
+        for k in range(2):
+            def spec(f):  # |W(f - df)|^2, W(f) = sum_n w_n e^{-i 2 pi f t_n}
+                return np.abs(np.exp(-2j * np.pi * np.outer(f - df, tc)) @ w[k]) ** 2
+            total = 0.0
+            for a, b in ((f_min, f_max), (-f_max, -f_min)):
+                # split each interval so 400 nodes resolve the oscillations (span ~60)
+                for a2, b2 in zip(np.linspace(a, b, 9)[:-1], np.linspace(a, b, 9)[1:]):
+                    f = 0.5 * (b2 - a2) * xg + 0.5 * (b2 + a2)
+                    total += 0.5 * (b2 - a2) * np.sum(wg * spec(f))
+            assert abs(D[k, j] - total) < 1e-10 * abs(total)
+
+
+def test_subband_leakage_reduces_to_full_band():
+    t = synth.jittered(120, 0.4, 10)
+    w, lam = ogpss.nominal_tapers(t, 1.0, 3.0 / 120, 3)
+    fr = np.linspace(-0.5, 0.5, 17)
+    a = oleak.leakage_denominator_subband(t, w.astype(np.complex128), 0.0, 0.5, fr)
+    b = oleak.leakage_denominator(t, w, 1.0, fr)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+
+
+def test_subband_leakage_vanishes_at_the_nominal_centre():
+    t = synth.grid_bernoulli(300, 0.2, 11)
+    fw, f_c0, f_min, f_max = 4.0 / 300, 0.3, 0.2, 0.4
+    w, lam = ogpss.subband_tapers(t, fw, 4, f_c0, f_min, f_max)
+    L, E = oleak.leakage_subband_at(t, w, lam, fw, f_min, f_max, np.array([0.0, 0.01]))
+    assert np.max(L[:, 0]) < 1e-10 and E[0] < 1e-10
+    assert np.max(L[:, 1]) > 1e-6  # a shift off the nominal centre leaks
