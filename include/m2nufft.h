@@ -191,7 +191,10 @@ m2_status m2nufft_plan_with_tapers(const double* t, int64_t N, double fs, double
  *           standard Hermitian eigenproblem of the reduced matrix
  *   lambda  host [K] eigenvalues when w is given, or NULL
  * The tapers are complex, so exec runs the generic path (either precision);
- * leakage estimates and the F-statistic are not formed for sub-band plans.
+ * the F-statistic is not formed for sub-band plans.  The leakage estimates
+ * (App. B, taken with R(B^q) and the shifts f_ci - f_c0 from the nominal
+ * centre) are formed by the direct FP64 pair sum when the eigenvalues are known
+ * and N^2 I <= 1e9; otherwise exec rejects requests for them.
  * The phase of each taper is fixed by making
  * sum_n w_k(t_n) e^{-i 2 pi f_c0 t_n} (t_n - tbar)^(k mod 2) real and positive.
  * A multiband analysis is Q such plans (one per sub-band) run on the same x,

@@ -188,6 +188,64 @@ __global__ void leakage_const_kernel(int K, int64_t I, const double* __restrict_
     Eh[i] = s / K;
 }
 
+// Sub-band plans (complex tapers w = a + i b, band B^q = {f_min <= |f| <= f_max}, shifts
+// df_i = f_ci - f_c0), small problems: the same estimate with R(B^q) (App. B with Eq.
+// gpss_matrix_b_q):  D_k^i = sum_{n,m} Re[conj(w_n) w_m e^{-i 2 pi df_i (t_n - t_m)}] R(B^q|n,m)
+//   = sum_n |w_n|^2 R_nn + 2 sum_{n<m} [(a_n a_m + b_n b_m) cos(th) + (a_n b_m - b_n a_m) sin(th)] R_nm,
+// th = 2 pi df_i (t_n - t_m), R_nm = 2 cos(pi (f_max + f_min) d) sin(pi (f_max - f_min) d) / (pi d),
+// R_nn = 2 (f_max - f_min).  One CTA per band, fixed-order reduction, as leakage_direct_kernel.
+constexpr int kLeakThreadsC = 256;
+__global__ void __launch_bounds__(kLeakThreadsC) leakage_direct_cplx_kernel(
+    int N, int K, int64_t I, const double* __restrict__ tc, const double* __restrict__ wr /*[K][N] sorted*/,
+    const double* __restrict__ wi, double f_min, double f_max, double f_lo, double df,
+    const double* __restrict__ lam, double fw, double* __restrict__ L, double* __restrict__ Eh) {
+    __shared__ double s_red[kLeakThreadsC];
+    __shared__ double s_D[kMaxK];
+    const int64_t i = blockIdx.x;
+    const double f = f_lo + (double)i * df;
+    double D[kMaxK];
+    for (int k = 0; k < K; ++k) D[k] = 0.0;
+    const double rnn = 2.0 * (f_max - f_min);
+    for (int n = threadIdx.x; n < N; n += kLeakThreadsC) {
+        const double tn = tc[n];
+        for (int k = 0; k < K; ++k) {
+            const double a = wr[(int64_t)k * N + n], b = wi[(int64_t)k * N + n];
+            D[k] += (a * a + b * b) * rnn;
+        }
+        for (int m = n + 1; m < N; ++m) {
+            const double d = tn - tc[m];
+            const double r = 2.0 * cospi((f_max + f_min) * d) * sinpi((f_max - f_min) * d) / (kPi * d) * 2.0;
+            double sn, cs;
+            sincospi(2.0 * f * d, &sn, &cs);
+            for (int k = 0; k < K; ++k) {
+                const double an = wr[(int64_t)k * N + n], bn = wi[(int64_t)k * N + n];
+                const double am = wr[(int64_t)k * N + m], bm = wi[(int64_t)k * N + m];
+                D[k] += ((an * am + bn * bm) * cs + (an * bm - bn * am) * sn) * r;
+            }
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        s_red[threadIdx.x] = D[k];
+        __syncthreads();
+        for (int h = kLeakThreadsC / 2; h > 0; h >>= 1) {
+            if ((int)threadIdx.x < h) s_red[threadIdx.x] += s_red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) s_D[k] = s_red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double lh = lam[k] * 2.0 * fw / s_D[k];
+            const double l = fabs(lam[k] - lh);
+            L[(int64_t)k * I + i] = l;
+            s += l;
+        }
+        Eh[i] = s / K;
+    }
+}
+
 // General sampling, small problems: D_k^i = sum_{n,m} w_n w_m R(B|n,m) cos(2 pi f_i (t_n - t_m))
 // evaluated directly (App. B, Eq. lambda_hat_ki).  One CTA per band: the threads split the rows n
 // (n = tid, tid + blockDim, ...; row n adds the diagonal term and twice the pairs m > n), then a
@@ -1375,6 +1433,35 @@ m2_status build_plan(const double* t, int64_t N, double fs, double f_w, int K, c
             M2_TRY_OR(windowed_leakage(p, ts));
             p->have_leakage = 1;
         }
+    } else if (p->have_lambda && cplx && (double)N * (double)N * (double)g.I <= 1.0e9) {
+        // sub-band plan: the direct pair sum with R(B^q) and the shifts from the nominal centre
+        double tbar = 0;
+        for (double v : ts) tbar += v;
+        tbar /= (double)N;
+        std::vector<double> tc(N);
+        for (int64_t j = 0; j < N; ++j) tc[j] = ts[j] - tbar;
+        double *dtc = nullptr, *dwr = nullptr, *dwi = nullptr, *dl = nullptr;
+        M2_CUDA_TRY_OR(cudaMalloc(&dtc, N * sizeof(double)));
+        M2_CUDA_TRY_OR(cudaMalloc(&dwr, (size_t)K * N * sizeof(double)));
+        M2_CUDA_TRY_OR(cudaMalloc(&dwi, (size_t)K * N * sizeof(double)));
+        M2_CUDA_TRY_OR(cudaMalloc(&dl, K * sizeof(double)));
+        cudaMemcpy(dtc, tc.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(dwr, w_sorted.data(), (size_t)K * N * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(dwi, w_sorted_im.data(), (size_t)K * N * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(dl, p->lambda.data(), K * sizeof(double), cudaMemcpyHostToDevice);
+        leakage_direct_cplx_kernel<<<(unsigned)g.I, kLeakThreadsC>>>((int)N, K, g.I, dtc, dwr, dwi, sb->f_min,
+                                                                      sb->f_max, g.f_lo, g.df, dl, f_w, p->d_Lhat,
+                                                                      p->d_Ehat);
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(dtc);
+        cudaFree(dwr);
+        cudaFree(dwi);
+        cudaFree(dl);
+        if (e != cudaSuccess) {
+            set_error("leakage kernel failed: %s", cudaGetErrorString(e));
+            return bail(M2_ERR_CUDA);
+        }
+        p->have_leakage = 1;
     }
 
     // ---- workspace ----

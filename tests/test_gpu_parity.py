@@ -737,6 +737,26 @@ def test_subband_gep_matches_oracle(dev):
         assert s.real > 0 and abs(s.imag) < 1e-9 * abs(s)
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_subband_leakage_matches_oracle(dev, prec):
+    """Leakage estimates of a sub-band plan (App. B with R(B^q), shifts f_ci - f_c0) against the
+    oracle's dense form at every band, from the plan's own tapers and eigenvalues; exec hands them
+    out like those of a full-band plan."""
+    fw, f_c0, f_min, f_max = 4.0 / 400, 0.31, 0.22, 0.45
+    t = synth.grid_bernoulli(500, 0.2, 7)
+    K, I = 4, 256
+    plan = pkg.Plan(t, 1.0, fw, K, 0.25, 0.12 / I, I, precision=prec, subband=(f_c0, f_min, f_max))
+    wg, lg = plan.tapers()
+    L, E = plan.leakage()
+    Lo, Eo = oleak.leakage_subband_at(t, wg, lg, fw, f_min, f_max, 0.25 - f_c0 + 0.12 / I * np.arange(I))
+    np.testing.assert_allclose(L, Lo, rtol=1e-9, atol=1e-13)
+    np.testing.assert_allclose(E, Eo, rtol=1e-9, atol=1e-13)
+    x = torch.from_numpy(synth.white(t, 1.0, 3)[None, :].astype(np.float64 if prec == 64 else np.float32)).to(dev)
+    out = plan.run(x, want=("P", "Lhat", "Ehat"))
+    torch.cuda.synchronize()
+    assert np.array_equal(out["Lhat"].cpu().numpy(), L) and np.array_equal(out["Ehat"].cpu().numpy(), E)
+
+
 def test_multiband_partition_batch(dev):
     """Q = 3 sub-bands partitioning [0, 1/2] run as one exec_batch on the same signal: each equals
     its own exec bit for bit and the oracle within the FP64 tolerance."""
