@@ -185,12 +185,15 @@ def test_batch_equals_alone_bitwise(dev, path):
 
 
 @pytest.mark.parametrize("K,I,N", [(1, 1024, 400), (5, 1024, 700), (3, 2048, 900), (7, 4096, 1500),
-                                   (2, 3000, 1000), (9, 20000, 4000)])
+                                   (2, 3000, 1000), (9, 20000, 4000), (4, 1024, 8000), (6, 2048, 20000)])
 def test_packed_path_edge_cases(dev, K, I, N):
     """Packed FP32 path: odd K (last pair half empty), K = 1, the smallest row
     counts n1 = 2, 4, 8 (self-paired rows 0 and n1/2), wrap-around (span
-    longer than the period) and I not a power of two; against the oracle and
-    against the generic FP32 path."""
+    longer than the period), I not a power of two, and many more samples than
+    bands (N = 8 I, 10 I: the support wraps many times, ~30 spreading-matrix
+    entries per cell, tiles whose samples span the whole signal and are read
+    from global memory instead of staged); against the oracle and against the
+    generic FP32 path."""
     t = synth.jittered(N, 0.4, K + N)
     X = np.stack([synth.white(t, 1.0, 70 + b) for b in range(3)])
     w = seeded_tapers(K, N, K)
