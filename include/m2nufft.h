@@ -286,6 +286,24 @@ m2_status m2nufft_exec_ftest(m2nufft_plan_t p, const void* x, int64_t B, void* J
 m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
                              void* const* Js, void* const* Es, void* const* Ps, void* stream);
 
+/*
+ * As m2nufft_exec_batch, plus Thomson's F-statistic (Sec. 3, Eq. f_stat; the
+ * definition as for m2nufft_exec_ftest) for the signals that ask for it:
+ *   Fs     host [nsig] device pointers, Fs[s] -> [I_s] real, or NULL entries
+ *          (no F for that signal); the array itself is required
+ * Every signal with an F output needs a full-band plan (real tapers) with
+ * K >= 2.  All-packed batches run stage-batched in batch modes 0 and 1 (the
+ * persistent kernel forms no F; its tasks take the 16 x 16 epilogue tiles of
+ * the four-kernel path); batch mode 2 tunes over the stage-batched shapes
+ * only.  Results are bit-identical to m2nufft_exec_ftest on each signal's
+ * plan.  The graph cache key includes the F pointers.
+ * Errors: as m2nufft_exec_batch; M2_ERR_ARG for Fs == NULL, or for a signal
+ * with an F output whose plan has K < 2 or complex (sub-band) tapers.
+ */
+m2_status m2nufft_exec_batch_ftest(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
+                                   void* const* Js, void* const* Es, void* const* Ps, void* const* Fs,
+                                   void* stream);
+
 /* Select how m2nufft_exec_batch runs all-packed batches (process-wide):
  * 0 = one launch per stage (default; spread 2 tiles per CTA, row FFTs 8 rows
  * per CTA, epilogue tiles of 32 x 16 positions), 1 = one persistent pipelined

@@ -65,6 +65,9 @@ EXPORTS = [
     ("m2nufft_exec_ftest", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP]),
     ("m2nufft_exec_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("m2nufft_exec_batch_ftest", ctypes.c_int,
+     [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int64, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+      ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("m2nufft_set_batch_mode", ctypes.c_int, [ctypes.c_int]),
     ("m2nufft_get_batch_tuning", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), _VP, _DP]),
     ("m2nufft_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), _VP, _DP]),
@@ -368,30 +371,37 @@ class Plan:
 
 
 class BatchCall:
-    """m2nufft_exec_batch with its argument arrays marshalled once: for a batch that is run
-    repeatedly on the same plans and buffers, each call then only launches (the library replays
-    its cached graph for the same plans and pointers).  The tensors must stay alive and in place
-    while the object is used."""
+    """m2nufft_exec_batch (m2nufft_exec_batch_ftest when Fs is given) with its argument arrays
+    marshalled once: for a batch that is run repeatedly on the same plans and buffers, each call
+    then only launches (the library replays its cached graph for the same plans and pointers).
+    The tensors must stay alive and in place while the object is used."""
 
-    def __init__(self, plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None):
+    def __init__(self, plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, Fs=None):
         n = len(plans)
         arr = lambda vals: (_VP * n)(*vals)
-        self._keep = (list(plans), xs, Js, Es, Ps)
+        self._keep = (list(plans), xs, Js, Es, Ps, Fs)
         self.n = n
         self.hp = arr([p.handle.value for p in plans])
         self.hx = arr([_tptr(x) for x in xs])
         self.hJ = arr([_optr(j) for j in Js]) if Js is not None else None
         self.hE = arr([_optr(e) for e in Es]) if Es is not None else None
         self.hP = arr([_optr(q) for q in Ps]) if Ps is not None else None
+        self.hF = arr([_optr(f) for f in Fs]) if Fs is not None else None
 
     def __call__(self, stream=None):
+        if self.hF is not None:
+            st = load().m2nufft_exec_batch_ftest(self.hp, self.hx, self.n, self.hJ, self.hE, self.hP, self.hF,
+                                                 _stream_handle(stream))
+            _check(st, "m2nufft_exec_batch_ftest")
+            return
         st = load().m2nufft_exec_batch(self.hp, self.hx, self.n, self.hJ, self.hE, self.hP, _stream_handle(stream))
         _check(st, "m2nufft_exec_batch")
 
 
-def exec_batch(plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, stream=None):
-    """Uneven batch: one signal per entry, each with its own plan."""
-    BatchCall(plans, xs, Js, Es, Ps)(stream)
+def exec_batch(plans: Sequence[Plan], xs, Js=None, Es=None, Ps=None, Fs=None, stream=None):
+    """Uneven batch: one signal per entry, each with its own plan; Fs (optional, entries may be
+    None) adds Thomson's F-statistic for the signals that give one."""
+    BatchCall(plans, xs, Js, Es, Ps, Fs)(stream)
 
 
 def leakage_static(t, w, lam, fs: float, f_w: float, f_lo: float, df: float, I: int, Lhat, Ehat, stream=None):

@@ -23,6 +23,7 @@ void clear_error();
         if (e_ != cudaSuccess) {                                                           \
             ::m2::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),        \
                             __FILE__, __LINE__);                                           \
+            (void)cudaGetLastError(); /* reported here: not again by a later launch check */ \
             return e_ == cudaErrorMemoryAllocation ? M2_ERR_NOMEM : M2_ERR_CUDA;           \
         }                                                                                  \
     } while (0)
@@ -108,7 +109,8 @@ m2_status spread_fast(m2nufft_plan_s* p, const float* x, int nb, float2* g_out, 
 // Stage-batched executor of uneven batches of packed plans (hbatch.cu).  CTA shapes of its stage
 // launches (every shape gives the same bits): spread tiles per CTA (1, 2, 4), row FFTs per CTA
 // (4, 8), largest epilogue tile height T1 (16, 32; tiles T1 x 16, one position per thread; each task
-// takes the height of 8, 16 or 32 up to it that leaves the fewest idle rows of its n1).
+// takes the height of 8, 16 or 32 up to it that leaves the fewest idle rows of its n1).  Tasks with
+// an F-statistic output (Fs[s] non-NULL) take 16 x 16 epilogue tiles whatever the shape.
 struct HBConfig {
     int spread_tiles = 2;
     int row_warps = 8;
@@ -116,7 +118,7 @@ struct HBConfig {
 };
 struct HBatch;
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                        void* const* Es, void* const* Ps, const HBConfig& cfg, HBatch** out);
+                        void* const* Es, void* const* Ps, void* const* Fs, const HBConfig& cfg, HBatch** out);
 m2_status hbatch_run(HBatch* H, cudaStream_t st);
 int hbatch_launches(const HBatch* H);
 void hbatch_free(HBatch* H);

@@ -440,6 +440,18 @@ __global__ void __launch_bounds__(128) ftest_kernel(const typename CT<R>::C* __r
     F[(int64_t)b * I + i] = (cx * cx + cy * cy) * (R)(K - 1) * wq / res;
 }
 
+// The generic path forms F from J: a chunk-sized J buffer for calls that want F but no J,
+// allocated on first use (before a batch capture by exec_batch).
+m2_status prepare_jscratch(m2nufft_plan_s* p) {
+    if (p->d_Jscratch) return M2_OK;
+    const Geometry& g = p->g;
+    const size_t bytes = (p->precision == 32 ? sizeof(float2) : sizeof(double2)) * (size_t)g.chunk * g.K * g.I;
+    M2_CUDA_TRY(cudaMalloc(&p->d_Jscratch, bytes));
+    p->allocations.push_back(p->d_Jscratch);
+    p->device_bytes += bytes;
+    return M2_OK;
+}
+
 template <typename R>
 m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, void* Ev, void* Pv, void* Fv,
                      cudaStream_t st) {
@@ -454,12 +466,7 @@ m2_status exec_typed(m2nufft_plan_s* p, const void* xv, int64_t B, void* Jv, voi
         // all B signals in one launch; the F-statistic runs the four-kernel form (same stages)
         if (g.path == 3 && !F) return exec_pipe(p, x, B, J, E, P, st);
     }
-    if (F && g.path == 1 && !J && !p->d_Jscratch) {
-        // the generic path forms F from J: a chunk-sized J buffer when the caller wants none
-        M2_CUDA_TRY(cudaMalloc(&p->d_Jscratch, sizeof(C) * (size_t)g.chunk * g.K * g.I));
-        p->allocations.push_back(p->d_Jscratch);
-        p->device_bytes += sizeof(C) * (size_t)g.chunk * g.K * g.I;
-    }
+    if (F && g.path == 1 && !J) M2_TRY(prepare_jscratch(p));
     const float2* gall = nullptr;
     if constexpr (std::is_same<R, float>::value) {
         // multi-chunk execs of the packed path: the spread grids of all signals in one launch (the
@@ -718,14 +725,17 @@ m2_status batch_resources(int dev, BatchResources** out) {
 }
 
 m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                        void* const* Es, void* const* Ps, BatchResources& r, cudaGraphExec_t* out) {
+                        void* const* Es, void* const* Ps, void* const* Fs, BatchResources& r, cudaGraphExec_t* out) {
     // stream of each distinct plan, round robin in order of first appearance
     std::unordered_map<const m2nufft_plan_s*, int> lane;
     for (int64_t s = 0; s < nsig; ++s)
         if (!lane.count(plans[s])) lane.emplace(plans[s], (int)(lane.size() % kBatchStreams));
-    // launch configurations of pipelined plans are created before the capture (they allocate)
+    // launch configurations of pipelined plans, and the J buffers of generic plans asked for F
+    // without J, are created before the capture (they allocate)
     for (const auto& kv : lane)
         if (kv.first->g.path == 3) M2_TRY(pipe_prepare(const_cast<m2nufft_plan_s*>(kv.first), 1));
+    for (int64_t s = 0; s < nsig; ++s)
+        if (Fs && Fs[s] && plans[s]->g.path == 1 && !(Js && Js[s])) M2_TRY(prepare_jscratch(plans[s]));
     M2_CUDA_TRY(cudaStreamBeginCapture(r.origin, cudaStreamCaptureModeThreadLocal));
     m2_status st = M2_OK;
     cudaError_t e = cudaEventRecord(r.fork, r.origin);
@@ -738,14 +748,16 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
         m2nufft_plan_s* p = plans[s];
         const int saved = p->timing;
         p->timing = 0;
-        st = exec_one(p, xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr, Ps ? Ps[s] : nullptr, nullptr,
-                      nullptr, nullptr, r.ws[lane[p]]);
+        st = exec_one(p, xs[s], 1, Js ? Js[s] : nullptr, Es ? Es[s] : nullptr, Ps ? Ps[s] : nullptr,
+                      Fs ? Fs[s] : nullptr, nullptr, nullptr, r.ws[lane[p]]);
         p->timing = saved;
     }
-    for (int w = 0; w < kBatchStreams && st == M2_OK; ++w) {
+    // the worker streams are joined back even after a failure, so that ending the capture leaves
+    // none of them capturing
+    for (int w = 0; w < kBatchStreams; ++w) {
         e = cudaEventRecord(r.join[w], r.ws[w]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(r.origin, r.join[w], 0);
-        if (e != cudaSuccess) {
+        if (e != cudaSuccess && st == M2_OK) {
             set_error("batch capture join failed: %s", cudaGetErrorString(e));
             st = M2_ERR_CUDA;
         }
@@ -764,6 +776,7 @@ m2_status capture_batch(const m2nufft_plan_t* plans, const void* const* xs, int6
         }
     }
     if (graph) cudaGraphDestroy(graph);
+    if (st != M2_OK) (void)cudaGetLastError();  // reported: not again by a later launch check
     return st;
 }
 
@@ -786,6 +799,7 @@ m2_status capture_packed_batch(PipeLaunch* L, HBatch* H, BatchResources& r, cuda
         }
     }
     if (graph) cudaGraphDestroy(graph);
+    if (st != M2_OK) (void)cudaGetLastError();  // reported: not again by a later launch check
     return st;
 }
 
@@ -793,9 +807,10 @@ m2_status capture_packed_batch(PipeLaunch* L, HBatch* H, BatchResources& r, cuda
 // rows per CTA 8 / 4, epilogue tiles 32 x 16 / 16 x 16) and the persistent kernel are built,
 // captured and timed on `st` (one warm-up launch, then the mean of three, CUDA events); the
 // fastest is kept (its resources returned), the others freed.  Every candidate writes the same
-// bits.  Synchronous; not allowed while `st` is capturing.
+// bits.  With F-statistic outputs the persistent kernel (which forms none) is not a candidate.
+// Synchronous; not allowed while `st` is capturing.
 m2_status tune_packed_batch(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                            void* const* Es, void* const* Ps, BatchResources& r, cudaStream_t st,
+                            void* const* Es, void* const* Ps, void* const* Fs, BatchResources& r, cudaStream_t st,
                             cudaGraphExec_t* out, PipeLaunch** out_pipe, HBatch** out_hb) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     M2_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
@@ -807,7 +822,7 @@ m2_status tune_packed_batch(m2nufft_plan_s* const* plans, const void* const* xs,
     for (int nt : {1, 2, 4})
         for (int rw : {8, 4})
             for (int t1 : {32, 16}) cands.push_back({0, HBConfig{nt, rw, t1}});
-    cands.push_back({1, HBConfig{}});
+    if (!Fs) cands.push_back({1, HBConfig{}});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     M2_CUDA_TRY(cudaEventCreate(&e0));
     M2_CUDA_TRY(cudaEventCreate(&e1));
@@ -822,7 +837,7 @@ m2_status tune_packed_batch(m2nufft_plan_s* const* plans, const void* const* xs,
         HBatch* hb = nullptr;
         cudaGraphExec_t ex = nullptr;
         status = c.first == 1 ? pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe)
-                              : hbatch_create(plans, xs, nsig, Js, Es, Ps, c.second, &hb);
+                              : hbatch_create(plans, xs, nsig, Js, Es, Ps, Fs, c.second, &hb);
         if (status == M2_OK) status = capture_packed_batch(pipe, hb, r, &ex);
         float ms = 0.f;
         cudaError_t e = cudaSuccess;
@@ -862,6 +877,7 @@ m2_status tune_packed_batch(m2nufft_plan_s* const* plans, const void* const* xs,
         if (best) cudaGraphExecDestroy(best);
         if (best_pipe) pipe_free(best_pipe);
         if (best_hb) hbatch_free(best_hb);
+        (void)cudaGetLastError();  // reported: not again by a later launch check
         return status;
     }
     g_batch_tuning = rows;
@@ -892,31 +908,48 @@ void purge_batch_graphs(const m2nufft_plan_s* p) {
 
 }  // namespace m2
 
-extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
-                                        void* const* Js, void* const* Es, void* const* Ps, void* stream) {
-    m2::clear_error();
+namespace m2 {
+namespace {
+
+// Uneven batches with or without the F-statistic outputs (Fs NULL: none); `fn` names the entry
+// point in error messages.
+m2_status exec_batch_impl(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig, void* const* Js,
+                          void* const* Es, void* const* Ps, void* const* Fs, void* stream, const char* fn) {
+    clear_error();
     if (nsig < 0 || (nsig > 0 && (!plans || !xs))) {
-        m2::set_error("m2nufft_exec_batch: invalid arguments");
+        set_error("%s: invalid arguments", fn);
         return M2_ERR_ARG;
     }
     if (nsig == 0) return M2_OK;
     for (int64_t s = 0; s < nsig; ++s) {
         if (!plans[s] || !xs[s]) {
-            m2::set_error("m2nufft_exec_batch: plan or x %lld is NULL", (long long)s);
+            set_error("%s: plan or x %lld is NULL", fn, (long long)s);
             return M2_ERR_ARG;
         }
         if (plans[s]->precision != plans[0]->precision || plans[s]->device != plans[0]->device) {
-            m2::set_error("m2nufft_exec_batch: plans differ in precision or device");
+            set_error("%s: plans differ in precision or device", fn);
+            return M2_ERR_ARG;
+        }
+        if (Fs && Fs[s] && plans[s]->g.K < 2) {
+            set_error("%s: signal %lld: the F-statistic needs K >= 2 tapers (F(2, 2K - 2))", fn, (long long)s);
+            return M2_ERR_ARG;
+        }
+        if (Fs && Fs[s] && plans[s]->complex_taper) {
+            set_error("%s: signal %lld: the F-statistic is formed for full-band plans (real tapers, f_c0 = 0)", fn,
+                      (long long)s);
             return M2_ERR_ARG;
         }
     }
-    for (int64_t s = 0; s < nsig; ++s) M2_TRY(m2::check_stage_status(plans[s]));
+    bool any_f = false;
+    for (int64_t s = 0; s < nsig && Fs; ++s) any_f = any_f || Fs[s];
+    if (!any_f) Fs = nullptr;
+    for (int64_t s = 0; s < nsig; ++s) M2_TRY(check_stage_status(plans[s]));
     const int dev = plans[0]->device;
-    m2::DeviceGuard guard(dev);
+    DeviceGuard guard(dev);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::vector<uintptr_t> key;
-    key.reserve(1 + 5 * nsig);
-    const int mode = m2::g_batch_mode.load();
+    key.reserve(2 + 6 * nsig);
+    const int mode = g_batch_mode.load();
     key.push_back((uintptr_t)nsig);
     key.push_back((uintptr_t)mode);
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)plans[s]);
@@ -924,47 +957,68 @@ extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void*
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Js ? Js[s] : nullptr));
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Es ? Es[s] : nullptr));
     for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Ps ? Ps[s] : nullptr));
+    for (int64_t s = 0; s < nsig; ++s) key.push_back((uintptr_t)(Fs ? Fs[s] : nullptr));
 
-    std::lock_guard<std::mutex> lock(m2::g_batch_mu);
-    for (auto it = m2::g_graphs.begin(); it != m2::g_graphs.end(); ++it) {
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
         if (it->device == dev && it->key == key) {
-            m2::g_graphs.splice(m2::g_graphs.begin(), m2::g_graphs, it);
-            if (m2::g_graphs.front().pipe) {
-                M2_TRY(m2::pipe_check(m2::g_graphs.front().pipe));
-                m2::pipe_batch_mark_launched(m2::g_graphs.front().pipe);
+            g_graphs.splice(g_graphs.begin(), g_graphs, it);
+            if (g_graphs.front().pipe) {
+                M2_TRY(pipe_check(g_graphs.front().pipe));
+                pipe_batch_mark_launched(g_graphs.front().pipe);
             }
-            M2_CUDA_TRY(cudaGraphLaunch(m2::g_graphs.front().exec, st));
+            M2_CUDA_TRY(cudaGraphLaunch(g_graphs.front().exec, st));
             return M2_OK;
         }
     }
-    m2::BatchResources* res = nullptr;
-    M2_TRY(m2::batch_resources(dev, &res));
+    BatchResources* res = nullptr;
+    M2_TRY(batch_resources(dev, &res));
     cudaGraphExec_t exec = nullptr;
-    m2::PipeLaunch* pipe = nullptr;
-    m2::HBatch* hb = nullptr;
+    PipeLaunch* pipe = nullptr;
+    HBatch* hb = nullptr;
     bool all_packed = plans[0]->precision == 32;
     for (int64_t s = 0; s < nsig && all_packed; ++s) all_packed = plans[s]->g.path >= 2;
     if (all_packed && mode == 2) {
-        M2_TRY(m2::tune_packed_batch(plans, xs, nsig, Js, Es, Ps, *res, st, &exec, &pipe, &hb));
+        M2_TRY(tune_packed_batch(plans, xs, nsig, Js, Es, Ps, Fs, *res, st, &exec, &pipe, &hb));
     } else if (all_packed) {
-        if (mode == 1) M2_TRY(m2::pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
-        else M2_TRY(m2::hbatch_create(plans, xs, nsig, Js, Es, Ps, m2::HBConfig{}, &hb));
-        const m2_status cs = m2::capture_packed_batch(pipe, hb, *res, &exec);
+        // the persistent kernel forms no F-statistic: such batches run stage-batched
+        if (mode == 1 && !Fs) M2_TRY(pipe_batch_create(plans, xs, nsig, Js, Es, Ps, &pipe));
+        else M2_TRY(hbatch_create(plans, xs, nsig, Js, Es, Ps, Fs, HBConfig{}, &hb));
+        const m2_status cs = capture_packed_batch(pipe, hb, *res, &exec);
         if (cs != M2_OK) {
-            if (pipe) m2::pipe_free(pipe);
-            if (hb) m2::hbatch_free(hb);
+            if (pipe) pipe_free(pipe);
+            if (hb) hbatch_free(hb);
             return cs;
         }
     } else {
-        M2_TRY(m2::capture_batch(plans, xs, nsig, Js, Es, Ps, *res, &exec));
+        M2_TRY(capture_batch(plans, xs, nsig, Js, Es, Ps, Fs, *res, &exec));
     }
-    m2::g_graphs.push_front(m2::GraphEntry{dev, std::move(key), exec, pipe, hb});
-    while (m2::g_graphs.size() > m2::kMaxGraphs) {
-        m2::drop_entry(m2::g_graphs.back());
-        m2::g_graphs.pop_back();
+    g_graphs.push_front(GraphEntry{dev, std::move(key), exec, pipe, hb});
+    while (g_graphs.size() > kMaxGraphs) {
+        drop_entry(g_graphs.back());
+        g_graphs.pop_back();
     }
     M2_CUDA_TRY(cudaGraphLaunch(exec, st));
     return M2_OK;
+}
+
+}  // namespace
+}  // namespace m2
+
+extern "C" m2_status m2nufft_exec_batch(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
+                                        void* const* Js, void* const* Es, void* const* Ps, void* stream) {
+    return m2::exec_batch_impl(plans, xs, nsig, Js, Es, Ps, nullptr, stream, "m2nufft_exec_batch");
+}
+
+extern "C" m2_status m2nufft_exec_batch_ftest(const m2nufft_plan_t* plans, const void* const* xs, int64_t nsig,
+                                              void* const* Js, void* const* Es, void* const* Ps, void* const* Fs,
+                                              void* stream) {
+    if (!Fs) {
+        m2::clear_error();
+        m2::set_error("m2nufft_exec_batch_ftest: Fs is NULL");
+        return M2_ERR_ARG;
+    }
+    return m2::exec_batch_impl(plans, xs, nsig, Js, Es, Ps, Fs, stream, "m2nufft_exec_batch_ftest");
 }
 
 extern "C" m2_status m2nufft_set_timing(m2nufft_plan_t p, int enable) {

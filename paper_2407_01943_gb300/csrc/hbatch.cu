@@ -40,7 +40,8 @@ struct __align__(16) HTask {
     int64_t g_off;  // spread grids [Kp][Lg] at ws + g_off
     int64_t z_off;  // Z [Kp][n1][1024] at ws + z_off (then, in place, the row transforms)
     int ctx;
-    int pad0, pad1, pad2;
+    int pad0;
+    float* F;  // Thomson F-statistic [I], or NULL
 };
 static_assert(sizeof(HTask) == 64, "HTask layout");
 
@@ -105,6 +106,20 @@ __global__ void __launch_bounds__(32 * R, 16 / R) hb_rows_kernel(const int4* __r
     packed::rowfft_rows<R, true>(c, tw, Z, m.z, m.w, smem_f2);
 }
 
+// map entry: (task, epilogue tile); the epilogue with the F-statistic: 16 x 16 tiles, 256 threads,
+// one position per thread (the stage and tile shape of the four-kernel path's F epilogue, so the
+// results are bit-identical to m2nufft_exec_ftest)
+__global__ void __launch_bounds__(256, 4) hb_epi_f_kernel(const int2* __restrict__ map, const HTask* tasks,
+                                                          const Ctx* ctxs, const float2* ws) {
+    __shared__ __align__(16) Ctx s_ctx;
+    __shared__ __align__(16) HTask s_task;
+    __shared__ __align__(16) float2 smem[packed::epi_tile_smem_bytes(16) / sizeof(float2)];
+    const int2 m = map[blockIdx.x];
+    load_task(tasks, ctxs, m.x, &s_task, &s_ctx);
+    packed::epi_tile<16, 256, true, true, true>(s_ctx, ws + s_task.z_off, m.y, s_task.J, s_task.E, s_task.P,
+                                                s_task.F, smem);
+}
+
 // map entry: (task, epilogue tile); one T1 x 16 tile per CTA, one position per thread
 template <int T1>
 __global__ void __launch_bounds__(16 * T1) hb_epi_kernel(const int2* __restrict__ map, const HTask* tasks,
@@ -148,6 +163,8 @@ struct HBatch {
     int n_rows = 0;
     int2* d_epi[3] = {};  // epilogue tile heights 8, 16, 32
     int n_epi[3] = {};
+    int2* d_epif = nullptr;  // epilogue with the F-statistic
+    int n_epif = 0;
     size_t ws_bytes = 0;
     size_t spread_smem = 0;
 
@@ -192,6 +209,7 @@ struct Maps {
     size_t smem_cols[6] = {};
     std::vector<int4> ro;
     std::vector<int2> ep[3];  // by epilogue tile height 8, 16, 32
+    std::vector<int2> epf;    // tasks with the F-statistic (16 x 16 tiles)
     int64_t ws_f2 = 0;  // workspace, float2 units
     size_t spread_smem_max = 16;  // largest shared memory a task's spread tiles need
     size_t spread_smem() const { return spread_smem_max; }
@@ -226,6 +244,12 @@ void add_task(Maps& m, int task, const Ctx& c, int64_t ntiles, HTask& t, const H
     const int rw = cfg.row_warps;
     for (int j = 0; j < c.Kp; ++j)
         for (int r0 = 0; r0 < c.n1; r0 += rw) m.ro.push_back(make_int4(task, j, r0, std::min(rw, c.n1 - r0)));
+    // epilogue with the F-statistic: 16 x 16 tiles (every J_k of a position in one thread)
+    if (t.F) {
+        const int nf16 = packed::epi_tiles(c.n1, c.k2max, 16);
+        for (int e = 0; e < nf16; ++e) m.epf.push_back(make_int2(task, e));
+        return;
+    }
     // epilogue: one T1 x 16 tile per CTA, T1 <= cfg.epi_t1 the height of 8, 16 or 32 rows that leaves
     // the fewest idle rows in the task's n1 rows (the largest on a tie): small signals (n1 = 6, 12, 24)
     // do not run 32-row tiles that are mostly empty
@@ -255,6 +279,8 @@ struct MapView {
     int n_ro = 0;
     const int2* ep[3] = {};
     int n_ep[3] = {};
+    const int2* epf = nullptr;
+    int n_epf = 0;
 };
 
 template <int NT>
@@ -289,6 +315,7 @@ m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, con
         else hb_rows_kernel<8><<<v.n_ro, 32 * 8, packed::rowfft_smem_bytes(8), st>>>(v.ro, tasks, ctxs, tw, ws);
         M2_CUDA_TRY(cudaGetLastError());
     }
+    if (v.n_epf) hb_epi_f_kernel<<<v.n_epf, 256, 0, st>>>(v.epf, tasks, ctxs, ws);
     if (v.n_ep[0]) hb_epi_kernel<8><<<v.n_ep[0], 16 * 8, 0, st>>>(v.ep[0], tasks, ctxs, ws);
     if (v.n_ep[1]) hb_epi_kernel<16><<<v.n_ep[1], 16 * 16, 0, st>>>(v.ep[1], tasks, ctxs, ws);
     if (v.n_ep[2]) hb_epi_kernel<32><<<v.n_ep[2], 16 * 32, 0, st>>>(v.ep[2], tasks, ctxs, ws);
@@ -299,7 +326,7 @@ m2_status launch_maps(const MapView& v, const HTask* tasks, const Ctx* ctxs, con
 }  // namespace
 
 m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int64_t nsig, void* const* Js,
-                        void* const* Es, void* const* Ps, const HBConfig& cfg, HBatch** out) {
+                        void* const* Es, void* const* Ps, void* const* Fs, const HBConfig& cfg, HBatch** out) {
     if (!(cfg.spread_tiles == 1 || cfg.spread_tiles == 2 || cfg.spread_tiles == 4) ||
         !(cfg.row_warps == 4 || cfg.row_warps == 8) || !(cfg.epi_t1 == 16 || cfg.epi_t1 == 32)) {
         set_error("internal: unsupported stage-batched CTA shapes");
@@ -325,8 +352,9 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
         t.J = Js ? static_cast<float2*>(Js[s]) : nullptr;
         t.E = Es ? static_cast<float*>(Es[s]) : nullptr;
         t.P = Ps ? static_cast<float*>(Ps[s]) : nullptr;
+        t.F = Fs ? static_cast<float*>(Fs[s]) : nullptr;
         t.ctx = f->second;
-        t.pad0 = t.pad1 = t.pad2 = 0;
+        t.pad0 = 0;
         add_task(m, (int)s, ctxs[(size_t)f->second], p->g.ntiles, t, cfg);
     }
     const int64_t off = m.ws_f2;
@@ -354,6 +382,8 @@ m2_status hbatch_create(m2nufft_plan_s* const* plans, const void* const* xs, int
         M2_TRY(upload_vec(H->owned, &H->d_epi[k], m.ep[k]));
         H->n_epi[k] = (int)m.ep[k].size();
     }
+    M2_TRY(upload_vec(H->owned, &H->d_epif, m.epf));
+    H->n_epif = (int)m.epf.size();
     *out = H.release();
     return M2_OK;
 }
@@ -377,11 +407,13 @@ m2_status hbatch_run(HBatch* H, cudaStream_t st) {
         v.ep[k] = H->d_epi[k];
         v.n_ep[k] = H->n_epi[k];
     }
+    v.epf = H->d_epif;
+    v.n_epf = H->n_epif;
     return launch_maps(v, H->d_tasks, H->d_ctxs, H->tw, H->ws, H->cfg, st);
 }
 
 int hbatch_launches(const HBatch* H) {
-    int n = H->n_rows ? 1 : 0;
+    int n = (H->n_rows ? 1 : 0) + (H->n_epif ? 1 : 0);
     for (int k = 0; k < 3; ++k) n += H->n_epi[k] ? 1 : 0;
     for (int k = 0; k < 3; ++k) n += H->n_spread[k] ? 1 : 0;
     for (int k = 0; k < 6; ++k) n += H->n_cols[k] ? 1 : 0;
@@ -449,8 +481,9 @@ m2_status hserve_launch(HServe* H, int n, const int* plan, const float* const* x
         t.J = J ? J[r] : nullptr;
         t.E = E ? E[r] : nullptr;
         t.P = P[r];
+        t.F = nullptr;
         t.ctx = plan[r];
-        t.pad0 = t.pad1 = t.pad2 = 0;
+        t.pad0 = 0;
         add_task(m, r, H->ctxs[plan[r]], H->ntiles[plan[r]], t, HBConfig{});
     }
     // staging layout: tasks, then the maps, each section 16-byte aligned

@@ -641,6 +641,84 @@ def test_ftest_rejects_single_taper(dev):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["stage_batched", "persistent", "tuned"])
+def test_exec_batch_ftest_matches_single(dev, mode):
+    """m2nufft_exec_batch_ftest over an all-packed uneven batch (different N, K, I; one signal
+    without F): F, J and P-hat equal per-signal m2nufft_exec_ftest bit for bit in every batch
+    mode (mode 1 runs stage-batched, the persistent kernel forms no F); the batch without F
+    outputs on the same plans still equals plain exec."""
+    ws = synth.batched_uneven(5, seed=44, n_min=300, n_max=6000)
+    Ks = [4, 3, 8, 2, 5]
+    plans, xs, Js, Ps, Fs = [], [], [], [], []
+    for s, (wl, K) in enumerate(zip(ws, Ks)):
+        plans.append(pkg.Plan(wl.t, wl.fs, wl.f_w, K, wl.f_lo, wl.df, wl.I, precision=32,
+                              tapers=seeded_tapers(K, wl.N, 70 + s)))
+        xs.append(torch.from_numpy(wl.x[0].astype(np.float32)).to(dev))
+        Js.append(torch.empty((K, wl.I), dtype=torch.complex64, device=dev))
+        Ps.append(torch.empty((wl.I,), dtype=torch.float32, device=dev))
+        Fs.append(None if s == 2 else torch.empty((wl.I,), dtype=torch.float32, device=dev))
+    prev = pkg.binding.set_batch_mode(mode)
+    try:
+        pkg.exec_batch(plans, xs, Js, None, Ps, Fs=Fs)
+        torch.cuda.synchronize()
+        for p, x, J, P, F in zip(plans, xs, Js, Ps, Fs):
+            Jr = torch.empty((1,) + tuple(J.shape), dtype=J.dtype, device=dev)
+            Pr = torch.empty((1,) + tuple(P.shape), dtype=P.dtype, device=dev)
+            if F is None:
+                p.exec(x[None, :], J=Jr, P=Pr)
+            else:
+                Fr = torch.empty((1,) + tuple(F.shape), dtype=F.dtype, device=dev)
+                p.exec(x[None, :], J=Jr, P=Pr, F=Fr)
+            torch.cuda.synchronize()
+            assert torch.equal(Jr[0], J) and torch.equal(Pr[0], P)
+            if F is not None:
+                assert torch.equal(Fr[0], F)
+        # same plans and buffers without F: another graph, plain exec's bits
+        P2 = [torch.empty_like(P) for P in Ps]
+        pkg.exec_batch(plans, xs, None, None, P2)
+        torch.cuda.synchronize()
+        for P, Q in zip(Ps, P2):
+            assert torch.equal(P, Q)
+    finally:
+        pkg.binding.set_batch_mode(prev)
+
+
+def test_exec_batch_ftest_generic_and_rejections(dev):
+    """A batch with a generic-path plan is captured per signal with each signal's F (bitwise equal
+    to exec_ftest); a signal with F on a one-taper plan or a sub-band plan is rejected, and the
+    one-taper plan without an F output is accepted."""
+    ws = synth.batched_uneven(3, seed=45, n_min=300, n_max=1500)
+    paths = [2, 1, 3]
+    plans = [pkg.Plan(wl.t, wl.fs, wl.f_w, wl.K, wl.f_lo, wl.df, wl.I, precision=32,
+                      tapers=seeded_tapers(wl.K, wl.N, 80 + i), path=pth) for i, (wl, pth) in enumerate(zip(ws, paths))]
+    xs = [torch.from_numpy(wl.x[0].astype(np.float32)).to(dev) for wl in ws]
+    Fs = [torch.empty((wl.I,), dtype=torch.float32, device=dev) for wl in ws]
+    pkg.exec_batch(plans, xs, None, None, None, Fs=Fs)
+    torch.cuda.synchronize()
+    for p, x, F in zip(plans, xs, Fs):
+        Fr = torch.empty((1,) + tuple(F.shape), dtype=F.dtype, device=dev)
+        p.exec(x[None, :], F=Fr)
+        torch.cuda.synchronize()
+        assert torch.equal(Fr[0], F)
+    t = synth.jittered(300, 0.4, 1)
+    one = pkg.Plan(t, 1.0, 0.01, 1, -0.5, 1 / 1024, 1024, precision=32, tapers=seeded_tapers(1, 300, 0))
+    x1 = torch.zeros((300,), dtype=torch.float32, device=dev)
+    F1 = torch.empty((1024,), dtype=torch.float32, device=dev)
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.exec_batch([plans[0], one], [xs[0], x1], None, None, None, Fs=[Fs[0], F1])
+    assert e.value.status == 1
+    P1 = torch.empty((1024,), dtype=torch.float32, device=dev)
+    pkg.exec_batch([plans[0], one], [xs[0], x1], None, None, [None, P1], Fs=[Fs[0], None])
+    torch.cuda.synchronize()
+    fw, f_c0, f_min, f_max = 4.0 / 300, 0.3, 0.2, 0.4
+    w, lam = ogpss.subband_tapers(t, fw, 3, f_c0, f_min, f_max)
+    sb = pkg.Plan(t, 1.0, fw, 3, 0.25, 0.1 / 512, 512, precision=32, tapers=w, lam=lam, subband=(f_c0, f_min, f_max))
+    Fsb = torch.empty((512,), dtype=torch.float32, device=dev)
+    with pytest.raises(pkg.M2Error) as e:
+        pkg.exec_batch([sb], [x1], None, None, None, Fs=[Fsb])
+    assert e.value.status == 1
+
+
 # ---------------------------------------------------------------------------
 # interpolated-DPSS tapers (Table 1 step 3 a-c), no GEP
 # ---------------------------------------------------------------------------
