@@ -456,6 +456,16 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
     # library call (cached-graph lookup and launch), not the Python list building
     call = pkg.BatchCall(plans, xs, Js, Es, Ps)
     ms_batch = timed_ms(torch, stream, dev, lambda: call(stream), steps, warmup)
+    # the same batch with Thomson's F-statistic per signal as well (m2nufft_exec_batch_ftest: the
+    # signals' epilogues take the 16 x 16 F tiles)
+    ms_batch_f = None
+    if all_packed:
+        Fs = [torch.empty((wl.I,), dtype=torch.float32, device=dev) for wl in ws]
+        call_f = pkg.BatchCall(plans, xs, Js, Es, Ps, Fs)
+        call_f(stream)  # build + capture + instantiate
+        torch.cuda.synchronize()
+        ms_batch_f = timed_ms(torch, stream, dev, lambda: call_f(stream), steps, warmup)
+        del call_f, Fs
     def coset_len(n1):
         f = 1
         while f < 32 and n1 % (2 * f) == 0:
@@ -535,6 +545,9 @@ def measure_uneven(nsig: int, steps: int, warmup: int, local: int, seed: int, pe
         "l2": "flushed between timed steps (512 MiB write + read-back)",
         "batched": {"value": units / (ms_batch * 1e-3), "ms_per_step": ms_batch, "gpu_launches": hb_launches,
                     "form": "m2nufft_exec_batch, batch mode 0: one CUDA graph, one launch per stage over all signals"},
+        "batched_with_F": None if ms_batch_f is None else {
+            "value": units / (ms_batch_f * 1e-3), "ms_per_step": ms_batch_f,
+            "form": "m2nufft_exec_batch_ftest, batch mode 0: J, |J|^2, P-hat and the F-statistic of every signal"},
         "plain_per_signal": {"value": units / (ms_plain * 1e-3), "ms_per_step": ms_plain, "host_wall_s": wall_plain,
                              "gpu_launches": sum(1 if p.info["path"] == 3 else (4 if p.info["path"] == 2 else 3)
                                                  for p in plans)},
