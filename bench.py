@@ -178,19 +178,42 @@ class ClockSampler:
         return out
 
 
+def source_region_hash(path: str, start: str) -> str:
+    """sha256[:16] of one definition's source text: from the line holding `start` (with a template
+    line just above it) to the first line that is a lone closing brace ("}" or "};"), or that line
+    alone when it is a one-line definition."""
+    import hashlib
+    lines = open(path).read().split("\n")
+    i = next(k for k, ln in enumerate(lines) if start in ln)
+    j = i
+    if not (lines[i].rstrip().endswith("}") and "{" in lines[i]):
+        j = next(k for k in range(i, len(lines)) if lines[k] in ("}", "};"))
+    if i > 0 and lines[i - 1].startswith("template"):
+        i -= 1
+    return hashlib.sha256("\n".join(lines[i:j + 1]).encode()).hexdigest()[:16]
+
+
 def profiled_traffic(workload: str, kernel: str, nb: int):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of this workload
     (profiles/exec_kernels_<workload>_traffic.json), scaled to nb signals per launch; None if there
-    is no capture for this kernel/workload, it was taken at another chunk size, or the kernel
-    sources changed since it was taken."""
+    is no capture for this kernel/workload, it was taken at another chunk size, or the kernel's
+    source changed since it was taken (the definitions the capture lists for that kernel, else the
+    whole source files)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"exec_kernels_{workload}_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        for rel, h in d["sources"].items():
-            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16] != h:
-                return None
+        regions = d.get("kernel_sources", {}).get(kernel)
+        if regions:
+            for key, h in regions.items():
+                rel, start = key.split("::", 1)
+                if source_region_hash(os.path.join(ROOT, rel), start) != h:
+                    return None
+        else:
+            for rel, h in d["sources"].items():
+                if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()[:16] != h:
+                    return None
         k = d["kernels"][kernel]
         if int(d["signals_per_launch"]) != nb:
             return None

@@ -412,10 +412,23 @@ __device__ __forceinline__ void cols_group(const Ctx& c, const Tw32& tw, const f
     for (int r = gwarp; r < C; r += gw) {
         const float2 base = kStaged ? s_B[r * 32 + lane] : __ldg(c.colB + (int64_t)r * kRowLen + l2);
         float2 v[F];
-#pragma unroll
-        for (int q = 0; q < F; ++q) v[q] = make_float2(0.f, 0.f);
         int tix = 0;  // (l1 * r) mod n1, advanced incrementally (the [n1]-table form)
-        for (int f = 0; f < nfold; ++f) {
+        // the first F rows set the fold sums (the same values as adding them to zero, up to the
+        // sign of an exact zero), the later blocks of F rows add to them in row order
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            if (q < rows) {
+                const float2 t = kStaged ? s_tw[r * rows + q] : s_tw[tix];
+                v[q] = cmulf(s_in[q * 32 + lane], t);
+            } else {
+                v[q] = make_float2(0.f, 0.f);
+            }
+            if (!kStaged) {
+                tix += r;
+                if (tix >= n1) tix -= n1;
+            }
+        }
+        for (int f = 1; f < nfold; ++f) {
 #pragma unroll
             for (int q = 0; q < F; ++q) {
                 const int l1 = f * F + q;
