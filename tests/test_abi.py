@@ -43,6 +43,29 @@ def test_version_string_without_gpu():
     assert "sm_103a" in binding.version()
 
 
+def test_batch_argument_errors_without_gpu():
+    """The uneven-batch entry points reject bad arguments before any device work, with the
+    documented status and a message naming the entry point (an empty batch is a no-op)."""
+    lib = binding.load()
+    VP = ctypes.c_void_p
+    none = ctypes.POINTER(VP)()
+    assert lib.m2nufft_exec_batch(none, none, 0, none, none, none, None) == 0
+    assert lib.m2nufft_exec_batch(none, none, -1, none, none, none, None) == 1
+    assert b"m2nufft_exec_batch" in lib.m2nufft_last_error()
+    # the F entry point requires the Fs array itself, even for an empty batch
+    assert lib.m2nufft_exec_batch_ftest(none, none, 0, none, none, none, none, None) == 1
+    assert b"Fs is NULL" in lib.m2nufft_last_error()
+    fs = (VP * 1)(None)
+    assert lib.m2nufft_exec_batch_ftest(none, none, 0, none, none, none, fs, None) == 0
+    assert lib.m2nufft_exec_batch_ftest(none, none, -2, none, none, none, fs, None) == 1
+    assert b"m2nufft_exec_batch_ftest" in lib.m2nufft_last_error()
+    # a NULL plan inside a non-empty batch is named by its index
+    plans = (VP * 2)(None, None)
+    xs = (VP * 2)(None, None)
+    assert lib.m2nufft_exec_batch(plans, xs, 2, none, none, none, None) == 1
+    assert b"plan or x 0 is NULL" in lib.m2nufft_last_error()
+
+
 def test_struct_layouts_match_header():
     # m2_fgrid: 2 doubles + int64; m2_opts: int, double, size_t, int, int, int (natural alignment)
     assert ctypes.sizeof(binding.m2_fgrid) == 24
